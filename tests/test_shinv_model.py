@@ -1,0 +1,173 @@
+"""Pins for the exact-integer model of Algorithms 1-3 (oracle/shinv_model.py).
+
+* The whole-shifted Newton step of Eq. (3) must reproduce the iterates and
+  quotients printed in the paper's worked examples (tests/golden).
+* Algorithm 1 must return floor(B^h / v) + lambda with lambda in {0, 1}
+  (Theorem 2), checked against the Knuth-D oracle's floor(B^h / v).
+* Algorithm 3 must return exactly (u quo v, u rem v), with delta in {-1, 0, 1}.
+* The Refine loop runs ceil(max(log2(h-k-1), 0)) + 2 times.
+* Planted mistakes (sign of PowDiff, one Refine iteration short) must be caught.
+"""
+
+import os
+import random
+
+import pytest
+
+import oracle as O
+import oracle.shinv_model as M
+
+B32 = 1 << 32
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "worked_examples.txt")
+
+
+def _golden():
+    vals = {}
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *rest = line.split()
+            vals[key] = [int(x) for x in rest]
+    return vals
+
+
+def test_worked_examples_eq3_iterates_and_quotients():
+    g = _golden()
+    B, h, v = g["base"][0], g["h"][0], g["v"][0]
+    its = g["iterates"]
+    w = its[0]
+    for expect in its[1:]:
+        w = M.newton_shift_step(w, v, h, B)
+        assert w == expect
+    # Example 1: q = shift_{-h}(u * shinv_h(v)), no correction
+    u1 = g["example1_u"][0]
+    assert M.shift(-h, u1 * w, B) == g["example1_q"][0] == u1 // v
+    # Example 2: q0 is one short; the remainder u - q0 v exceeds v; delta = +1
+    u2 = g["example2_u"][0]
+    q0 = M.shift(-h, u2 * w, B)
+    assert q0 == g["example2_q0"][0]
+    assert u2 - q0 * v == g["example2_rem0"][0] >= v
+    assert q0 + 1 == g["example2_q"][0] == u2 // v
+    # the converged iterate is the shifted inverse of Definition 1
+    assert w == B**h // v
+
+
+def _rand_pair(rnd, nmax):
+    n = rnd.randint(1, nmax)
+    kl = rnd.randint(1, n)
+    u = rnd.getrandbits(32 * n)
+    v = rnd.getrandbits(32 * kl) or 1
+    r = rnd.random()
+    if r < 0.1:
+        v = B32 ** rnd.randint(1, kl) - 1
+    elif r < 0.15:
+        v = B32 ** rnd.randint(0, kl - 1)
+    elif r < 0.2:
+        v = 1 << rnd.randint(0, 32 * kl - 1)
+    return u, v
+
+
+def test_shinv_within_theorem2_against_knuth_oracle():
+    rnd = random.Random(21)
+    for _ in range(400):
+        u, v = _rand_pair(rnd, 24)
+        h = max(M.prec(u, B32), 1)
+        kl = M.prec(v, B32)
+        exact = O.to_int(O.shinv_u32(O.from_int(v, kl), h))
+        s = M.shinv(v, h, B32)
+        assert s - exact in (0, 1), (u, v)
+
+
+def test_div_matches_knuth_oracle_with_bounded_delta():
+    rnd = random.Random(22)
+    deltas = set()
+    for _ in range(400):
+        u, v = _rand_pair(rnd, 24)
+        n, kl = max(M.prec(u, B32), 1), M.prec(v, B32)
+        q, r, d = M.div(u, v, B32)
+        qo, ro, st = O.divmod_u32(O.from_int(u, n), O.from_int(v, kl))
+        assert st == 0 and (q, r) == (O.to_int(qo), O.to_int(ro))
+        assert d in (-1, 0, 1)
+        deltas.add(d)
+    assert 1 in deltas  # the delta = +1 correction is common (Example 2)
+
+
+def test_overestimated_shinv_and_negative_delta_at_base_16():
+    # Theorem 2: the revised Shinv may return floor(B^h/v) + 1. These base-16
+    # divisors reach lambda = 1, and some dividends then need delta = -1.
+    B = 16
+    for v, h in [(32638565307, 11), (13408681392, 11)]:
+        assert M.shinv(v, h, B) == B**h // v + 1
+    rnd = random.Random(23)
+    v, h = 13408681392, 11
+    seen = set()
+    for _ in range(20000):
+        u = rnd.randrange(B ** (h - 1), B**h)
+        q, r, d = M.div(u, v, B)
+        assert (q, r) == divmod(u, v)
+        seen.add(d)
+    assert -1 in seen
+
+
+def test_refine_iteration_count_formula():
+    assert M.refine_iterations(5, 4) == 2  # h-k-1 = 0: log undefined, read as 2
+    assert M.refine_iterations(6, 4) == 2  # h-k-1 = 1
+    assert M.refine_iterations(7, 4) == 3  # h-k-1 = 2
+    assert M.refine_iterations(1024, 511) == 11
+    assert M.refine_iterations(8192, 4095) == 14
+    assert M.refine_iterations(8192, 31) == 15
+    tr = M.Trace()
+    rnd = random.Random(24)
+    v = rnd.getrandbits(32 * 512) | (1 << (32 * 512 - 1))
+    M.shinv(v, 1024, B32, tr)
+    assert tr.iterations == 11
+
+
+def test_special_cases_of_algorithm1():
+    B = B32
+    assert M.shinv(7, 5, B) == B**5 // 7  # v < B
+    assert M.shinv(B**6, 5, B) == 0  # v > B^h
+    assert M.shinv(B**5 // 2 + 1, 5, B) == 1  # 2v > B^h
+    assert M.shinv(B**3, 7, B) == B**4  # v = B^k
+
+
+def _first_bad(mutant):
+    rnd = random.Random(25)
+    for _ in range(300):
+        u, v = _rand_pair(rnd, 20)
+        h = max(M.prec(u, B32), 1)
+        s = mutant(v, h)
+        if s - B32**h // v not in (0, 1):
+            return True
+    return False
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    orig_pd = M.powdiff
+
+    def flipped(v, w, h, ell, B, tr):
+        s, x = orig_pd(v, w, h, ell, B, tr)
+        return (1 - s if x else s), x
+
+    monkeypatch.setattr(M, "powdiff", flipped)
+    assert _first_bad(lambda v, h: M.shinv(v, h, B32))
+    monkeypatch.setattr(M, "powdiff", orig_pd)
+    orig_it = M.refine_iterations
+    monkeypatch.setattr(M, "refine_iterations", lambda h, k: max(2, orig_it(h, k) - 1))
+    assert _first_bad(lambda v, h: M.shinv(v, h, B32))
+
+
+@pytest.mark.parametrize("n,kl", [(1024, 512), (64, 32), (300, 37)])
+def test_product_sizes_stay_near_cost_model(n, kl):
+    # Section 2.3: the division costs a handful of full multiplications; at
+    # half-length divisors the exact trace stays below 7 units of n(n+1)/2.
+    rnd = random.Random(n)
+    u = rnd.getrandbits(32 * n) | (1 << (32 * n - 1))
+    v = rnd.getrandbits(32 * kl) | (1 << (32 * kl - 1))
+    tr = M.Trace()
+    q, r, _ = M.div(u, v, B32, tr)
+    assert (q, r) == divmod(u, v)
+    total = sum(a * b for _, a, b in tr.products)
+    assert total <= 7 * n * (n + 1) / 2
