@@ -1,0 +1,181 @@
+/* mpdiv -- batched exact division of midsize unsigned integers on GB300 (sm_103a).
+ *
+ * Each division computes (q, r) with u = q*v + r and 0 <= r < v by the
+ * whole-shifted-inverse method of arXiv 2606.06386: the shifted inverse
+ * shinv_h(v) = floor(B^h / v) (Definition 1, B = 2^32, h = prec(u)) is refined
+ * by an all-integer Newton iteration (Algorithm 1 with PowDiff, Algorithm 2),
+ * the quotient is shift_{-h}(u * shinv_h(v)), and one-step corrections
+ * (Algorithm 3, Theorem 2) make the remainder exact. One thread block runs one
+ * division; operands and intermediates live in shared memory.
+ *
+ * Conventions for every entry point below:
+ *  - Integers are little-endian arrays of uint32 digits. Digit counts may
+ *    include leading zero digits; effective precisions are found on the device.
+ *  - "Device" pointers are CUDA global-memory pointers of the context's device
+ *    (for instance the data pointers of torch tensors); the caller owns them and
+ *    they must stay valid until the work on `stream` completes. The library
+ *    never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Calls are asynchronous; results are valid after the stream is
+ *    synchronised.
+ *  - Sizes: 1 <= u_limbs, v_limbs <= MPDIV_MAX_LIMBS (8192 digits = 2^18 bits).
+ *    q_limbs >= 1 and r_limbs >= v_limbs. A quotient needs at most
+ *    u_limbs - prec(v) + 1 digits; with q_limbs = u_limbs every quotient fits.
+ *  - Return codes: MPDIV_OK (0) or a negative MPDIV_E* code; the text of the
+ *    last error of a context is available from mpdiv_last_error().
+ *  - Per-item status (int32 array, device): MPDIV_ST_*.
+ */
+#ifndef MPDIV_H
+#define MPDIV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPDIV_MAX_LIMBS 8192
+
+/* return codes */
+#define MPDIV_OK 0
+#define MPDIV_PENDING 1
+#define MPDIV_EINVAL (-1)
+#define MPDIV_EUNSUPPORTED (-2)
+#define MPDIV_ENOMEM (-3)
+#define MPDIV_ECUDA (-4)
+#define MPDIV_EBUSY (-5)
+#define MPDIV_ETIMEDOUT (-6)
+#define MPDIV_ESTATE (-7)
+
+/* per-item status */
+#define MPDIV_ST_OK 0
+#define MPDIV_ST_DIV_BY_ZERO 1          /* v == 0: q and r are written as zero */
+#define MPDIV_ST_CORRECTION_OVERFLOW 2  /* more than the two corrections Theorem 2 allows */
+#define MPDIV_ST_Q_OVERFLOW 3           /* the quotient does not fit in q_limbs (low digits written) */
+#define MPDIV_ST_INTERNAL 4             /* an internal working-buffer bound was exceeded */
+
+/* flags of mpdiv_config.flags */
+#define MPDIV_FLAG_INJECT_LAMBDA 1 /* test only: use shinv + 1, forcing Theorem 2's delta = -1 path */
+
+typedef struct mpdiv_ctx mpdiv_ctx; /* opaque; owned by the library */
+
+typedef struct mpdiv_config {
+  int warps_per_block; /* 0: per size class from the tuning table (mpdiv_autotune) */
+  int blocks_per_sm;   /* persistent kernels: resident blocks per SM; 0: from occupancy */
+  int flags;           /* MPDIV_FLAG_* */
+} mpdiv_config;
+
+/* Create a context on CUDA device `device` (cfg may be NULL for defaults).
+ * The context owns its device workspace, queue buffers, captured CUDA graphs,
+ * tuning table and serving pools. Returns MPDIV_OK or MPDIV_ECUDA/EINVAL. */
+int mpdiv_init(mpdiv_ctx **ctx, int device, const mpdiv_config *cfg);
+
+/* Release everything the context owns (stops a running server first). */
+void mpdiv_destroy(mpdiv_ctx *ctx);
+
+/* Text of the last error recorded on ctx ("" if none). Valid until the next call. */
+const char *mpdiv_last_error(const mpdiv_ctx *ctx);
+
+/* Uniform batch, the plain launch (one thread block per division; Section 3 of
+ * the paper): item i reads u + i*u_stride (u_limbs digits) and v + i*v_stride
+ * (v_limbs digits), writes q + i*q_stride (q_limbs digits, zero-padded),
+ * r + i*r_stride (r_limbs digits, zero-padded) and status[i]. iters may be NULL;
+ * otherwise iters[i] gets the number of Newton (Refine) iterations run.
+ * Strides are in digits. All pointers are device pointers.
+ * Errors: MPDIV_EINVAL (null pointer, non-positive size, r_limbs < v_limbs,
+ * stride shorter than the digit count), MPDIV_EUNSUPPORTED (more than
+ * MPDIV_MAX_LIMBS digits), MPDIV_ECUDA (launch failure). */
+int mpdiv_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, int32_t u_limbs, int64_t u_stride,
+                const uint32_t *v, int32_t v_limbs, int64_t v_stride, uint32_t *q, int32_t q_limbs,
+                int64_t q_stride, uint32_t *r, int32_t r_limbs, int64_t r_stride, int32_t *status, int32_t *iters,
+                void *stream);
+
+/* Ragged batch of mixed precisions in one persistent launch: items are taken
+ * largest-first from a size-sorted queue by resident blocks. Item i reads
+ * u + u_off[i] (u_len[i] digits), v + v_off[i] (v_len[i] digits) and writes
+ * q + q_off[i] (q_len[i] digits), r + r_off[i] (r_len[i] digits), status[i],
+ * iters[i] (iters may be NULL). Offsets are in digits. u_off..r_len and status
+ * are device arrays; the host-side copies of u_len and v_len (u_len_host,
+ * v_len_host, n_items entries each) are used to size and order the work.
+ * Requirements as for mpdiv_batch, per item (r_len[i] >= v_len[i]).
+ * When the same shape list is submitted again, the launch replays a captured
+ * CUDA graph. */
+int mpdiv_batch_ragged(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, const int64_t *u_off,
+                       const int32_t *u_len, const uint32_t *v, const int64_t *v_off, const int32_t *v_len,
+                       uint32_t *q, const int64_t *q_off, const int32_t *q_len, uint32_t *r, const int64_t *r_off,
+                       const int32_t *r_len, int32_t *status, int32_t *iters, const int32_t *u_len_host,
+                       const int32_t *v_len_host, void *stream);
+
+/* Test entry: the shifted inverse of Algorithm 1 for each item, as the
+ * division path computes it: out + i*out_stride gets shinv_h(v_i) (out_limbs
+ * digits, zero-padded) with h = h_digits[i] (device int32 array), iters[i]
+ * the Refine iteration count. By Theorem 2 the value is floor(B^h/v) or one
+ * more. Requires v_i != 0 and h_i >= prec(v_i); otherwise status[i] is set. */
+int mpdiv_debug_shinv(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *v, int32_t v_limbs, int64_t v_stride,
+                      const int32_t *h_digits, uint32_t *out, int32_t out_limbs, int64_t out_stride,
+                      int32_t *iters, int32_t *status, void *stream);
+
+/* Tuning: time the plain kernel for the given (u_limbs, v_limbs) shape at each
+ * candidate block size on `n_items` synthetic divisions and keep the fastest in
+ * the context's tuning table (used when cfg->warps_per_block == 0). Returns the
+ * chosen warps per block (> 0) or a negative error code. Synchronous. */
+int mpdiv_autotune(mpdiv_ctx *ctx, int32_t u_limbs, int32_t v_limbs, int32_t n_items);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching: a host scheduler thread admits submitted requests into
+ * device-resident operand pools (by digit footprint), launches batches of
+ * admitted requests as slots free up, with several batches in flight on
+ * separate streams, and publishes results. Requests that arrive while batches
+ * run join the next launch. */
+typedef struct mpdiv_serve_config {
+  int64_t pool_digits;  /* digits of device operand/result pool (0: 64 Mi digits) */
+  int32_t max_batch;    /* most requests per launch (0: 4096) */
+  int32_t max_inflight; /* launches in flight at once (0: 3) */
+  int32_t max_pending;  /* submitted-but-unfinished requests before EBUSY (0: 1<<20) */
+} mpdiv_serve_config;
+
+/* Start the server on ctx (cfg may be NULL). MPDIV_ESTATE if already running. */
+int mpdiv_serve_start(mpdiv_ctx *ctx, const mpdiv_serve_config *cfg);
+
+/* Submit one division from host memory; the operands are copied before the
+ * call returns. *ticket identifies the request. MPDIV_EBUSY when the request
+ * would exceed max_pending or can never fit the pool; MPDIV_EUNSUPPORTED for
+ * sizes beyond MPDIV_MAX_LIMBS. */
+int mpdiv_serve_submit(mpdiv_ctx *ctx, const uint32_t *u_host, int32_t u_len, const uint32_t *v_host,
+                       int32_t v_len, uint64_t *ticket);
+
+/* Poll a ticket: MPDIV_PENDING while it is queued or running; MPDIV_OK once
+ * done, after copying q (q_cap digits, zero-padded; q_cap >= u_len - prec(v) + 1
+ * always suffices) and r (r_cap >= v_len digits) to host memory and the item
+ * status to *status. A finished ticket can be polled once; afterwards it is
+ * MPDIV_EINVAL. timeout_us > 0 waits up to that long for completion
+ * (MPDIV_ETIMEDOUT after); 0 returns at once. */
+int mpdiv_serve_poll(mpdiv_ctx *ctx, uint64_t ticket, uint32_t *q_host, int32_t q_cap, uint32_t *r_host,
+                     int32_t r_cap, int32_t *status, int64_t timeout_us);
+
+/* Stop admitting, finish every admitted request, stop the scheduler. Results
+ * of finished tickets stay pollable until mpdiv_destroy. */
+int mpdiv_serve_stop(mpdiv_ctx *ctx);
+
+/* Counters of the server: completed requests, launches, and the sum of
+ * requests per launch (for the mean batch size). Any pointer may be NULL. */
+int mpdiv_serve_stats(mpdiv_ctx *ctx, int64_t *completed, int64_t *launches, int64_t *batched_items);
+
+/* Open-loop replay of an arrival stream against the running server, for
+ * latency measurement: request i (operands at u + u_off[i], v + v_off[i] in
+ * host memory) is submitted at t0 + arrival_ns[i] from a submitter thread;
+ * latency_ns[i] is the time from that scheduled arrival until its result was
+ * pollable. Results go to host arrays q + q_off[i] (q_len[i] digits) and
+ * r + r_off[i] (r_len[i] digits); status[i] per item (-1 if never admitted).
+ * *rejected (may be NULL) counts MPDIV_EBUSY retries. Synchronous. */
+int mpdiv_serve_replay(mpdiv_ctx *ctx, int64_t n, const int64_t *arrival_ns, const uint32_t *u,
+                       const int64_t *u_off, const int32_t *u_len, const uint32_t *v, const int64_t *v_off,
+                       const int32_t *v_len, uint32_t *q, const int64_t *q_off, const int32_t *q_len, uint32_t *r,
+                       const int64_t *r_off, const int32_t *r_len, int32_t *status, int64_t *latency_ns,
+                       int64_t *rejected);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPDIV_H */

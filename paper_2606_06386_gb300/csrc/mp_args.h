@@ -1,0 +1,53 @@
+// Kernel argument blocks, shared by the kernels and the host runtime.
+#pragma once
+#include <cstdint>
+
+namespace mp {
+
+struct UniformArgs {
+  const uint32_t* u;
+  const uint32_t* v;
+  uint32_t* q;
+  uint32_t* r;
+  int32_t* status;
+  int32_t* iters;
+  int64_t n, us, vs, qs, rs;
+  int un, vn, qn, rn;
+  int smem_words;
+  int flags;
+};
+
+struct RaggedArgs {
+  const uint32_t* u;
+  const int64_t* u_off;
+  const int32_t* u_len;
+  const uint32_t* v;
+  const int64_t* v_off;
+  const int32_t* v_len;
+  uint32_t* q;
+  const int64_t* q_off;
+  const int32_t* q_len;
+  uint32_t* r;
+  const int64_t* r_off;
+  const int32_t* r_len;
+  int32_t* status;
+  int32_t* iters;
+  const int32_t* order;  // item indices, most expensive first
+  int32_t* head;         // queue head, zero at launch
+  int64_t n;
+  int smem_words;
+  int flags;
+};
+
+struct ShinvArgs {
+  const uint32_t* v;
+  const int32_t* h;
+  uint32_t* out;
+  int32_t* iters;
+  int32_t* status;
+  int64_t n, vs, os;
+  int vn, on;
+  int smem_words;
+};
+
+}  // namespace mp

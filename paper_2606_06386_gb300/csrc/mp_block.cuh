@@ -1,0 +1,370 @@
+// Block-level multi-precision primitives for one division per thread block.
+//
+// Numbers are little-endian arrays of 32-bit digits in shared memory. Every
+// primitive is called by all threads of a group (the whole block, or a slice
+// of whole warps with its own named barrier) with group-uniform arguments and
+// ends with a barrier of that group, so its result is visible to every thread
+// of the group on return.
+//
+// Linear operations (Section 3.2-3.3 of arXiv 2606.06386: compare, subtract,
+// add, shift, subtract a power of B) give each warp a contiguous range of
+// digits and walk it 32 digits at a time, one digit per lane, so that shared
+// memory is read without bank conflicts. Carries and borrows are resolved with
+// the (generate, propagate) formulation of the paper's map-scan-map
+// subtraction (Listings 5-6), but the scan over a 32-digit row is one integer
+// addition of two ballot masks instead of a shuffle ladder, and the scan over
+// warps is the same trick on the per-warp summaries: one barrier per
+// operation.
+//
+// Multiplication (Section 3.4, Fig. 3) is the classical product scheduled as
+// column strips: lane L of a warp owns T consecutive output columns and walks
+// the rows of the shorter operand, keeping a sliding window of T digits of the
+// longer operand in registers and three-word column accumulators updated with
+// mad.lo.cc / madc.hi.cc / addc. Warps take 32-lane strips from a shared
+// counter, heaviest first. A final carry pass folds each strip's two overflow
+// digits into its neighbour.
+#pragma once
+#include <cstdint>
+
+namespace mp {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int T = 7;                // output columns per lane (odd: conflict-free window loads)
+constexpr int WSPAN = 32 * T;       // output columns per warp strip
+constexpr int PAD = WSPAN + T;      // zero digits kept on each side of a multiply operand
+constexpr int RED_WORDS = 96;       // block scratch: per-warp slots + counters
+
+// block scratch layout
+constexpr int RED_CNT = 64;   // multiply work counter
+constexpr int RED_AUX = 65;   // misc broadcast
+
+// A group of whole warps that cooperates on one division: the whole thread
+// block, or a slice of it synchronised by its own named barrier.
+struct Blk {
+  int tid, lane, warp, nw, nt;
+  int bar;   // named barrier id (0: the whole block)
+  int* red;  // RED_WORDS ints of shared scratch owned by this group
+
+  __device__ __forceinline__ void sync() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
+  }
+};
+
+// Group of warps [w0, w0 + nw) of the block with barrier id `bar`.
+__device__ __forceinline__ Blk make_group(int* red, int w0, int nw, int bar) {
+  Blk b;
+  b.tid = threadIdx.x - 32 * w0;
+  b.lane = threadIdx.x & 31;
+  b.warp = (threadIdx.x >> 5) - w0;
+  b.nw = nw;
+  b.nt = 32 * nw;
+  b.bar = bar;
+  b.red = red;
+  return b;
+}
+
+__device__ __forceinline__ Blk make_blk(int* red) { return make_group(red, 0, blockDim.x >> 5, 0); }
+
+// Range of a warp's digits for a linear operation over [0, len): a multiple of 32.
+__device__ __forceinline__ void warp_range(const Blk& b, int len, int& lo, int& hi) {
+  int cw = (len + b.nw - 1) / b.nw;
+  cw = (cw + 31) & ~31;
+  lo = b.warp * cw;
+  hi = min(lo + cw, len);
+}
+
+// ---------------------------------------------------------------- carries
+// C[i] = X(i) + Y(i) (+ cin at digit 0) or X(i) - Y(i) (- cin) for i < len.
+// Returns the carry (borrow) out of digit len-1. C may alias X or Y only where
+// that functor reads index i itself.
+template <bool SUB, class FX, class FY>
+__device__ uint32_t addsub(const Blk& b, uint32_t* C, int len, FX X, FY Y, uint32_t cin) {
+  int lo, hi;
+  warp_range(b, len, lo, hi);
+  uint32_t c = (b.warp == 0) ? cin : 0u;
+  bool allp = true;
+  for (int base = lo; base < hi; base += 32) {
+    const int i = base + b.lane;
+    const bool valid = i < hi;
+    uint32_t d = 0;
+    bool g = false, p = true;
+    if (valid) {
+      const uint32_t x = X(i), y = Y(i);
+      if (!SUB) {
+        const uint64_t s = (uint64_t)x + y;
+        d = (uint32_t)s;
+        g = (s >> 32) != 0;
+        p = (d == FULL);
+      } else {
+        d = x - y;
+        g = x < y;
+        p = (d == 0u);
+      }
+    }
+    const uint32_t gm = __ballot_sync(FULL, g), pm = __ballot_sync(FULL, p);
+    const uint64_t xm = (uint64_t)(gm | pm);
+    const uint64_t sum = xm + gm + c;
+    const uint32_t cinm = (uint32_t)(sum ^ xm ^ gm);  // bit L: carry into lane L
+    const uint32_t ci = (cinm >> b.lane) & 1u;
+    if (valid) C[i] = SUB ? d - ci : d + ci;
+    c = (uint32_t)(sum >> 32);
+    allp = allp && (pm == FULL);
+  }
+  if (b.lane == 0) b.red[b.warp] = (int)(c | ((allp && b.warp != 0) ? 2u : 0u));
+  b.sync();
+  const uint32_t sw = (b.lane < b.nw) ? (uint32_t)b.red[b.lane] : 2u;
+  const uint32_t Gm = __ballot_sync(FULL, (sw & 1u) != 0);
+  const uint32_t Pm = __ballot_sync(FULL, (sw & 3u) == 2u);
+  const uint64_t xw = (uint64_t)(Gm | Pm);
+  const uint64_t ws = xw + Gm;
+  const uint32_t wcm = (uint32_t)(ws ^ xw ^ Gm);
+  const uint32_t wcin = (wcm >> b.warp) & 1u;
+  const uint32_t cout = (b.nw < 32) ? ((wcm >> b.nw) & 1u) : (uint32_t)(ws >> 32);
+  if (wcin) {
+    // add (subtract) one at the bottom of this warp's range
+    for (int base = lo; base < hi; base += 32) {
+      const int i = base + b.lane;
+      const bool valid = i < hi;
+      const uint32_t d = valid ? C[i] : 0u;
+      const bool stop = valid && (SUB ? d != 0u : d != FULL);
+      const uint32_t sm = __ballot_sync(FULL, stop);
+      if (sm == 0u) {
+        if (valid) C[i] = SUB ? FULL : 0u;
+      } else {
+        const int f = __ffs(sm) - 1;
+        if (valid && b.lane < f) C[i] = SUB ? FULL : 0u;
+        if (b.lane == f) C[i] = SUB ? d - 1u : d + 1u;
+        break;
+      }
+    }
+  }
+  b.sync();
+  return cout;
+}
+
+// ---------------------------------------------------------------- reductions
+// Largest i in [lo, hi) with pred(i), or -1.
+template <class F>
+__device__ inline int find_last(const Blk& b, int lo, int hi, F pred) {
+  int best = -1;
+  const int len = hi - lo;
+  if (len > 0) {
+    int wl, wh;
+    warp_range(b, len, wl, wh);
+    for (int top = wh; top > wl; top -= 32) {
+      const int base = top - 32 >= wl ? top - 32 : wl;
+      const int i = base + b.lane;
+      const bool hit = (i < top) && pred(lo + i);
+      const uint32_t m = __ballot_sync(FULL, hit);
+      if (m) {
+        best = lo + base + 31 - __clz(m);
+        break;
+      }
+      if (base == wl) break;
+    }
+  }
+  if (b.lane == 0) b.red[b.warp] = best;
+  b.sync();
+  int r = (b.lane < b.nw) ? b.red[b.lane] : -1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r = max(r, __shfl_xor_sync(FULL, r, o));
+  b.sync();
+  return r;
+}
+
+// Smallest i in [lo, hi) with pred(i), or -1.
+template <class F>
+__device__ inline int find_first(const Blk& b, int lo, int hi, F pred) {
+  int best = 0x7fffffff;
+  const int len = hi - lo;
+  if (len > 0) {
+    int wl, wh;
+    warp_range(b, len, wl, wh);
+    for (int base = wl; base < wh; base += 32) {
+      const int i = base + b.lane;
+      const bool hit = (i < wh) && pred(lo + i);
+      const uint32_t m = __ballot_sync(FULL, hit);
+      if (m) {
+        best = lo + base + __ffs(m) - 1;
+        break;
+      }
+    }
+  }
+  if (b.lane == 0) b.red[b.warp] = best;
+  b.sync();
+  int r = (b.lane < b.nw) ? b.red[b.lane] : 0x7fffffff;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r = min(r, __shfl_xor_sync(FULL, r, o));
+  b.sync();
+  return r == 0x7fffffff ? -1 : r;
+}
+
+// number of significant digits of X[0..len)
+__device__ __forceinline__ int prec(const Blk& b, const uint32_t* X, int len) {
+  return find_last(b, 0, len, [&](int i) { return X[i] != 0u; }) + 1;
+}
+
+// -1, 0, 1 for X < Y, X == Y, X > Y (X has nx digits, Y has ny; zero-extended)
+template <class PX, class PY>
+__device__ inline int cmp(const Blk& b, PX X, int nx, PY Y, int ny) {
+  const int n = max(nx, ny);
+  auto xd = [&](int i) -> uint32_t { return i < nx ? X[i] : 0u; };
+  auto yd = [&](int i) -> uint32_t { return i < ny ? Y[i] : 0u; };
+  const int i = find_last(b, 0, n, [&](int j) { return xd(j) != yd(j); });
+  if (i < 0) return 0;
+  return xd(i) < yd(i) ? -1 : 1;
+}
+
+// C[i] = X(i) for i < len (C must not alias what X reads at other indices)
+template <class FX>
+__device__ inline void copy(const Blk& b, uint32_t* C, int len, FX X) {
+  for (int i = b.tid; i < len; i += b.nt) C[i] = X(i);
+  b.sync();
+}
+
+// X <- X - B^e, digits [e, len); requires X >= B^e. Returns false if no digit
+// at or above e was nonzero (X < B^e).
+__device__ inline bool sub_pow(const Blk& b, uint32_t* X, int e, int len) {
+  const int z = find_first(b, e, len, [&](int i) { return X[i] != 0u; });
+  if (z < 0) return false;
+  for (int i = e + b.tid; i <= z; i += b.nt) X[i] = (i == z) ? X[i] - 1u : FULL;
+  b.sync();
+  return true;
+}
+
+// X <- X + B^e over digits [e, cap); returns false on carry out of cap.
+__device__ inline bool add_pow(const Blk& b, uint32_t* X, int e, int cap) {
+  const int z = find_first(b, e, cap, [&](int i) { return X[i] != FULL; });
+  if (z < 0) return false;
+  for (int i = e + b.tid; i <= z; i += b.nt) X[i] = (i == z) ? X[i] + 1u : 0u;
+  b.sync();
+  return true;
+}
+
+// C <- B^L - P over L digits, P (np digits, zero-extended) nonzero below L.
+// C may alias P.
+__device__ inline void negate(const Blk& b, uint32_t* C, int L, const uint32_t* P, int np) {
+  const int z = find_first(b, 0, min(L, np), [&](int i) { return P[i] != 0u; });
+  for (int i = b.tid; i < L; i += b.nt) {
+    const uint32_t p = i < np ? P[i] : 0u;
+    C[i] = (i < z) ? 0u : ((i == z) ? (0u - p) : ~p);
+  }
+  b.sync();
+}
+
+// ---------------------------------------------------------------- global memory
+template <class F>
+__device__ inline void load_global(const Blk& b, uint32_t* dst, int len, F src) {
+  for (int i = b.tid; i < len; i += b.nt) dst[i] = src(i);
+  b.sync();
+}
+
+// ---------------------------------------------------------------- multiply
+__device__ __forceinline__ void mac3(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t a, uint32_t bb) {
+  asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+      "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+      "addc.u32 %2, %2, 0;"
+      : "+r"(c0), "+r"(c1), "+r"(c2)
+      : "r"(a), "r"(bb));
+}
+
+// One warp strip: lane owns columns [p0, p0+T) of A*B restricted to rows
+// j in [jlo, jhi) of B. Writes the lane's low T digits to C (columns < npos)
+// and its two overflow digits to OV[2s], OV[2s+1] with s = p0 / T.
+__device__ __forceinline__ void mul_strip(const Blk& b, uint32_t* C, int npos, const uint32_t* A, int na,
+                                          const uint32_t* Bv, int nb, uint32_t* OV, int ws) {
+  const int P0 = ws * WSPAN;
+  const int jlo = max(0, P0 - na + 1);
+  const int jhi = min(nb, P0 + WSPAN);
+  const int p0 = P0 + b.lane * T;
+  uint32_t a0[T], a1[T], a2[T];
+#pragma unroll
+  for (int c = 0; c < T; c++) a0[c] = a1[c] = a2[c] = 0u;
+  if (jhi > jlo) {
+    const uint32_t* Aw = A + p0;  // row j, column c reads Aw[c - j]
+    uint32_t ring[T];
+#pragma unroll
+    for (int c = 1; c < T; c++) ring[c] = Aw[c - jlo];
+    ring[0] = 0u;
+    const int ngroups = (jhi - jlo + T - 1) / T;
+    int j = jlo;
+    for (int gi = 0; gi < ngroups; gi++) {
+#pragma unroll
+      for (int r = 0; r < T; r++) {
+        ring[(T - r) % T] = Aw[-(j + r)];
+        const uint32_t bj = Bv[j + r];
+#pragma unroll
+        for (int c = 0; c < T; c++) mac3(a0[c], a1[c], a2[c], ring[(c - r + T) % T], bj);
+      }
+      j += T;
+    }
+  }
+  // fold the three-word columns into T+2 digits
+  uint32_t o[T + 2];
+  uint64_t carry = 0;
+#pragma unroll
+  for (int c = 0; c < T + 2; c++) {
+    uint64_t s = carry;
+    if (c < T) s += a0[c];
+    if (c >= 1 && c - 1 < T) s += a1[c - 1];
+    if (c >= 2 && c - 2 < T) s += a2[c - 2];
+    o[c] = (uint32_t)s;
+    carry = s >> 32;
+  }
+#pragma unroll
+  for (int c = 0; c < T; c++)
+    if (p0 + c < npos) C[p0 + c] = o[c];
+  const int s = ws * 32 + b.lane;
+  OV[2 * s] = o[T];
+  OV[2 * s + 1] = o[T + 1];
+}
+
+// C[0..npos) = (X * Y) mod B^npos. X (nx digits) and Y (ny digits) are
+// multiply operands: PAD zero digits must be addressable below index 0 and
+// above the digit count (the high pads are zeroed here). OV needs
+// 2 * 32 * ceil(npos / WSPAN) words. C must not alias X or Y.
+__device__ inline void mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int nx, uint32_t* Y, int ny, uint32_t* OV) {
+  uint32_t* A = X;
+  uint32_t* Bv = Y;
+  int na = nx, nb = ny;
+  if (nb > na) {
+    A = Y;
+    Bv = X;
+    na = ny;
+    nb = nx;
+  }
+  if (nb <= 0 || npos <= 0) {
+    for (int i = b.tid; i < npos; i += b.nt) C[i] = 0u;
+    b.sync();
+    return;
+  }
+  for (int i = b.tid; i < PAD; i += b.nt) {
+    A[na + i] = 0u;
+    if (i < T) Bv[nb + i] = 0u;
+  }
+  if (b.tid == 0) b.red[RED_CNT] = 0;
+  b.sync();
+  const int nws = (npos + WSPAN - 1) / WSPAN;
+  const int mid = (nws - 1) / 2;
+  while (true) {
+    int idx = 0;
+    if (b.lane == 0) idx = atomicAdd(&b.red[RED_CNT], 1);
+    idx = __shfl_sync(FULL, idx, 0);
+    if (idx >= nws) break;
+    // centre-out order: the strips of a full product carry a trapezoid of work
+    const int ws = (idx == 0) ? mid : ((idx & 1) ? mid + (idx + 1) / 2 : mid - idx / 2);
+    mul_strip(b, C, npos, A, na, Bv, nb, OV, ws);
+  }
+  b.sync();
+  // fold each strip's overflow digits into the next strip's first two columns
+  addsub<false>(
+      b, C, npos, [&](int i) { return C[i]; },
+      [&](int i) -> uint32_t {
+        const int s = i / T;
+        const int off = i - s * T;
+        return (s >= 1 && off < 2) ? OV[2 * (s - 1) + off] : 0u;
+      },
+      0u);
+}
+
+}  // namespace mp

@@ -1,0 +1,362 @@
+// One exact division per thread block: Algorithms 1-3 of arXiv 2606.06386.
+//
+//   h = prec(u);  w = Shinv(v, h)                 (Algorithm 1)
+//   q = shift_{-h}(u * w);  m = v * q             (Algorithm 3)
+//   if u < m: q -= 1, m -= v;  r = u - m;  if r >= v: q += 1, r -= v
+//
+// Shinv handles the special cases of Algorithm 1 (v < B: B^h quo v by a
+// parallel short division; 2v > B^h: 1; v = B^k: B^(h-k)), forms the two-digit
+// initial approximation w = B^3 quo (v_{k-1} + v_k B), and refines it with
+// Refine / Step / PowDiff (Algorithm 2, with the sign kept explicitly). The
+// corrections of Algorithm 3 run at most twice each way (Theorem 2 allows one);
+// more would set MPDIV_ST_CORRECTION_OVERFLOW.
+//
+// Shared-memory plan for an item with h dividend digits and kl divisor digits
+// (all digit counts; PAD zero digits between buffers, shared by neighbours):
+//   V  [kl]            divisor, whole run
+//   W  [h-kl+9]        shifted inverse; later the quotient q
+//   X  [kl+32]         divisor prefix v' and PowDiff result x      } u overlays
+//   R  [h-kl+16]       Step result before its shift                } X..R later
+//   P  [max(h+41, 2h-kl+9)]  products
+//   OV [2 (ceil(|P|/T) + 64)] multiply overflow digits
+// The total does not depend on kl and grows as ~4.6 h digits.
+#pragma once
+#include "mp_block.cuh"
+
+namespace mp {
+
+enum : int { ST_OK = 0, ST_DIV_BY_ZERO = 1, ST_CORR = 2, ST_QOVF = 3, ST_INTERNAL = 4 };
+enum : int { FLAG_INJECT_LAMBDA = 1 };
+
+struct Layout {
+  uint32_t *V, *W, *X, *R, *U, *P, *OV;
+  int capV, capW, capX, capR, capP, capOV, total;
+};
+
+__host__ __device__ __forceinline__ int cap_p(int h, int kl) {
+  const int a = h + 41, c = 2 * h - kl + 9;
+  return a > c ? a : c;
+}
+
+__host__ __device__ __forceinline__ int layout_words(int h, int kl) {
+  const int capP = cap_p(h, kl);
+  const int capOV = 2 * ((capP + T - 1) / T + 64);
+  return 5 * PAD + kl + (h - kl + 9) + (kl + 32) + (h - kl + 16) + capP + capOV;
+}
+
+// Words of dynamic shared memory that cover every item with at most h digits.
+__host__ __device__ __forceinline__ int smem_words_for(int h) { return layout_words(h, 1); }
+
+__device__ __forceinline__ Layout make_layout(uint32_t* sm, int h, int kl) {
+  Layout L;
+  L.capV = kl;
+  L.capW = h - kl + 9;
+  L.capX = kl + 32;
+  L.capR = h - kl + 16;
+  L.capP = cap_p(h, kl);
+  L.capOV = 2 * ((L.capP + T - 1) / T + 64);
+  int off = PAD;
+  L.V = sm + off;
+  off += L.capV + PAD;
+  L.W = sm + off;
+  off += L.capW + PAD;
+  L.X = sm + off;
+  off += L.capX + PAD;
+  L.R = sm + off;
+  off += L.capR + PAD;
+  L.P = sm + off;
+  off += L.capP;
+  L.OV = sm + off;
+  off += L.capOV;
+  L.total = off;
+  L.U = L.X;  // u (h digits) overlays X, the pad and R once the shifted inverse is known
+  return L;
+}
+
+__device__ __forceinline__ int ceil_log2(int x) {  // x >= 1
+  return 32 - __clz(x - 1);
+}
+
+struct ItemIO {
+  const uint32_t* u;
+  int un;
+  const uint32_t* v;
+  int vn;
+  uint32_t* q;
+  int qn;
+  uint32_t* r;
+  int rn;
+};
+
+// Refine loop count of Algorithm 1: ceil(max(log2(h-k-1), 0)) + 2, taken as 2
+// when h-k-1 <= 1.
+__device__ __forceinline__ int refine_iters(int h, int k) {
+  const int t = h - k - 1;
+  return t <= 1 ? 2 : ceil_log2(t) + 2;
+}
+
+// Algorithm 1 for v (in L.V, kl digits, top digit nonzero) and h >= kl.
+// Leaves shinv_h(v) in L.W and returns its digit count bound in *lw.
+// Returns a status.
+__device__ inline int shinv(const Blk& b, const Layout& L, int h, int kl, int* lw_out, int* iters_out) {
+  const int k = kl - 1;
+  uint32_t* V = L.V;
+  uint32_t* W = L.W;
+  *iters_out = 0;
+  if (kl == 1) {
+    // v < B: B^h quo v by short division from the top. The running remainder
+    // above digit i is B^(h-1-i) mod v, so each thread starts its chunk with a
+    // modular power and then steps down one digit at a time.
+    const uint32_t v0 = V[0];
+    if (h + 1 > L.capW) return ST_INTERNAL;
+    const int chunk = (h + b.nt - 1) / b.nt;
+    const int c0 = b.tid * chunk, c1 = min(h, c0 + chunk);
+    if (c0 < c1) {
+      const uint64_t beta = (1ull << 32) % v0;
+      uint64_t rho = 1 % v0, base = beta;
+      for (int e = h - c1; e > 0; e >>= 1) {  // rho = beta^(h - c1) mod v0
+        if (e & 1) rho = (rho * base) % v0;
+        base = (base * base) % v0;
+      }
+      for (int i = c1 - 1; i >= c0; i--) {
+        const uint64_t cur = rho << 32;
+        W[i] = (uint32_t)(cur / v0);
+        rho = cur % v0;
+      }
+    }
+    if (b.tid == 0) W[h] = (v0 == 1u) ? 1u : 0u;
+    b.sync();
+    *lw_out = h + 1;
+    return ST_OK;
+  }
+  const bool low_zero = find_first(b, 0, k, [&](int i) { return V[i] != 0u; }) < 0;
+  const uint32_t vtop = V[k];
+  if (h == kl && (vtop > 0x80000000u || (vtop == 0x80000000u && !low_zero))) {
+    // 2v > B^h
+    if (b.tid == 0) W[0] = 1u;
+    b.sync();
+    *lw_out = 1;
+    return ST_OK;
+  }
+  if (vtop == 1u && low_zero) {
+    // v = B^k
+    if (h - k + 1 > L.capW) return ST_INTERNAL;
+    if (b.tid == 0) W[h - k] = 1u;
+    b.sync();
+    *lw_out = h - k + 1;
+    return ST_OK;
+  }
+  // initial approximation: w = B^3 quo (v_{k-1} + v_k B), then shift_g with g = 2
+  {
+    const uint64_t V2 = ((uint64_t)vtop << 32) | V[k - 1];
+    const unsigned __int128 num = (unsigned __int128)1 << 96;
+    const unsigned __int128 w0 = num / V2;  // in (B, B^2]
+    if (b.tid == 0) {
+      W[2] = (uint32_t)w0;
+      W[3] = (uint32_t)(w0 >> 32);
+      W[4] = (uint32_t)(w0 >> 64);
+    }
+    b.sync();
+  }
+  int lw = 5;
+  int ell = 2;
+  const int g = 2;
+  const int nit = refine_iters(h, k);
+  uint32_t* X = L.X;
+  uint32_t* P = L.P;
+  uint32_t* R = L.R;
+  for (int it = 0; it < nit; it++) {
+    const int m = min(h - k + 1 - ell, ell);
+    const int s = max(0, k - 2 * ell + 1 - g);
+    const int hh = k + ell + m - s + g;  // Step's h
+    const int e = hh - 2 * m;            // digits Step drops from w*x
+    if (m < 0 || e < 1) return ST_INTERNAL;
+    const int pv = kl - s;               // prec of v' = shift_{-s}(v)
+    if (pv > L.capX) return ST_INTERNAL;
+    copy(b, X, pv, [&](int i) { return V[s + i]; });
+    const int pw = prec(b, W, lw);
+    // ---- PowDiff(v', w, hp, ellp): (sign, |B^hp - v' w|)
+    const int hp = hh - m;
+    const int ellp = ell - g;
+    const int Lc = pv + pw - ellp + 1;
+    int sign, px;
+    if (pw == 0 || Lc >= hp) {
+      const int np = pv + pw;
+      if (np > L.capP || np > L.capX || hp + 1 > L.capX) return ST_INTERNAL;
+      mul(b, P, np, X, pv, W, pw, L.OV);
+      const bool ge = find_first(b, hp, np, [&](int i) { return P[i] != 0u; }) >= 0;
+      if (!ge) {
+        sign = 1;
+        if (pw == 0) {  // v' w = 0: x = B^hp
+          for (int i = b.tid; i <= hp; i += b.nt) X[i] = (i == hp) ? 1u : 0u;
+          b.sync();
+          px = hp + 1;
+        } else {
+          negate(b, X, hp, P, np);
+          px = hp;
+        }
+      } else {
+        sign = 0;
+        copy(b, X, np, [&](int i) { return P[i]; });
+        sub_pow(b, X, hp, np);
+        px = np;
+      }
+    } else {
+      if (Lc > L.capP || Lc > L.capX) return ST_INTERNAL;
+      mul(b, P, Lc, X, pv, W, pw, L.OV);  // MultMod: v' w mod B^L
+      const int top = find_last(b, 0, Lc, [&](int i) { return P[i] != 0u; });
+      if (top < 0) {
+        sign = 1;
+        px = 0;
+      } else if (top < Lc - 1) {
+        sign = 0;
+        copy(b, X, Lc, [&](int i) { return P[i]; });
+        px = Lc;
+      } else {
+        sign = 1;
+        negate(b, X, Lc, P, Lc);
+        px = Lc;
+      }
+    }
+    px = (px > 0) ? prec(b, X, px) : 0;
+    // ---- Step: res = w B^m +/- shift_{2m-hh}(w x), floor semantics
+    int lr;
+    if (px == 0) {
+      lr = pw + m;
+      if (lr > L.capR) return ST_INTERNAL;
+      copy(b, R, lr, [&](int i) { return i >= m ? W[i - m] : 0u; });
+    } else {
+      const int nt = pw + px;
+      if (nt > L.capP) return ST_INTERNAL;
+      mul(b, P, nt, W, pw, X, px, L.OV);
+      lr = max(pw + m, nt - e) + 1;
+      if (lr > L.capR) return ST_INTERNAL;
+      auto wm = [&](int i) -> uint32_t { return (i >= m && i - m < pw) ? W[i - m] : 0u; };
+      auto pe = [&](int i) -> uint32_t { return (i + e < nt) ? P[i + e] : 0u; };
+      if (sign) {
+        addsub<false>(b, R, lr, wm, pe, 0u);
+      } else {
+        const uint32_t c = find_first(b, 0, min(e, nt), [&](int i) { return P[i] != 0u; }) >= 0 ? 1u : 0u;
+        const uint32_t bout = addsub<true>(b, R, lr, wm, pe, c);
+        if (bout) return ST_INTERNAL;  // a negative iterate never happens (Theorem 2)
+      }
+    }
+    // ---- w <- shift_{-m}(res) for the first two iterations, else shift_{-1}(res)
+    const int d = (it < 2) ? m : 1;
+    lw = max(lr - d, 0);
+    if (lw > L.capW) return ST_INTERNAL;
+    copy(b, W, lw, [&](int i) { return R[i + d]; });
+    if (it >= 2) ell = ell + m - 1;
+  }
+  // final shift of Refine: h-k-4 digits when h-k < 2, else -2
+  const int dd = (h - k < 2) ? 4 - (h - k) : 2;
+  const int nl = max(lw - dd, 0);
+  copy(b, R, nl, [&](int i) { return W[i + dd]; });
+  copy(b, W, nl, [&](int i) { return R[i]; });
+  *lw_out = nl;
+  *iters_out = nit;
+  return ST_OK;
+}
+
+// Store digits [0, n) of S to global g[0..cap), zero-padded; S digits at or
+// above n are treated as zero.
+__device__ __forceinline__ void store_digits(const Blk& b, uint32_t* g, int cap, const uint32_t* S, int n) {
+  for (int i = b.tid; i < cap; i += b.nt) g[i] = (i < n) ? S[i] : 0u;
+}
+
+// The whole of Algorithm 3 for one item. Returns a status; q and r are always
+// written (zeros on division by zero).
+__device__ inline int div_item(const Blk& b, uint32_t* sm, int smem_words, const ItemIO& io, int flags, int* iters_out,
+                        uint32_t* dbg_w, int dbg_cap, int h_override) {
+  const uint32_t* gu = io.u;
+  const uint32_t* gv = io.v;
+  *iters_out = 0;
+  const int kl = find_last(b, 0, io.vn, [&](int i) { return gv[i] != 0u; }) + 1;
+  int h;
+  if (h_override > 0) {
+    h = h_override;  // debug entry: shinv_h(v) only
+  } else {
+    h = find_last(b, 0, io.un, [&](int i) { return gu[i] != 0u; }) + 1;
+  }
+  if (kl == 0) {
+    store_digits(b, io.q, io.qn, nullptr, 0);
+    store_digits(b, io.r, io.rn, nullptr, 0);
+    return ST_DIV_BY_ZERO;
+  }
+  if (h_override <= 0) {
+    bool ult = h < kl;
+    if (h == kl) ult = cmp(b, gu, h, gv, kl) < 0;
+    if (ult) {  // u < v: q = 0, r = u
+      store_digits(b, io.q, io.qn, nullptr, 0);
+      for (int i = b.tid; i < io.rn; i += b.nt) io.r[i] = (i < h) ? gu[i] : 0u;
+      return (h > io.rn) ? ST_INTERNAL : ST_OK;
+    }
+  } else if (h < kl) {
+    return ST_INTERNAL;
+  }
+  const Layout L = make_layout(sm, h, kl);
+  if (L.total > smem_words) return ST_INTERNAL;
+  for (int i = b.tid; i < L.total; i += b.nt) sm[i] = 0u;
+  b.sync();
+  load_global(b, L.V, kl, [&](int i) { return gv[i]; });
+  int lw = 0, iters = 0;
+  int st = shinv(b, L, h, kl, &lw, &iters);
+  *iters_out = iters;
+  if (st != ST_OK) return st;
+  uint32_t* W = L.W;
+  if (flags & FLAG_INJECT_LAMBDA) {
+    if (!add_pow(b, W, 0, L.capW)) return ST_INTERNAL;
+    lw = min(lw + 1, L.capW);
+  }
+  lw = prec(b, W, lw);
+  if (dbg_w != nullptr) {
+    store_digits(b, dbg_w, dbg_cap, W, lw);
+    return lw > dbg_cap ? ST_QOVF : ST_OK;
+  }
+  // ---- q0 = shift_{-h}(u * w)
+  uint32_t* U = L.U;
+  uint32_t* P = L.P;
+  load_global(b, U, h, [&](int i) { return gu[i]; });
+  const int np = h + lw;
+  if (np > L.capP) return ST_INTERNAL;
+  mul(b, P, np, U, h, W, lw, L.OV);
+  int lq = np - h;
+  if (lq + 1 > L.capW) return ST_INTERNAL;
+  copy(b, W, lq, [&](int i) { return P[h + i]; });  // q lives in W from here
+  if (b.tid == 0) W[lq] = 0u;
+  lq = prec(b, W, lq);
+  // ---- m = v * q
+  uint32_t* V = L.V;
+  int nm = kl + lq;
+  if (nm > L.capP) return ST_INTERNAL;
+  mul(b, P, nm, V, kl, W, lq, L.OV);
+  nm = prec(b, P, nm);
+  // ---- if u < m: q -= 1, m -= v   (Theorem 2: delta = -1)
+  for (int t = 0;; t++) {
+    if (cmp(b, U, h, P, nm) >= 0) break;
+    if (t == 2) return ST_CORR;
+    if (!sub_pow(b, W, 0, lq)) return ST_INTERNAL;
+    addsub<true>(b, P, nm, [&](int i) { return P[i]; }, [&](int i) { return i < kl ? V[i] : 0u; }, 0u);
+    lq = prec(b, W, lq);
+    nm = prec(b, P, nm);
+  }
+  // ---- r = u - m (into P, in place)
+  addsub<true>(b, P, h, [&](int i) { return U[i]; }, [&](int i) { return i < nm ? P[i] : 0u; }, 0u);
+  int lr = prec(b, P, h);
+  // ---- if r >= v: q += 1, r -= v   (Theorem 2: delta = +1)
+  for (int t = 0;; t++) {
+    if (cmp(b, P, lr, V, kl) < 0) break;
+    if (t == 2) return ST_CORR;
+    if (!add_pow(b, W, 0, L.capW)) return ST_INTERNAL;
+    lq = min(lq + 1, L.capW);
+    addsub<true>(b, P, lr, [&](int i) { return P[i]; }, [&](int i) { return i < kl ? V[i] : 0u; }, 0u);
+    lq = prec(b, W, lq);
+    lr = prec(b, P, lr);
+  }
+  store_digits(b, io.q, io.qn, W, lq);
+  store_digits(b, io.r, io.rn, P, lr);
+  if (lr > io.rn) return ST_INTERNAL;
+  return lq > io.qn ? ST_QOVF : ST_OK;
+}
+
+}  // namespace mp

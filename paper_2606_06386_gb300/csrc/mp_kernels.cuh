@@ -1,0 +1,96 @@
+// Kernels of the division library: the plain launch (one thread block per
+// division, grid over the batch), the persistent launch over a size-sorted
+// work queue for mixed precisions, and the shifted-inverse test entry.
+#pragma once
+#include "mp_args.h"
+#include "mp_div.cuh"
+
+namespace mp {
+
+// Plain launch: block b handles items b, b + gridDim.x, ...
+template <int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_div_uniform(UniformArgs a) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ int red[RED_WORDS];
+  const Blk b = make_blk(red);
+  for (int64_t item = blockIdx.x; item < a.n; item += gridDim.x) {
+    ItemIO io;
+    io.u = a.u + item * a.us;
+    io.un = a.un;
+    io.v = a.v + item * a.vs;
+    io.vn = a.vn;
+    io.q = a.q + item * a.qs;
+    io.qn = a.qn;
+    io.r = a.r + item * a.rs;
+    io.rn = a.rn;
+    int it = 0;
+    const int st = div_item(b, sm, a.smem_words, io, a.flags, &it, nullptr, 0, 0);
+    if (b.tid == 0) {
+      a.status[item] = st;
+      if (a.iters) a.iters[item] = it;
+    }
+    b.sync();
+  }
+}
+
+// Persistent launch over a size-sorted queue: each block repeatedly takes the
+// next item (largest first) until the queue is empty.
+template <int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_div_ragged(RaggedArgs a) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ int red[RED_WORDS];
+  const Blk b = make_blk(red);
+  while (true) {
+    if (b.tid == 0) red[RED_AUX] = atomicAdd(a.head, 1);
+    b.sync();
+    const int idx = red[RED_AUX];
+    b.sync();
+    if ((int64_t)idx >= a.n) break;
+    const int item = a.order[idx];
+    ItemIO io;
+    io.u = a.u + a.u_off[item];
+    io.un = a.u_len[item];
+    io.v = a.v + a.v_off[item];
+    io.vn = a.v_len[item];
+    io.q = a.q + a.q_off[item];
+    io.qn = a.q_len[item];
+    io.r = a.r + a.r_off[item];
+    io.rn = a.r_len[item];
+    int it = 0;
+    const int st = div_item(b, sm, a.smem_words, io, a.flags, &it, nullptr, 0, 0);
+    if (b.tid == 0) {
+      a.status[item] = st;
+      if (a.iters) a.iters[item] = it;
+    }
+    b.sync();
+  }
+}
+
+// Test entry: shinv_h(v) as the division path computes it.
+template <int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_shinv(ShinvArgs a) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ int red[RED_WORDS];
+  const Blk b = make_blk(red);
+  for (int64_t item = blockIdx.x; item < a.n; item += gridDim.x) {
+    ItemIO io;
+    io.u = nullptr;
+    io.un = 0;
+    io.v = a.v + item * a.vs;
+    io.vn = a.vn;
+    io.q = a.out + item * a.os;  // unused by the debug path except on v == 0
+    io.qn = a.on;
+    io.r = a.out + item * a.os;
+    io.rn = 0;
+    int it = 0;
+    const int h = max(a.h[item], 1);
+    const int st = div_item(b, sm, a.smem_words, io, 0, &it, a.out + item * a.os, a.on, h);
+    if (b.tid == 0) {
+      a.status[item] = st;
+      if (a.iters) a.iters[item] = it;
+    }
+    b.sync();
+  }
+}
+
+}  // namespace mp

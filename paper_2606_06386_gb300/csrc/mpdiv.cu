@@ -1,0 +1,412 @@
+// Host side of the C ABI in include/mpdiv.h: argument checks, launch
+// configuration, the size-sorted queue of the persistent launch and its CUDA
+// graph cache, the shifted-inverse test entry and the block-size tuner.
+// The serving loop lives in mpdiv_serve.cu.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "mp_kernels.cuh"
+#include "mpdiv.h"
+#include "mpdiv_internal.h"
+
+using namespace mp;
+
+// ------------------------------------------------------------------ kernels
+namespace {
+
+template <int MAXT, int MINB>
+struct Kern {
+  static void* get(int kk) {
+    switch (kk) {
+      case 0: return (void*)k_div_uniform<MAXT / 32, MINB>;
+      case 1: return (void*)k_div_ragged<MAXT / 32, MINB>;
+      default: return (void*)k_shinv<MAXT / 32, MINB>;
+    }
+  }
+};
+
+enum KernKind { KK_UNIFORM = 0, KK_RAGGED = 1, KK_SHINV = 2 };
+
+// Instantiations by block size; the minimum-blocks bound caps registers at 64
+// per thread so that several blocks of the smaller size classes share an SM.
+void* kernel_for(KernKind kk, int warps) {
+  if (warps <= 4) return Kern<128, 8>::get(kk);
+  if (warps <= 8) return Kern<256, 4>::get(kk);
+  if (warps <= 16) return Kern<512, 2>::get(kk);
+  return Kern<1024, 1>::get(kk);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ context helpers
+int mpdiv_set_error(mpdiv_ctx* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    std::lock_guard<std::mutex> g(ctx->err_mu);
+    ctx->err = buf;
+  }
+  return code;
+}
+
+int mpdiv_cuda_check(mpdiv_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MPDIV_OK;
+  return mpdiv_set_error(ctx, MPDIV_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int mpdiv_smem_bytes(int max_digits) { return (smem_words_for(max_digits) * 4 + 15) & ~15; }
+
+int mpdiv_default_warps(mpdiv_ctx* ctx, int max_digits) {
+  if (ctx->cfg.warps_per_block > 0) return ctx->cfg.warps_per_block;
+  {
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    const int cls = mpdiv_size_class(max_digits);
+    auto it = ctx->tuned.find(cls);
+    if (it != ctx->tuned.end()) return it->second;
+  }
+  if (max_digits <= 1536) return 8;
+  if (max_digits <= 3072) return 8;
+  return 16;
+}
+
+int mpdiv_size_class(int digits) {
+  int c = 1024;
+  while (c < digits) c *= 2;
+  return c;
+}
+
+static int prepare_kernel(mpdiv_ctx* ctx, void* k, int smem) {
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return mpdiv_cuda_check(ctx, e, "cudaFuncSetAttribute(max dynamic shared memory)");
+}
+
+// ------------------------------------------------------------------ init / destroy
+extern "C" int mpdiv_init(mpdiv_ctx** out, int device, const mpdiv_config* cfg) {
+  if (!out) return MPDIV_EINVAL;
+  *out = nullptr;
+  mpdiv_ctx* ctx = new mpdiv_ctx();
+  ctx->device = device;
+  if (cfg) ctx->cfg = *cfg;
+  int rc;
+  if ((rc = mpdiv_cuda_check(ctx, cudaSetDevice(device), "cudaSetDevice")) != MPDIV_OK) {
+    delete ctx;
+    return rc;
+  }
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&ctx->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&ctx->d_head, 64), "cudaMalloc(queue head)")) != MPDIV_OK) {
+    delete ctx;
+    return rc;
+  }
+  if ((rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking),
+                             "cudaStreamCreate")) != MPDIV_OK) {
+    cudaFree(ctx->d_head);
+    delete ctx;
+    return rc;
+  }
+  const char* tf = getenv("MPDIV_TUNE_FILE");
+  if (tf) mpdiv_tune_load(ctx, tf);
+  *out = ctx;
+  return MPDIV_OK;
+}
+
+extern "C" void mpdiv_destroy(mpdiv_ctx* ctx) {
+  if (!ctx) return;
+  mpdiv_serve_shutdown(ctx);
+  cudaSetDevice(ctx->device);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->d_order) cudaFree(ctx->d_order);
+  if (ctx->d_head) cudaFree(ctx->d_head);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  delete ctx;
+}
+
+extern "C" const char* mpdiv_last_error(const mpdiv_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+// ------------------------------------------------------------------ plain batch
+int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t stream) {
+  const int max_digits = L.un;
+  const int smem = mpdiv_smem_bytes(max_digits);
+  if (smem > ctx->max_smem)
+    return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory, device allows %d", smem,
+                           ctx->max_smem);
+  const int warps = L.warps > 0 ? L.warps : mpdiv_default_warps(ctx, max_digits);
+  void* k = kernel_for(KK_UNIFORM, warps);
+  int rc = prepare_kernel(ctx, k, smem);
+  if (rc) return rc;
+  UniformArgs a;
+  a.u = L.u;
+  a.v = L.v;
+  a.q = L.q;
+  a.r = L.r;
+  a.status = L.status;
+  a.iters = L.iters;
+  a.n = L.n;
+  a.us = L.us;
+  a.vs = L.vs;
+  a.qs = L.qs;
+  a.rs = L.rs;
+  a.un = L.un;
+  a.vn = L.vn;
+  a.qn = L.qn;
+  a.rn = L.rn;
+  a.smem_words = smem / 4;
+  a.flags = ctx->cfg.flags;
+  const int64_t grid = std::min<int64_t>(L.n, 0x7fffffff);
+  void* args[] = {&a};
+  cudaError_t e = cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * warps), args, smem, stream);
+  return mpdiv_cuda_check(ctx, e, "launch of the division kernel");
+}
+
+extern "C" int mpdiv_batch(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* u, int32_t u_limbs, int64_t u_stride,
+                           const uint32_t* v, int32_t v_limbs, int64_t v_stride, uint32_t* q, int32_t q_limbs,
+                           int64_t q_stride, uint32_t* r, int32_t r_limbs, int64_t r_stride, int32_t* status,
+                           int32_t* iters, void* stream) {
+  if (!ctx) return MPDIV_EINVAL;
+  if (n_items < 0) return mpdiv_set_error(ctx, MPDIV_EINVAL, "n_items < 0");
+  if (n_items == 0) return MPDIV_OK;
+  if (!u || !v || !q || !r || !status) return mpdiv_set_error(ctx, MPDIV_EINVAL, "null pointer argument");
+  if (u_limbs < 1 || v_limbs < 1 || q_limbs < 1 || r_limbs < 1)
+    return mpdiv_set_error(ctx, MPDIV_EINVAL, "digit counts must be positive");
+  if (u_limbs > MPDIV_MAX_LIMBS || v_limbs > MPDIV_MAX_LIMBS)
+    return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "at most %d digits per operand", MPDIV_MAX_LIMBS);
+  if (r_limbs < v_limbs) return mpdiv_set_error(ctx, MPDIV_EINVAL, "r_limbs < v_limbs");
+  if (u_stride < u_limbs || v_stride < v_limbs || q_stride < q_limbs || r_stride < r_limbs)
+    return mpdiv_set_error(ctx, MPDIV_EINVAL, "a stride is shorter than its digit count");
+  cudaSetDevice(ctx->device);
+  UniformLaunch L{};
+  L.u = u;
+  L.v = v;
+  L.q = q;
+  L.r = r;
+  L.status = status;
+  L.iters = iters;
+  L.n = n_items;
+  L.us = u_stride;
+  L.vs = v_stride;
+  L.qs = q_stride;
+  L.rs = r_stride;
+  L.un = u_limbs;
+  L.vn = v_limbs;
+  L.qn = q_limbs;
+  L.rn = r_limbs;
+  L.warps = 0;
+  return mpdiv_launch_uniform(ctx, L, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ ragged (persistent) batch
+// Cost estimate used to order the queue (largest first): limb products of the
+// quotient and remainder products plus the Newton refinement, from the
+// multiplication-count model of Section 2.3.
+static double item_cost(int n, int kl) {
+  if (kl > n) return 1.0;
+  const double a = n - kl + 1;
+  const double newton = 2.0 * a * std::min<double>(kl, a);
+  return a * n + a * kl + newton + 64.0;
+}
+
+int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stream) {
+  int max_u = 1;
+  for (int64_t i = 0; i < L.n; i++) max_u = std::max(max_u, (int)L.u_len_host[i]);
+  const int smem = mpdiv_smem_bytes(max_u);
+  if (smem > ctx->max_smem)
+    return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory", smem);
+  const int warps = L.warps > 0 ? L.warps : mpdiv_default_warps(ctx, max_u);
+  void* k = kernel_for(KK_RAGGED, warps);
+  int rc = prepare_kernel(ctx, k, smem);
+  if (rc) return rc;
+  // size-sorted order (cached by content of the shape list)
+  uint64_t hsh = 1469598103934665603ull;
+  for (int64_t i = 0; L.order == nullptr && i < L.n; i++) {
+    hsh = (hsh ^ (uint64_t)(uint32_t)L.u_len_host[i]) * 1099511628211ull;
+    hsh = (hsh ^ (uint64_t)(uint32_t)L.v_len_host[i]) * 1099511628211ull;
+  }
+  std::lock_guard<std::mutex> g(ctx->ragged_mu);
+  const bool same_shapes = L.order != nullptr || (hsh == ctx->order_hash && L.n == ctx->order_n);
+  if (!same_shapes) {
+    std::vector<int32_t> order(L.n);
+    std::iota(order.begin(), order.end(), 0);
+    std::vector<double> cost(L.n);
+    for (int64_t i = 0; i < L.n; i++) cost[i] = item_cost(L.u_len_host[i], L.v_len_host[i]);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    if ((size_t)L.n > ctx->order_cap) {
+      if (ctx->d_order) cudaFree(ctx->d_order);
+      ctx->d_order = nullptr;
+      ctx->order_cap = 0;
+      if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&ctx->d_order, sizeof(int32_t) * L.n), "cudaMalloc(order)")))
+        return rc;
+      ctx->order_cap = L.n;
+    }
+    if ((rc = mpdiv_cuda_check(
+             ctx, cudaMemcpy(ctx->d_order, order.data(), sizeof(int32_t) * L.n, cudaMemcpyHostToDevice),
+             "upload of the queue order")))
+      return rc;
+    ctx->order_hash = hsh;
+    ctx->order_n = L.n;
+  }
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 32 * warps, smem);
+  if (occ < 1) return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "kernel does not fit on an SM");
+  if (ctx->cfg.blocks_per_sm > 0) occ = std::min(occ, ctx->cfg.blocks_per_sm);
+  int64_t grid = (int64_t)ctx->num_sms * occ;
+  if (L.grid_items) grid = L.n;  // one block per item: later launches backfill freed SMs
+  grid = std::max<int64_t>(1, std::min<int64_t>(grid, std::min<int64_t>(L.n, 0x7fffffff)));
+  RaggedArgs a;
+  std::memset(&a, 0, sizeof a);  // the graph cache compares argument blocks bytewise
+  a.u = L.u;
+  a.u_off = L.u_off;
+  a.u_len = L.u_len;
+  a.v = L.v;
+  a.v_off = L.v_off;
+  a.v_len = L.v_len;
+  a.q = L.q;
+  a.q_off = L.q_off;
+  a.q_len = L.q_len;
+  a.r = L.r;
+  a.r_off = L.r_off;
+  a.r_len = L.r_len;
+  a.status = L.status;
+  a.iters = L.iters;
+  a.order = L.order ? L.order : ctx->d_order;
+  a.head = L.head ? L.head : ctx->d_head;
+  a.n = L.n;
+  a.smem_words = smem / 4;
+  a.flags = ctx->cfg.flags;
+  if (!L.use_graph) {
+    if ((rc = mpdiv_cuda_check(ctx, cudaMemsetAsync(a.head, 0, sizeof(int32_t), stream), "queue reset"))) return rc;
+    void* args[] = {&a};
+    return mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * warps), args, smem, stream),
+                            "launch of the persistent division kernel");
+  }
+  // CUDA graph: [reset queue head, persistent kernel], replayed while the
+  // arguments are unchanged.
+  const bool same_args = ctx->gexec && same_shapes && std::memcmp(&a, &ctx->g_args, sizeof a) == 0 &&
+                         ctx->g_grid == grid && ctx->g_warps == warps && ctx->g_smem == smem;
+  if (!same_args) {
+    if (ctx->gexec) {
+      cudaGraphExecDestroy(ctx->gexec);
+      ctx->gexec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    if ((rc = mpdiv_cuda_check(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal),
+                               "begin graph capture")))
+      return rc;
+    cudaMemsetAsync(a.head, 0, sizeof(int32_t), ctx->cap_stream);
+    void* args[] = {&a};
+    cudaError_t le = cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * warps), args, smem, ctx->cap_stream);
+    cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if ((rc = mpdiv_cuda_check(ctx, le, "captured launch"))) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if ((rc = mpdiv_cuda_check(ctx, ee, "end graph capture"))) return rc;
+    cudaError_t ie = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if ((rc = mpdiv_cuda_check(ctx, ie, "graph instantiate"))) {
+      ctx->gexec = nullptr;
+      return rc;
+    }
+    ctx->g_args = a;
+    ctx->g_grid = grid;
+    ctx->g_warps = warps;
+    ctx->g_smem = smem;
+    ctx->graph_captures++;
+  } else {
+    ctx->graph_replays++;
+  }
+  return mpdiv_cuda_check(ctx, cudaGraphLaunch(ctx->gexec, stream), "graph launch");
+}
+
+extern "C" int mpdiv_batch_ragged(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* u, const int64_t* u_off,
+                                  const int32_t* u_len, const uint32_t* v, const int64_t* v_off,
+                                  const int32_t* v_len, uint32_t* q, const int64_t* q_off, const int32_t* q_len,
+                                  uint32_t* r, const int64_t* r_off, const int32_t* r_len, int32_t* status,
+                                  int32_t* iters, const int32_t* u_len_host, const int32_t* v_len_host,
+                                  void* stream) {
+  if (!ctx) return MPDIV_EINVAL;
+  if (n_items < 0) return mpdiv_set_error(ctx, MPDIV_EINVAL, "n_items < 0");
+  if (n_items == 0) return MPDIV_OK;
+  if (!u || !u_off || !u_len || !v || !v_off || !v_len || !q || !q_off || !q_len || !r || !r_off || !r_len ||
+      !status || !u_len_host || !v_len_host)
+    return mpdiv_set_error(ctx, MPDIV_EINVAL, "null pointer argument");
+  for (int64_t i = 0; i < n_items; i++) {
+    if (u_len_host[i] < 1 || v_len_host[i] < 1)
+      return mpdiv_set_error(ctx, MPDIV_EINVAL, "item %lld: digit counts must be positive", (long long)i);
+    if (u_len_host[i] > MPDIV_MAX_LIMBS || v_len_host[i] > MPDIV_MAX_LIMBS)
+      return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "item %lld: at most %d digits", (long long)i,
+                             MPDIV_MAX_LIMBS);
+  }
+  cudaSetDevice(ctx->device);
+  RaggedLaunch L{};
+  L.u = u;
+  L.u_off = u_off;
+  L.u_len = u_len;
+  L.v = v;
+  L.v_off = v_off;
+  L.v_len = v_len;
+  L.q = q;
+  L.q_off = q_off;
+  L.q_len = q_len;
+  L.r = r;
+  L.r_off = r_off;
+  L.r_len = r_len;
+  L.status = status;
+  L.iters = iters;
+  L.u_len_host = u_len_host;
+  L.v_len_host = v_len_host;
+  L.n = n_items;
+  L.use_graph = true;
+  return mpdiv_launch_ragged(ctx, L, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ shinv test entry
+extern "C" int mpdiv_debug_shinv(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* v, int32_t v_limbs,
+                                 int64_t v_stride, const int32_t* h_digits, uint32_t* out, int32_t out_limbs,
+                                 int64_t out_stride, int32_t* iters, int32_t* status, void* stream) {
+  if (!ctx) return MPDIV_EINVAL;
+  if (n_items <= 0) return n_items == 0 ? MPDIV_OK : mpdiv_set_error(ctx, MPDIV_EINVAL, "n_items < 0");
+  if (!v || !h_digits || !out || !status) return mpdiv_set_error(ctx, MPDIV_EINVAL, "null pointer argument");
+  if (v_limbs < 1 || out_limbs < 1 || v_stride < v_limbs || out_stride < out_limbs)
+    return mpdiv_set_error(ctx, MPDIV_EINVAL, "bad sizes");
+  if (v_limbs > MPDIV_MAX_LIMBS || out_limbs > MPDIV_MAX_LIMBS + 1)
+    return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "too many digits");
+  cudaSetDevice(ctx->device);
+  const int max_h = MPDIV_MAX_LIMBS;  // h_digits live on the device: size for the largest
+  const int smem = mpdiv_smem_bytes(max_h);
+  const int warps = ctx->cfg.warps_per_block > 0 ? ctx->cfg.warps_per_block : 16;
+  void* k = kernel_for(KK_SHINV, warps);
+  int rc = prepare_kernel(ctx, k, smem);
+  if (rc) return rc;
+  ShinvArgs a;
+  a.v = v;
+  a.h = h_digits;
+  a.out = out;
+  a.iters = iters;
+  a.status = status;
+  a.n = n_items;
+  a.vs = v_stride;
+  a.os = out_stride;
+  a.vn = v_limbs;
+  a.on = out_limbs;
+  a.smem_words = smem / 4;
+  void* args[] = {&a};
+  const int64_t grid = std::min<int64_t>(n_items, 0x7fffffff);
+  return mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * warps), args, smem,
+                                                (cudaStream_t)stream),
+                          "launch of the shifted-inverse kernel");
+}

@@ -1,0 +1,84 @@
+// Internal state and launch descriptors shared by the host-side sources.
+#pragma once
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "mp_args.h"
+#include "mpdiv.h"
+
+struct MpServer;  // mpdiv_serve.cu
+
+struct mpdiv_ctx {
+  int device = 0;
+  int num_sms = 0;
+  int max_smem = 0;
+  mpdiv_config cfg{0, 0, 0};
+  mutable std::mutex err_mu;
+  std::string err;
+  // tuning table: size class (digits, power of two >= 1024) -> warps per block
+  std::mutex tune_mu;
+  std::map<int, int> tuned;
+  // persistent launch: queue head, cached order, cached graph
+  std::mutex ragged_mu;
+  int32_t* d_head = nullptr;
+  int32_t* d_order = nullptr;
+  size_t order_cap = 0;
+  uint64_t order_hash = 0;
+  int64_t order_n = -1;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  mp::RaggedArgs g_args{};
+  int64_t g_grid = 0;
+  int g_warps = 0, g_smem = 0;
+  int64_t graph_captures = 0, graph_replays = 0;
+  // serving
+  MpServer* server = nullptr;
+};
+
+struct UniformLaunch {
+  const uint32_t *u, *v;
+  uint32_t *q, *r;
+  int32_t *status, *iters;
+  int64_t n, us, vs, qs, rs;
+  int un, vn, qn, rn;
+  int warps;  // 0: from the tuning table
+};
+
+struct RaggedLaunch {
+  const uint32_t* u;
+  const int64_t* u_off;
+  const int32_t* u_len;
+  const uint32_t* v;
+  const int64_t* v_off;
+  const int32_t* v_len;
+  uint32_t* q;
+  const int64_t* q_off;
+  const int32_t* q_len;
+  uint32_t* r;
+  const int64_t* r_off;
+  const int32_t* r_len;
+  int32_t *status, *iters;
+  const int32_t *u_len_host, *v_len_host;
+  const int32_t* order;  // device order array (nullptr: computed and cached here)
+  int32_t* head;         // device queue head (nullptr: the context's)
+  int64_t n;
+  int warps;       // 0: from the tuning table
+  bool use_graph;  // capture/replay as a CUDA graph
+  bool grid_items; // one block per item instead of one wave of resident blocks
+};
+
+int mpdiv_set_error(mpdiv_ctx* ctx, int code, const char* fmt, ...);
+int mpdiv_cuda_check(mpdiv_ctx* ctx, cudaError_t e, const char* what);
+int mpdiv_smem_bytes(int max_digits);
+int mpdiv_size_class(int digits);
+int mpdiv_default_warps(mpdiv_ctx* ctx, int max_digits);
+int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t stream);
+int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stream);
+void mpdiv_tune_load(mpdiv_ctx* ctx, const char* path);
+void mpdiv_serve_shutdown(mpdiv_ctx* ctx);

@@ -1,0 +1,120 @@
+// Block-size tuner for the division kernels (Section 5 of arXiv 2606.06386
+// names autotuning of block size and sequentialisation as future work): for a
+// size class it times the plain kernel at each candidate warps-per-block on
+// synthetic divisions and records the fastest in the context's table, which
+// can be saved to and loaded from a text file (MPDIV_TUNE_FILE).
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "mpdiv_internal.h"
+
+namespace {
+
+// splitmix64 finaliser on a counter: synthetic digits for timing only
+__global__ void k_fill(uint32_t* x, int64_t n_items, int digits, int64_t stride, uint64_t seed) {
+  const int64_t total = n_items * (int64_t)digits;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + (uint64_t)(t + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const int64_t item = t / digits;
+    const int d = (int)(t - item * digits);
+    uint32_t val = (uint32_t)z;
+    if (d == digits - 1 && val == 0u) val = 1u;
+    x[item * stride + d] = val;
+  }
+}
+
+}  // namespace
+
+void mpdiv_tune_load(mpdiv_ctx* ctx, const char* path) {
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  int cls, w;
+  std::lock_guard<std::mutex> g(ctx->tune_mu);
+  while (fscanf(f, "%d %d", &cls, &w) == 2)
+    if (cls > 0 && w > 0 && w <= 32) ctx->tuned[cls] = w;
+  fclose(f);
+}
+
+static void tune_save(mpdiv_ctx* ctx, const char* path) {
+  FILE* f = fopen(path, "w");
+  if (!f) return;
+  std::lock_guard<std::mutex> g(ctx->tune_mu);
+  for (auto& kv : ctx->tuned) fprintf(f, "%d %d\n", kv.first, kv.second);
+  fclose(f);
+}
+
+extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, int32_t n_items) {
+  if (!ctx) return MPDIV_EINVAL;
+  if (u_limbs < 1 || v_limbs < 1 || v_limbs > u_limbs || n_items < 1)
+    return mpdiv_set_error(ctx, MPDIV_EINVAL, "autotune: bad shape");
+  if (u_limbs > MPDIV_MAX_LIMBS) return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "autotune: too many digits");
+  cudaSetDevice(ctx->device);
+  uint32_t *u = nullptr, *v = nullptr, *q = nullptr, *r = nullptr;
+  int32_t* st = nullptr;
+  const size_t n = (size_t)n_items;
+  int rc = MPDIV_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int best_w = 0;
+  float best_ms = 1e30f;
+  if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&u, n * u_limbs * 4), "autotune alloc"))) goto done;
+  if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&v, n * v_limbs * 4), "autotune alloc"))) goto done;
+  if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&q, n * u_limbs * 4), "autotune alloc"))) goto done;
+  if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&r, n * v_limbs * 4), "autotune alloc"))) goto done;
+  if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&st, n * 4), "autotune alloc"))) goto done;
+  k_fill<<<256, 256>>>(u, n_items, u_limbs, u_limbs, 0x1234567ull);
+  k_fill<<<256, 256>>>(v, n_items, v_limbs, v_limbs, 0x7654321ull);
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int w : {4, 8, 16, 32}) {
+    UniformLaunch L{};
+    L.u = u;
+    L.v = v;
+    L.q = q;
+    L.r = r;
+    L.status = st;
+    L.iters = nullptr;
+    L.n = n_items;
+    L.us = L.qs = u_limbs;
+    L.vs = L.rs = v_limbs;
+    L.un = u_limbs;
+    L.vn = v_limbs;
+    L.qn = u_limbs;
+    L.rn = v_limbs;
+    L.warps = w;
+    if (mpdiv_launch_uniform(ctx, L, 0) != MPDIV_OK) continue;  // e.g. does not fit
+    cudaEventRecord(e0, 0);
+    mpdiv_launch_uniform(ctx, L, 0);
+    mpdiv_launch_uniform(ctx, L, 0);
+    cudaEventRecord(e1, 0);
+    if ((rc = mpdiv_cuda_check(ctx, cudaEventSynchronize(e1), "autotune timing"))) goto done;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_w = w;
+    }
+  }
+  if (best_w == 0) {
+    rc = mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "autotune: no candidate block size ran");
+    goto done;
+  }
+  {
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    ctx->tuned[mpdiv_size_class(u_limbs)] = best_w;
+  }
+  if (const char* tf = getenv("MPDIV_TUNE_FILE")) tune_save(ctx, tf);
+  rc = best_w;
+done:
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(u);
+  cudaFree(v);
+  cudaFree(q);
+  cudaFree(r);
+  cudaFree(st);
+  return rc;
+}

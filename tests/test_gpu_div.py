@@ -1,0 +1,99 @@
+"""Parity of the CUDA division path with the CPU oracle (bit-exact), through the C ABI."""
+
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.shinv_model as M
+from paper_2606_06386_gb300 import inputs as I
+
+from gpu_util import assert_same, dev, host_u32, oracle_uniform, run_uniform, ctx
+
+pytestmark = pytest.mark.gpu
+B = 1 << 32
+
+
+def test_plain_1024_with_edge_cases():
+    # 256 uniform (u: 1024 digits, v: 512 digits) + 16 seeded edge cases
+    U, V, names = I.plain_1024()
+    Q, R, S, it = run_uniform(U, V)
+    Qo, Ro, So = oracle_uniform(U, V)
+    assert_same(Q, R, S, Qo, Ro, So, names)
+    # Newton iteration count = ceil(log2(h-k-1)) + 2 on the uniform items (h = 1024, k = 511)
+    assert (it[:256] == M.refine_iterations(1024, 511)).all()
+
+
+@pytest.mark.parametrize(
+    "n,kl",
+    [(1, 1), (2, 1), (2, 2), (3, 2), (5, 3), (8, 3), (40, 17), (97, 96), (230, 100), (300, 150), (333, 1),
+     (512, 511), (700, 2), (1000, 999), (1500, 3)],
+)
+def test_small_and_ragged_shapes(n, kl):
+    U = I.uniform_batch(24, n, seed=1000 + n, stream=kl)
+    V = I.uniform_batch(24, kl, seed=2000 + n, stream=kl)
+    Q, R, S, _ = run_uniform(U, V)
+    Qo, Ro, So = oracle_uniform(U, V)
+    assert_same(Q, R, S, Qo, Ro, So)
+
+
+def test_full_size_2e18_bits():
+    # 2^18-bit dividends, 2^17-bit divisors: every item against the oracle
+    U, V = I.sweep(8192, 4096, 48)
+    Q, R, S, it = run_uniform(U, V, qn=4097, rn=4096)
+    Qo, Ro, So = oracle_uniform(U, V, 4097, 4096)
+    assert_same(Q, R, S, Qo, Ro, So)
+    assert (it == M.refine_iterations(8192, 4095)).all()
+
+
+def test_special_values():
+    n, kl = 64, 32
+    rnd = random.Random(9)
+    cases = []
+    for u, v in [
+        (0, 5), (0, 1), (7, 0), (123, 456), (rnd.getrandbits(32 * n), 1), (rnd.getrandbits(32 * n), 2),
+        (rnd.getrandbits(32 * n), B - 1), (rnd.getrandbits(32 * n), B**31), (rnd.getrandbits(32 * n), B**31 + 1),
+        (B**n - 1, B**kl - 1), (B**(n - 1), B**(kl - 1)), (B**kl - 1, B**kl - 1), (B**kl - 2, B**kl - 1),
+        ((B**kl - 1) * (B**kl - 1), B**kl - 1), (B**32 * 3, (B**32) // 2 + 1), (B**32 - 1, B**31 * 2**31),
+        (rnd.getrandbits(32 * n), 1 << (32 * kl - 1)), (rnd.getrandbits(32 * n), (1 << (32 * kl - 1)) + 1),
+    ]:
+        cases.append((u, v))
+    U = np.stack([oracle.from_int(u, n) for u, _ in cases])
+    V = np.stack([oracle.from_int(v, kl) for _, v in cases])
+    Q, R, S, _ = run_uniform(U, V)
+    Qo, Ro, So = oracle_uniform(U, V)
+    assert_same(Q, R, S, Qo, Ro, So)
+    assert S[2] == 1  # v == 0
+
+
+def test_shinv_equals_model_and_theorem2():
+    import torch
+    import paper_2606_06386_gb300 as mp
+
+    rnd = random.Random(31)
+    vs, hs = [], []
+    for _ in range(60):
+        kl = rnd.randint(2, 40)
+        v = rnd.getrandbits(32 * kl) | (1 << (32 * kl - 1 - rnd.randint(0, 31)))
+        h = rnd.randint(kl, 90)
+        vs.append(v)
+        hs.append(h)
+    V = np.stack([oracle.from_int(v, 40) for v in vs])
+    out = torch.zeros((len(vs), 100), dtype=torch.int32, device="cuda:0")
+    it = torch.zeros(len(vs), dtype=torch.int32, device="cuda:0")
+    st = torch.full((len(vs),), -1, dtype=torch.int32, device="cuda:0")
+    h_t = torch.tensor(hs, dtype=torch.int32, device="cuda:0")
+    mp.mpdiv_debug_shinv(ctx(), dev(V), h_t, out, it, st)
+    torch.cuda.synchronize()
+    O = host_u32(out)
+    S = st.cpu().numpy()
+    I_ = it.cpu().numpy()
+    for i, (v, h) in enumerate(zip(vs, hs)):
+        assert S[i] == 0
+        tr = M.Trace()
+        s_model = M.shinv(v, h, B, tr)
+        s_gpu = oracle.to_int(O[i])
+        assert s_gpu == s_model, (i, v, h)
+        assert s_gpu - B**h // v in (0, 1)
+        assert I_[i] == tr.iterations
