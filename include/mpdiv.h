@@ -81,6 +81,10 @@ const char *mpdiv_last_error(const mpdiv_ctx *ctx);
  * (v_limbs digits), writes q + i*q_stride (q_limbs digits, zero-padded),
  * r + i*r_stride (r_limbs digits, zero-padded) and status[i]. iters may be NULL;
  * otherwise iters[i] gets the number of Newton (Refine) iterations run.
+ * products may be NULL; otherwise products[i] gets the digit products of the
+ * multiplications of Algorithms 1-3 for item i at their operand precisions
+ * (a close product modulo B^L counts only the digit pairs below L): the unit
+ * of the paper's multiplication cost model (Section 2.3).
  * Strides are in digits. All pointers are device pointers.
  * Errors: MPDIV_EINVAL (null pointer, non-positive size, r_limbs < v_limbs,
  * stride shorter than the digit count), MPDIV_EUNSUPPORTED (more than
@@ -88,13 +92,13 @@ const char *mpdiv_last_error(const mpdiv_ctx *ctx);
 int mpdiv_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, int32_t u_limbs, int64_t u_stride,
                 const uint32_t *v, int32_t v_limbs, int64_t v_stride, uint32_t *q, int32_t q_limbs,
                 int64_t q_stride, uint32_t *r, int32_t r_limbs, int64_t r_stride, int32_t *status, int32_t *iters,
-                void *stream);
+                int64_t *products, void *stream);
 
 /* Ragged batch of mixed precisions in one persistent launch: items are taken
  * largest-first from a size-sorted queue by resident blocks. Item i reads
  * u + u_off[i] (u_len[i] digits), v + v_off[i] (v_len[i] digits) and writes
  * q + q_off[i] (q_len[i] digits), r + r_off[i] (r_len[i] digits), status[i],
- * iters[i] (iters may be NULL). Offsets are in digits. u_off..r_len and status
+ * iters[i] and products[i] (each may be NULL). Offsets are in digits. u_off..r_len and status
  * are device arrays; the host-side copies of u_len and v_len (u_len_host,
  * v_len_host, n_items entries each) are used to size and order the work.
  * Requirements as for mpdiv_batch, per item (r_len[i] >= v_len[i]).
@@ -103,8 +107,8 @@ int mpdiv_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, int32_t u_li
 int mpdiv_batch_ragged(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, const int64_t *u_off,
                        const int32_t *u_len, const uint32_t *v, const int64_t *v_off, const int32_t *v_len,
                        uint32_t *q, const int64_t *q_off, const int32_t *q_len, uint32_t *r, const int64_t *r_off,
-                       const int32_t *r_len, int32_t *status, int32_t *iters, const int32_t *u_len_host,
-                       const int32_t *v_len_host, void *stream);
+                       const int32_t *r_len, int32_t *status, int32_t *iters, int64_t *products,
+                       const int32_t *u_len_host, const int32_t *v_len_host, void *stream);
 
 /* Test entry: the shifted inverse of Algorithm 1 for each item, as the
  * division path computes it: out + i*out_stride gets shinv_h(v_i) (out_limbs

@@ -66,9 +66,23 @@ class Trace:
     products: list = field(default_factory=list)  # (tag, prec a, prec b)
     iterates: list = field(default_factory=list)  # w after each Refine step
 
-    def mult(self, tag: str, a: int, b: int, B: int) -> int:
-        self.products.append((tag, prec(a, B), prec(b, B)))
+    def mult(self, tag: str, a: int, b: int, B: int, keep: int | None = None) -> int:
+        """Record a product of prec(a) x prec(b) digits; ``keep`` is the number of
+        low digits a close product (MultMod) keeps."""
+        self.products.append((tag, prec(a, B), prec(b, B), keep))
         return a * b
+
+    def digit_products(self) -> int:
+        """Digit products of the multiplications made: a full product of m x n
+        digits costs m n; one kept modulo B^L costs the pairs (i, j) with
+        i + j < L."""
+        total = 0
+        for _, m, n, keep in self.products:
+            if keep is None or keep >= m + n - 1:
+                total += m * n
+            else:
+                total += sum(max(0, min(n, keep - i)) for i in range(m))
+        return total
 
 
 def powdiff(v: int, w: int, h: int, ell: int, B: int, tr: Trace) -> tuple[int, int]:
@@ -80,7 +94,7 @@ def powdiff(v: int, w: int, h: int, ell: int, B: int, tr: Trace) -> tuple[int, i
             return 1, B**h - P
         return 0, P - B**h
     # MultMod: the product kept modulo B^L (the close product)
-    P = tr.mult("powdiff_mod", v, w, B) % B**L
+    P = tr.mult("powdiff_mod", v, w, B, keep=L) % B**L
     if P == 0:
         return 1, 0
     if (P // B ** (L - 1)) % B == 0:

@@ -93,8 +93,8 @@ _SIGS = {
     "mpdiv_init": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(mpdiv_config)]),
     "mpdiv_destroy": (None, [_P]),
     "mpdiv_last_error": (ctypes.c_char_p, [_P]),
-    "mpdiv_batch": (ctypes.c_int, [_P, _I64, _P, _I32, _I64, _P, _I32, _I64, _P, _I32, _I64, _P, _I32, _I64, _P, _P, _P]),
-    "mpdiv_batch_ragged": (ctypes.c_int, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "mpdiv_batch": (ctypes.c_int, [_P, _I64, _P, _I32, _I64, _P, _I32, _I64, _P, _I32, _I64, _P, _I32, _I64, _P, _P, _P, _P]),
+    "mpdiv_batch_ragged": (ctypes.c_int, [_P, _I64] + [_P] * 18),
     "mpdiv_debug_shinv": (ctypes.c_int, [_P, _I64, _P, _I32, _I64, _P, _P, _I32, _I64, _P, _P, _P]),
     "mpdiv_autotune": (ctypes.c_int, [_P, _I32, _I32, _I32]),
     "mpdiv_serve_start": (ctypes.c_int, [_P, ctypes.POINTER(mpdiv_serve_config)]),
@@ -179,25 +179,26 @@ def mpdiv_last_error(ctx) -> str:
     return lib().mpdiv_last_error(ctx).decode()
 
 
-def mpdiv_batch(ctx, u, v, q, r, status, iters=None, stream=None) -> None:
+def mpdiv_batch(ctx, u, v, q, r, status, iters=None, products=None, stream=None) -> None:
     """Uniform batch: u (items, u_limbs), v (items, v_limbs), q (items, q_limbs),
-    r (items, r_limbs) uint32/int32 CUDA tensors; status (and iters) int32 (items,)."""
-    _check_dev(u, v, q, r, status, iters)
+    r (items, r_limbs) uint32/int32 CUDA tensors; status (and iters) int32 (items,);
+    products int64 (items,)."""
+    _check_dev(u, v, q, r, status, iters, products)
     n = u.shape[0]
     _check(
         ctx,
         lib().mpdiv_batch(
             ctx, n, _ptr(u), u.shape[1], u.stride(0), _ptr(v), v.shape[1], v.stride(0), _ptr(q), q.shape[1],
-            q.stride(0), _ptr(r), r.shape[1], r.stride(0), _ptr(status), _ptr(iters), _stream(stream),
+            q.stride(0), _ptr(r), r.shape[1], r.stride(0), _ptr(status), _ptr(iters), _ptr(products), _stream(stream),
         ),
     )
 
 
 def mpdiv_batch_ragged(ctx, u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r, r_off, r_len, status,
-                       iters=None, u_len_host=None, v_len_host=None, stream=None) -> None:
+                       iters=None, products=None, u_len_host=None, v_len_host=None, stream=None) -> None:
     """Ragged batch over flat digit tensors with per-item int64 offsets and int32
     lengths (CUDA tensors); u_len_host / v_len_host are CPU int32 tensors."""
-    _check_dev(u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r, r_off, r_len, status, iters)
+    _check_dev(u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r, r_off, r_len, status, iters, products)
     if u_len_host is None:
         u_len_host = u_len.cpu()
     if v_len_host is None:
@@ -209,7 +210,7 @@ def mpdiv_batch_ragged(ctx, u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r
         ctx,
         lib().mpdiv_batch_ragged(
             ctx, n, _ptr(u), _ptr(u_off), _ptr(u_len), _ptr(v), _ptr(v_off), _ptr(v_len), _ptr(q), _ptr(q_off),
-            _ptr(q_len), _ptr(r), _ptr(r_off), _ptr(r_len), _ptr(status), _ptr(iters), _ptr(u_len_host),
+            _ptr(q_len), _ptr(r), _ptr(r_off), _ptr(r_len), _ptr(status), _ptr(iters), _ptr(products), _ptr(u_len_host),
             _ptr(v_len_host), _stream(stream),
         ),
     )

@@ -11,6 +11,7 @@ struct UniformArgs {
   uint32_t* r;
   int32_t* status;
   int32_t* iters;
+  int64_t* products;  // per item: algorithmic digit products (may be null)
   int64_t n, us, vs, qs, rs;
   int un, vn, qn, rn;
   int smem_words;
@@ -32,6 +33,7 @@ struct RaggedArgs {
   const int32_t* r_len;
   int32_t* status;
   int32_t* iters;
+  int64_t* products;
   const int32_t* order;  // item indices, most expensive first
   int32_t* head;         // queue head, zero at launch
   int64_t n;

@@ -44,6 +44,7 @@ struct Blk {
   int tid, lane, warp, nw, nt;
   int bar;   // named barrier id (0: the whole block)
   int* red;  // RED_WORDS ints of shared scratch owned by this group
+  unsigned long long* work;  // thread 0's running count of algorithmic digit products (may be null)
 
   __device__ __forceinline__ void sync() const {
     asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
@@ -60,6 +61,7 @@ __device__ __forceinline__ Blk make_group(int* red, int w0, int nw, int bar) {
   b.nt = 32 * nw;
   b.bar = bar;
   b.red = red;
+  b.work = nullptr;
   return b;
 }
 
@@ -319,6 +321,17 @@ __device__ __forceinline__ void mul_strip(const Blk& b, uint32_t* C, int npos, c
   OV[2 * s + 1] = o[T + 1];
 }
 
+// Digit pairs (i, j) with i < na, j < nb and i + j < npos: the digit products
+// of a product kept modulo B^npos (all na nb of them for a full product).
+__device__ __forceinline__ unsigned long long pair_count(int na, int nb, int npos) {
+  if (na <= 0 || nb <= 0 || npos <= 0) return 0ull;
+  const long long c1 = max(0, min(na, npos - nb + 1));
+  unsigned long long s = (unsigned long long)c1 * nb;
+  const long long a = c1, e = min(na, npos);
+  if (e > a) s += (unsigned long long)((e - a) * npos - (a + e - 1) * (e - a) / 2);
+  return s;
+}
+
 // C[0..npos) = (X * Y) mod B^npos. X (nx digits) and Y (ny digits) are
 // multiply operands: PAD zero digits must be addressable below index 0 and
 // above the digit count (the high pads are zeroed here). OV needs
@@ -333,6 +346,7 @@ __device__ inline void mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int
     na = ny;
     nb = nx;
   }
+  if (b.work != nullptr && b.tid == 0) *b.work += pair_count(na, nb, npos);
   if (nb <= 0 || npos <= 0) {
     for (int i = b.tid; i < npos; i += b.nt) C[i] = 0u;
     b.sync();

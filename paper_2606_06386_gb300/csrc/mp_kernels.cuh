@@ -24,10 +24,14 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_uniform(UniformArgs a) {
     io.r = a.r + item * a.rs;
     io.rn = a.rn;
     int it = 0;
-    const int st = div_item(b, sm, a.smem_words, io, a.flags, &it, nullptr, 0, 0);
+    unsigned long long work = 0ull;
+    Blk bw = b;
+    bw.work = a.products ? &work : nullptr;
+    const int st = div_item(bw, sm, a.smem_words, io, a.flags, &it, nullptr, 0, 0);
     if (b.tid == 0) {
       a.status[item] = st;
       if (a.iters) a.iters[item] = it;
+      if (a.products) a.products[item] = (int64_t)work;
     }
     b.sync();
   }
@@ -57,10 +61,14 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_ragged(RaggedArgs a) {
     io.r = a.r + a.r_off[item];
     io.rn = a.r_len[item];
     int it = 0;
-    const int st = div_item(b, sm, a.smem_words, io, a.flags, &it, nullptr, 0, 0);
+    unsigned long long work = 0ull;
+    Blk bw = b;
+    bw.work = a.products ? &work : nullptr;
+    const int st = div_item(bw, sm, a.smem_words, io, a.flags, &it, nullptr, 0, 0);
     if (b.tid == 0) {
       a.status[item] = st;
       if (a.iters) a.iters[item] = it;
+      if (a.products) a.products[item] = (int64_t)work;
     }
     b.sync();
   }

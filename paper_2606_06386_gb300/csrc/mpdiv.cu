@@ -156,6 +156,7 @@ int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t st
   a.r = L.r;
   a.status = L.status;
   a.iters = L.iters;
+  a.products = L.products;
   a.n = L.n;
   a.us = L.us;
   a.vs = L.vs;
@@ -176,7 +177,7 @@ int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t st
 extern "C" int mpdiv_batch(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* u, int32_t u_limbs, int64_t u_stride,
                            const uint32_t* v, int32_t v_limbs, int64_t v_stride, uint32_t* q, int32_t q_limbs,
                            int64_t q_stride, uint32_t* r, int32_t r_limbs, int64_t r_stride, int32_t* status,
-                           int32_t* iters, void* stream) {
+                           int32_t* iters, int64_t* products, void* stream) {
   if (!ctx) return MPDIV_EINVAL;
   if (n_items < 0) return mpdiv_set_error(ctx, MPDIV_EINVAL, "n_items < 0");
   if (n_items == 0) return MPDIV_OK;
@@ -196,6 +197,7 @@ extern "C" int mpdiv_batch(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* u, i
   L.r = r;
   L.status = status;
   L.iters = iters;
+  L.products = products;
   L.n = n_items;
   L.us = u_stride;
   L.vs = v_stride;
@@ -282,6 +284,7 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
   a.r_len = L.r_len;
   a.status = L.status;
   a.iters = L.iters;
+  a.products = L.products;
   a.order = L.order ? L.order : ctx->d_order;
   a.head = L.head ? L.head : ctx->d_head;
   a.n = L.n;
@@ -336,8 +339,8 @@ extern "C" int mpdiv_batch_ragged(mpdiv_ctx* ctx, int64_t n_items, const uint32_
                                   const int32_t* u_len, const uint32_t* v, const int64_t* v_off,
                                   const int32_t* v_len, uint32_t* q, const int64_t* q_off, const int32_t* q_len,
                                   uint32_t* r, const int64_t* r_off, const int32_t* r_len, int32_t* status,
-                                  int32_t* iters, const int32_t* u_len_host, const int32_t* v_len_host,
-                                  void* stream) {
+                                  int32_t* iters, int64_t* products, const int32_t* u_len_host,
+                                  const int32_t* v_len_host, void* stream) {
   if (!ctx) return MPDIV_EINVAL;
   if (n_items < 0) return mpdiv_set_error(ctx, MPDIV_EINVAL, "n_items < 0");
   if (n_items == 0) return MPDIV_OK;
@@ -367,6 +370,7 @@ extern "C" int mpdiv_batch_ragged(mpdiv_ctx* ctx, int64_t n_items, const uint32_
   L.r_len = r_len;
   L.status = status;
   L.iters = iters;
+  L.products = products;
   L.u_len_host = u_len_host;
   L.v_len_host = v_len_host;
   L.n = n_items;

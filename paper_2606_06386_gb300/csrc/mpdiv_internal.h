@@ -45,6 +45,7 @@ struct UniformLaunch {
   const uint32_t *u, *v;
   uint32_t *q, *r;
   int32_t *status, *iters;
+  int64_t* products;
   int64_t n, us, vs, qs, rs;
   int un, vn, qn, rn;
   int warps;  // 0: from the tuning table
@@ -64,6 +65,7 @@ struct RaggedLaunch {
   const int64_t* r_off;
   const int32_t* r_len;
   int32_t *status, *iters;
+  int64_t* products;
   const int32_t *u_len_host, *v_len_host;
   const int32_t* order;  // device order array (nullptr: computed and cached here)
   int32_t* head;         // device queue head (nullptr: the context's)

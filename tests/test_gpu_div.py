@@ -97,3 +97,24 @@ def test_shinv_equals_model_and_theorem2():
         assert s_gpu == s_model, (i, v, h)
         assert s_gpu - B**h // v in (0, 1)
         assert I_[i] == tr.iterations
+
+
+@pytest.mark.parametrize("n,kl", [(64, 32), (300, 37), (1024, 512), (97, 96), (500, 2)])
+def test_product_counter_equals_model(n, kl):
+    # the kernel's count of algorithmic digit products equals the exact model's
+    import torch
+    import paper_2606_06386_gb300 as mp
+
+    U = I.uniform_batch(4, n, seed=77, stream=n)
+    V = I.uniform_batch(4, kl, seed=78, stream=kl)
+    q = torch.zeros((4, n), dtype=torch.int32, device="cuda:0")
+    r = torch.zeros((4, kl), dtype=torch.int32, device="cuda:0")
+    st = torch.zeros(4, dtype=torch.int32, device="cuda:0")
+    pr = torch.zeros(4, dtype=torch.int64, device="cuda:0")
+    mp.mpdiv_batch(ctx(), dev(U), dev(V), q, r, st, None, pr)
+    torch.cuda.synchronize()
+    P = pr.cpu().numpy()
+    for i in range(4):
+        tr = M.Trace()
+        M.div(oracle.to_int(U[i]), oracle.to_int(V[i]), B, tr)
+        assert P[i] == tr.digit_products()

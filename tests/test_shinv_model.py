@@ -169,5 +169,5 @@ def test_product_sizes_stay_near_cost_model(n, kl):
     tr = M.Trace()
     q, r, _ = M.div(u, v, B32, tr)
     assert (q, r) == divmod(u, v)
-    total = sum(a * b for _, a, b in tr.products)
+    total = tr.digit_products()
     assert total <= 7 * n * (n + 1) / 2
