@@ -252,7 +252,7 @@ __device__ inline int shinv(const Blk& b, const Layout& L, int h, int kl, int* l
   const int dd = (h - k < 2) ? 4 - (h - k) : 2;
   const int nl = max(lw - dd, 0);
   copy(b, R, nl, [&](int i) { return W[i + dd]; });
-  copy(b, W, nl, [&](int i) { return R[i]; });
+  copy(b, W, lw, [&](int i) { return i < nl ? R[i] : 0u; });  // clear the vacated top digits
   *lw_out = nl;
   *iters_out = nit;
   return ST_OK;

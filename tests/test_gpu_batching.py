@@ -1,0 +1,112 @@
+"""Mixed-precision batches (persistent launch over a size-sorted queue, CUDA
+graph replay), stress shapes at 2^18 bits, Theorem 2's delta = -1 path and the
+block-size tuner, all bit-exact against the CPU oracle."""
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.shinv_model as M
+from paper_2606_06386_gb300 import inputs as I
+
+from gpu_util import assert_same, ctx, dev, host_u32, oracle_uniform, run_uniform
+
+pytestmark = pytest.mark.gpu
+
+
+def _ragged(u_len, v_len, seed, c=None, edge=False):
+    import torch
+    import paper_2606_06386_gb300 as mp
+
+    c = c or ctx()
+    u_len = np.asarray(u_len, np.int32)
+    v_len = np.asarray(v_len, np.int32)
+    u_flat, u_off, v_flat, v_off = I.ragged_operands(u_len, v_len, seed=seed)
+    if edge:  # some items with a dividend smaller than the divisor, zero digits, v = 1
+        u_flat[u_off[0] : u_off[0] + u_len[0]] = 0
+        v_flat[v_off[1] : v_off[1] + v_len[1]] = 0
+        v_flat[v_off[1]] = 1
+    q_len = u_len.copy()
+    q_off = np.concatenate([[0], np.cumsum(q_len)[:-1]]).astype(np.int64)
+    r_len = v_len.copy()
+    r_off = np.concatenate([[0], np.cumsum(r_len)[:-1]]).astype(np.int64)
+    n = len(u_len)
+    T = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")  # noqa: E731
+    q = torch.full((int(q_len.sum()),), -1, dtype=torch.int32, device="cuda:0")
+    r = torch.full((int(r_len.sum()),), -1, dtype=torch.int32, device="cuda:0")
+    st = torch.full((n,), -7, dtype=torch.int32, device="cuda:0")
+    it = torch.full((n,), -1, dtype=torch.int32, device="cuda:0")
+    args = (dev(u_flat), T(u_off, None), T(u_len, None), dev(v_flat), T(v_off, None), T(v_len, None), q,
+            T(q_off, None), T(q_len, None), r, T(r_off, None), T(r_len, None), st, it)
+    mp.mpdiv_batch_ragged(c, *args)
+    torch.cuda.synchronize()
+    Q, R, S, IT = host_u32(q), host_u32(r), st.cpu().numpy(), it.cpu().numpy()
+    # replay with the same shapes (captured graph) must give the same digits
+    q.fill_(-1)
+    r.fill_(-1)
+    mp.mpdiv_batch_ragged(c, *args)
+    torch.cuda.synchronize()
+    assert (host_u32(q) == Q).all() and (host_u32(r) == R).all()
+    qo, ro, so, _ = oracle.divmod_ragged_u32(u_flat, u_off, u_len, v_flat, v_off, v_len, q_off, q_len, r_off, r_len)
+    bad = [i for i in range(n) if S[i] != so[i]
+           or not (Q[q_off[i]:q_off[i] + q_len[i]] == qo[q_off[i]:q_off[i] + q_len[i]]).all()
+           or not (R[r_off[i]:r_off[i] + r_len[i]] == ro[r_off[i]:r_off[i] + r_len[i]]).all()]
+    assert not bad, f"{len(bad)} of {n} items differ, first {bad[0]} (u {u_len[bad[0]]}, v {v_len[bad[0]]} digits)"
+    return IT
+
+
+def test_mixed_precision_persistent_launch():
+    u_len, v_len = I.mixed_sizes(192, seed=I.SEED_BASE + 20)
+    _ragged(u_len, v_len, seed=5)
+
+
+def test_mixed_small_shapes_and_edges():
+    rnd = np.random.default_rng(3)
+    u_len = rnd.integers(1, 300, size=200).astype(np.int32)
+    v_len = np.maximum(1, (u_len * rnd.uniform(0.05, 1.3, size=200)).astype(np.int32))
+    _ragged(u_len, v_len, seed=6, edge=True)
+
+
+@pytest.mark.parametrize("variant", I.STRESS_VARIANTS)
+def test_stress_2e18_bits(variant):
+    U, V = I.stress(variant, n_items=24)
+    Q, R, S, it = run_uniform(U, V)
+    Qo, Ro, So = oracle_uniform(U, V)
+    assert_same(Q, R, S, Qo, Ro, So)
+    for i in range(len(U)):
+        h = oracle.sig_len(U[i])
+        kl = oracle.sig_len(V[i])
+        if kl > 1 and h > kl:  # the Newton iteration runs: its count is the formula's
+            vi = oracle.to_int(V[i])
+            special = vi == (1 << (32 * (kl - 1))) or (h == kl and 2 * vi > (1 << (32 * h)))
+            if not special:
+                assert it[i] == M.refine_iterations(h, kl - 1)
+
+
+def test_inject_lambda_keeps_results_exact():
+    # shinv + 1 (Theorem 2's lambda = 1) must be absorbed by the delta = -1 correction
+    import paper_2606_06386_gb300 as mp
+
+    U, V, names = I.plain_1024(n_random=64)
+    Q, R, S, _ = run_uniform(U, V, flags=mp.MPDIV_FLAG_INJECT_LAMBDA)
+    Qo, Ro, So = oracle_uniform(U, V)
+    assert_same(Q, R, S, Qo, Ro, So, names)
+
+
+@pytest.mark.parametrize("warps", [4, 8, 16, 32])
+def test_every_block_size_is_exact(warps):
+    U, V = I.sweep(2048, 1024, 16)
+    Q, R, S, _ = run_uniform(U, V, warps=warps)
+    Qo, Ro, So = oracle_uniform(U, V)
+    assert_same(Q, R, S, Qo, Ro, So)
+
+
+def test_autotune_picks_a_block_size():
+    import paper_2606_06386_gb300 as mp
+
+    c = mp.mpdiv_init(0)
+    try:
+        w = mp.mpdiv_autotune(c, 1024, 512, 1024)
+        assert w in (4, 8, 16, 32)
+    finally:
+        mp.mpdiv_destroy(c)
