@@ -178,6 +178,35 @@ int mpdiv_serve_replay(mpdiv_ctx *ctx, int64_t n, const int64_t *arrival_ns, con
                        const int64_t *r_off, const int32_t *r_len, int32_t *status, int64_t *latency_ns,
                        int64_t *rejected);
 
+/* ---------------------------------------------------------------- allocation-free form
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory when they divide (a memory pool that owns the
+ * whole device, an allocator that forbids cudaMalloc after start-up, an
+ * embedding with a fixed memory budget). It runs the same persistent
+ * mixed-precision division kernel as mpdiv_batch_ragged, with the same
+ * arguments and results (iters and products are not produced), but without a
+ * context: it calls no cudaMalloc, cudaFree or other allocating routine and
+ * captures no graph. Its queue head and size-ordered item list live in a fixed
+ * scratch array in the library image, on every GPU that loads the library,
+ * until the process exits.
+ *  - At most MPDIV_NOALLOC_MAX_ITEMS items per call (the scratch holds one
+ *    order slot per item); more returns MPDIV_EUNSUPPORTED with nothing run.
+ *  - Runs on the current CUDA device. The first call on a device looks up the
+ *    scratch array's device address (cudaGetSymbolAddress) once; make that
+ *    first call outside any stream capture.
+ *  - Every call reuses the same scratch and clears what must start at zero.
+ *    Calls whose work overlaps on the GPU (for example on two streams at once)
+ *    race on the scratch: serialise them, for instance on one stream.
+ *  - Returns MPDIV_OK, MPDIV_EINVAL (null pointer, n_items < 0, a u_len_host
+ *    entry < 1), MPDIV_EUNSUPPORTED (too many items or digits) or MPDIV_ECUDA.
+ * All arrays except u_len_host (host) are device arrays, as in
+ * mpdiv_batch_ragged; r_len[i] >= v_len[i] >= 1 is required. */
+#define MPDIV_NOALLOC_MAX_ITEMS 65536
+int mpdiv_batch_ragged_noalloc(int64_t n_items, const uint32_t *u, const int64_t *u_off, const int32_t *u_len,
+                               const uint32_t *v, const int64_t *v_off, const int32_t *v_len, uint32_t *q,
+                               const int64_t *q_off, const int32_t *q_len, uint32_t *r, const int64_t *r_off,
+                               const int32_t *r_len, int32_t *status, const int32_t *u_len_host, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 SO_PATH = os.path.join(_BUILD, "libmpdiv.so")
 HEADER = os.path.join(_ROOT, "include", "mpdiv.h")
-SOURCES = ["mpdiv.cu", "mpdiv_tune.cu", "mpdiv_serve.cu"]
+SOURCES = ["mpdiv.cu", "mpdiv_tune.cu", "mpdiv_serve.cu", "mpdiv_noalloc.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 # return codes and statuses (include/mpdiv.h)
@@ -33,6 +33,7 @@ MPDIV_ST_OK, MPDIV_ST_DIV_BY_ZERO, MPDIV_ST_CORRECTION_OVERFLOW = 0, 1, 2
 MPDIV_ST_Q_OVERFLOW, MPDIV_ST_INTERNAL = 3, 4
 MPDIV_FLAG_INJECT_LAMBDA = 1
 MPDIV_MAX_LIMBS = 8192
+MPDIV_NOALLOC_MAX_ITEMS = 65536
 
 _lock = threading.Lock()
 _lib = None
@@ -102,6 +103,7 @@ _SIGS = {
     "mpdiv_serve_poll": (ctypes.c_int, [_P, _U64, _P, _I32, _P, _I32, ctypes.POINTER(_I32), _I64]),
     "mpdiv_serve_stop": (ctypes.c_int, [_P]),
     "mpdiv_serve_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "mpdiv_batch_ragged_noalloc": (ctypes.c_int, [_I64] + [_P] * 15),
     "mpdiv_serve_replay": (
         ctypes.c_int,
         [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_I64)],
@@ -213,6 +215,21 @@ def mpdiv_batch_ragged(ctx, u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r
             _ptr(q_len), _ptr(r), _ptr(r_off), _ptr(r_len), _ptr(status), _ptr(iters), _ptr(products), _ptr(u_len_host),
             _ptr(v_len_host), _stream(stream),
         ),
+    )
+
+
+def mpdiv_batch_ragged_noalloc(u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r, r_off, r_len, status,
+                               u_len_host=None, stream=None) -> int:
+    """The allocation-free ragged launch (no context): same arrays as
+    mpdiv_batch_ragged. Returns the C return code (MPDIV_OK or a negative code)."""
+    _check_dev(u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r, r_off, r_len, status)
+    if u_len_host is None:
+        u_len_host = u_len.cpu()
+    u_len_host = u_len_host.contiguous()
+    n = u_off.shape[0]
+    return lib().mpdiv_batch_ragged_noalloc(
+        n, _ptr(u), _ptr(u_off), _ptr(u_len), _ptr(v), _ptr(v_off), _ptr(v_len), _ptr(q), _ptr(q_off),
+        _ptr(q_len), _ptr(r), _ptr(r_off), _ptr(r_len), _ptr(status), _ptr(u_len_host), _stream(stream),
     )
 
 
