@@ -304,6 +304,232 @@ def run_sweep(args, dev, dist, rank, ws):
     return out
 
 
+def _ragged_setup(u_len, v_len, seed, dev):
+    import torch
+
+    u_len = np.asarray(u_len, np.int32)
+    v_len = np.asarray(v_len, np.int32)
+    u_flat, u_off, v_flat, v_off = I.ragged_operands(u_len, v_len, seed=seed)
+    q_len, r_len = u_len.copy(), v_len.copy()
+    q_off = np.concatenate([[0], np.cumsum(q_len)[:-1]]).astype(np.int64)
+    r_off = np.concatenate([[0], np.cumsum(r_len)[:-1]]).astype(np.int64)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    n = len(u_len)
+    return dict(
+        n=n, u_len=u_len, v_len=v_len, u_flat=u_flat, u_off=u_off, v_flat=v_flat, v_off=v_off, q_off=q_off,
+        r_off=r_off, q_len=q_len, r_len=r_len,
+        args=[d(u_flat.view(np.int32)), d(u_off), d(u_len), d(v_flat.view(np.int32)), d(v_off), d(v_len),
+              torch.zeros(int(q_len.sum()), dtype=torch.int32, device=dev), d(q_off), d(q_len),
+              torch.zeros(int(r_len.sum()), dtype=torch.int32, device=dev), d(r_off), d(r_len),
+              torch.full((n,), -1, dtype=torch.int32, device=dev)],
+        u_len_host=torch.from_numpy(u_len), v_len_host=torch.from_numpy(v_len),
+    )
+
+
+def _class_batches(R, classes, dev, key):
+    """Group a ragged set into uniform zero-padded batches, one per group key."""
+    import torch
+
+    groups = {}
+    for i in range(R["n"]):
+        groups.setdefault(key(int(R["u_len"][i])), []).append(i)
+    out = []
+    for c, idx in sorted(groups.items()):
+        idx = np.array(idx)
+        vw = int(R["v_len"][idx].max())
+        U = np.zeros((len(idx), c), np.uint32)
+        V = np.zeros((len(idx), vw), np.uint32)
+        for j, i in enumerate(idx):
+            U[j, : R["u_len"][i]] = R["u_flat"][R["u_off"][i] : R["u_off"][i] + R["u_len"][i]]
+            V[j, : R["v_len"][i]] = R["v_flat"][R["v_off"][i] : R["v_off"][i] + R["v_len"][i]]
+        out.append(dict(u=_to_dev(U, dev), v=_to_dev(V, dev),
+                        q=torch.zeros((len(idx), c), dtype=torch.int32, device=dev),
+                        r=torch.zeros((len(idx), vw), dtype=torch.int32, device=dev),
+                        st=torch.full((len(idx),), -1, dtype=torch.int32, device=dev)))
+    return out
+
+
+def _time(fn, stream, reps):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_mixed(args, dev, dist, rank, ws):
+    """One persistent launch of 8192 mixed-precision divisions (size-sorted queue,
+    CUDA graph replay) against plain launches per padded size class and per
+    distinct dividend length."""
+    import torch
+
+    import paper_2606_06386_gb300 as mp
+
+    mp.build()
+    ctx = mp.mpdiv_init(dev.index or 0)
+    u_len, v_len = I.mixed_sizes(8192)
+    R = _ragged_setup(u_len, v_len, seed=I.SEED_BASE + 2, dev=dev)
+    stream = torch.cuda.current_stream(dev)
+    prod = torch.zeros(R["n"], dtype=torch.int64, device=dev)
+    mp.mpdiv_batch_ragged(ctx, *R["args"], None, prod, R["u_len_host"], R["v_len_host"], stream)
+    torch.cuda.synchronize(dev)
+    if int((R["args"][12] != 0).sum().item()):
+        raise RuntimeError("nonzero status in the mixed batch")
+    products = int(prod.sum().item())
+    persistent = lambda: mp.mpdiv_batch_ragged(ctx, *R["args"], None, None, R["u_len_host"], R["v_len_host"],  # noqa
+                                               stream)
+    for _ in range(args.warmup):
+        persistent()
+    _barrier(dist, dev)
+    with ClockSampler(dev.index or 0) as clk:
+        ms_persist = _time(persistent, stream, args.steps)
+    classes = _class_batches(R, None, dev, key=lambda n: 1 << max(10, (n - 1).bit_length()))
+    per_n = _class_batches(R, None, dev, key=lambda n: n)
+
+    def plain(batches):
+        for b in batches:
+            mp.mpdiv_batch(ctx, b["u"], b["v"], b["q"], b["r"], b["st"], None, None, stream)
+
+    plain(classes)
+    plain(per_n)
+    ms_class = _time(lambda: plain(classes), stream, max(3, args.steps // 2))
+    ms_n = _time(lambda: plain(per_n), stream, 2)
+    ms_persist = _max_over_ranks(dist, ms_persist, dev)
+    n = R["n"]
+    out = {
+        "metric": METRIC, "value": n * ws / (ms_persist / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_persist, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "mixed precisions: 8192 divisions, dividends 2^(15+3x) bits (x uniform), divisors "
+                               "(0.25+0.75y) x dividend length; one persistent launch over a size-sorted queue, "
+                               "replayed as a CUDA graph",
+                   "l2": "inputs 113 MB, re-read each step (compute-bound: ~1 MB/ms)"},
+        "plain_per_size_class": {"div_per_s": n / (ms_class / 1e3), "launches": len(classes), "ms": ms_class},
+        "plain_per_distinct_n": {"div_per_s": n / (ms_n / 1e3), "launches": len(per_n), "ms": ms_n},
+        "batched_over_plain_class": ms_class / ms_persist,
+        "digit_products_per_div": products / n,
+        "Tprod_per_s": products / (ms_persist / 1e3) / 1e12,
+        "gpu_launches": args.steps,
+    }
+    c = clk.summary()
+    if c is not None:
+        out["clocks"] = c
+    mp.mpdiv_destroy(ctx)
+    return out
+
+
+def run_serve(args, dev, dist, rank, ws):
+    """Poisson arrivals of mixed-precision requests through the serving loop at
+    50/80/95% of the plain path's measured capacity (per-size-class launches)."""
+    import torch
+
+    import paper_2606_06386_gb300 as mp
+
+    mp.build()
+    ctx = mp.mpdiv_init(dev.index or 0)
+    u_len, v_len = I.mixed_sizes(8192)
+    R = _ragged_setup(u_len, v_len, seed=I.SEED_BASE + 2, dev=dev)
+    stream = torch.cuda.current_stream(dev)
+    classes = _class_batches(R, None, dev, key=lambda n: 1 << max(10, (n - 1).bit_length()))
+
+    def plain():
+        for b in classes:
+            mp.mpdiv_batch(ctx, b["u"], b["v"], b["q"], b["r"], b["st"], None, None, stream)
+
+    plain()
+    cap = R["n"] / (_time(plain, stream, 3) / 1e3)
+    n_req = args.requests
+    pick = np.arange(n_req) % R["n"]  # request i divides mixed item i mod 8192
+    res = {}
+    for frac in (0.5, 0.8, 0.95):
+        rate = frac * cap
+        arr = (I.poisson_arrivals(n_req, rate, seed=I.SEED_BASE + 3, stream=int(frac * 100)) * 1e9).astype(np.int64)
+        ul = R["u_len"][pick].astype(np.int32)
+        vl = R["v_len"][pick].astype(np.int32)
+        uo = R["u_off"][pick].astype(np.int64)
+        vo = R["v_off"][pick].astype(np.int64)
+        qo = R["q_off"][pick].astype(np.int64)  # results of repeated items land in the same slots
+        ro = R["r_off"][pick].astype(np.int64)
+        q = np.zeros(int(R["q_len"].sum()), np.uint32)
+        r = np.zeros(int(R["r_len"].sum()), np.uint32)
+        st = np.full(n_req, -9, np.int32)
+        lat = np.zeros(n_req, np.int64)
+        mp.mpdiv_serve_start(ctx, pool_digits=256 << 20, max_batch=args.max_batch, max_inflight=3)
+        with ClockSampler(dev.index or 0) as clk:
+            t0 = time.perf_counter()
+            rej = mp.mpdiv_serve_replay(ctx, arr, R["u_flat"], uo, ul, R["v_flat"], vo, vl, q, qo, ul.copy(), r,
+                                        ro, vl.copy(), st, lat)
+            wall = time.perf_counter() - t0
+        completed, launches, batched = mp.mpdiv_serve_stats(ctx)
+        mp.mpdiv_serve_stop(ctx)
+        ok = int((st == 0).sum())
+        done_t = arr + lat
+        span = (done_t.max() - arr.min()) / 1e9
+        res[f"{int(frac * 100)}%"] = {
+            "offered_div_per_s": rate, "sustained_div_per_s": n_req / span, "p50_ms": float(np.percentile(lat, 50)) / 1e6,
+            "p99_ms": float(np.percentile(lat, 99)) / 1e6, "max_ms": float(lat.max()) / 1e6, "ok": ok,
+            "launches": launches, "mean_batch": batched / max(1, launches), "busy_retries": rej, "wall_s": wall,
+            "clocks": clk.summary(),
+        }
+    out = {
+        "metric": METRIC, "value": res["95%"]["sustained_div_per_s"], "unit": UNIT, "n_gpus": ws,
+        "steps": 1, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"serving: {n_req} Poisson-arrival requests, sizes as the mixed batch, offered at "
+                               "50/80/95% of the plain per-size-class capacity; latency from scheduled arrival "
+                               "to result pollable on the host"},
+        "plain_capacity_div_per_s": cap, "loads": res,
+    }
+    mp.mpdiv_destroy(ctx)
+    return out
+
+
+def run_stress(args, dev, dist, rank, ws):
+    """Adversarial cases at 2^18 bits, 1024 divisions each, with Newton iteration counts."""
+    import torch
+
+    import paper_2606_06386_gb300 as mp
+
+    mp.build()
+    ctx = mp.mpdiv_init(dev.index or 0)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    total_items, total_ms = 0, 0.0
+    for variant in I.STRESS_VARIANTS:
+        U, V = I.stress(variant)
+        u, v = _to_dev(U, dev), _to_dev(V, dev)
+        n = U.shape[0]
+        q = torch.zeros((n, U.shape[1]), dtype=torch.int32, device=dev)
+        r = torch.zeros((n, V.shape[1]), dtype=torch.int32, device=dev)
+        st = torch.full((n,), -1, dtype=torch.int32, device=dev)
+        it = torch.zeros(n, dtype=torch.int32, device=dev)
+        pr = torch.zeros(n, dtype=torch.int64, device=dev)
+        mp.mpdiv_batch(ctx, u, v, q, r, st, it, pr, stream)
+        torch.cuda.synchronize(dev)
+        ms = _time(lambda: mp.mpdiv_batch(ctx, u, v, q, r, st, None, None, stream), stream, max(3, args.steps // 4))
+        its = it.cpu().numpy()
+        res[variant] = {"div_per_s": n / (ms / 1e3), "ms": ms, "status_nonzero": int((st != 0).sum().item()),
+                        "newton_iters_min": int(its.min()), "newton_iters_max": int(its.max()),
+                        "digit_products_per_div": float(pr.sum().item()) / n,
+                        "Tprod_per_s": float(pr.sum().item()) / (ms / 1e3) / 1e12}
+        total_items += n
+        total_ms += ms
+    out = {
+        "metric": METRIC, "value": total_items / (total_ms / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "stress at 2^18-bit dividends: 1024 divisions per variant (short divisor, just over "
+                               "half, all ones, 1% sparse, v = B^k - 1)"},
+        "variants": res,
+    }
+    mp.mpdiv_destroy(ctx)
+    return out
+
+
 def run_reference(args, rank, ws):
     """The reference arm: the CPU oracle on this machine's host cores."""
     out_sample = []
@@ -340,6 +566,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep", choices=["sweep", "mixed", "serve", "stress"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=200000, help="serve workload: number of requests")
+    ap.add_argument("--max-batch", type=int, default=1024, help="serve workload: most requests per launch")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -355,12 +583,8 @@ def main():
     dist, rank, ws, local = _dist()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    if args.workload == "sweep":
-        out = run_sweep(args, dev, dist, rank, ws)
-    else:
-        import bench_workloads
-
-        out = bench_workloads.run(args.workload, args, dev, dist, rank, ws)
+    runner = {"sweep": run_sweep, "mixed": run_mixed, "serve": run_serve, "stress": run_stress}[args.workload]
+    out = runner(args, dev, dist, rank, ws)
     if rank == 0:
         print(json.dumps(out))
     if dist is not None:

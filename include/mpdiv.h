@@ -138,7 +138,9 @@ typedef struct mpdiv_serve_config {
   int32_t max_pending;  /* submitted-but-unfinished requests before EBUSY (0: 1<<20) */
 } mpdiv_serve_config;
 
-/* Start the server on ctx (cfg may be NULL). MPDIV_ESTATE if already running. */
+/* Start the server on ctx (cfg may be NULL). MPDIV_ESTATE if one is running.
+ * Starting again after mpdiv_serve_stop releases the stopped server first, and
+ * with it the results of tickets that were never polled. */
 int mpdiv_serve_start(mpdiv_ctx *ctx, const mpdiv_serve_config *cfg);
 
 /* Submit one division from host memory; the operands are copied before the

@@ -333,7 +333,15 @@ void MpServer::run() {
 // ------------------------------------------------------------------ C ABI
 extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) {
   if (!ctx) return MPDIV_EINVAL;
-  if (ctx->server) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server already running");
+  if (ctx->server) {
+    bool stopped;
+    {
+      std::lock_guard<std::mutex> g(ctx->server->mu);
+      stopped = ctx->server->stopping;
+    }
+    if (!stopped) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server already running");
+    mpdiv_serve_shutdown(ctx);  // a stopped server is released: its unpolled results are dropped
+  }
   cudaSetDevice(ctx->device);
   auto* S = new MpServer();
   S->ctx = ctx;
