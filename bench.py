@@ -183,6 +183,8 @@ def run_sweep(args, dev, dist, rank, ws):
                  prod=torch.zeros((b,), dtype=torch.int64, device=dev))
         sizes.append(d)
     stream = torch.cuda.current_stream(dev)
+    # the tuner picks warps per block for each size class (kept in the context)
+    tuned = {d["n"]: mp.mpdiv_autotune(ctx, d["n"], d["kl"], d["b"]) for d in sizes}
     # one untimed pass that also records the algorithmic digit products per item
     for d in sizes:
         mp.mpdiv_batch(ctx, d["u"], d["v"], d["q"], d["r"], d["st"], None, d["prod"], stream)
@@ -269,6 +271,7 @@ def run_sweep(args, dev, dist, rank, ws):
             "digit_products_per_div": d["products"] / d["b"],
             "cost_units_per_div": d["products"] / d["b"] / (d["n"] * (d["n"] + 1) / 2),
             "Tprod_per_s": d["products"] / (per_size_ms[i] / 1e3) / 1e12,
+            "warps_per_block": tuned[d["n"]],
         }
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
@@ -388,6 +391,8 @@ def run_mixed(args, dev, dist, rank, ws):
     with ClockSampler(dev.index or 0) as clk:
         ms_persist = _time(persistent, stream, args.steps)
     classes = _class_batches(R, None, dev, key=lambda n: 1 << max(10, (n - 1).bit_length()))
+    for c in (1024, 2048, 4096, 8192):  # tuned block size per class for the plain launches
+        mp.mpdiv_autotune(ctx, c, c // 2, 1024)
     per_n = _class_batches(R, None, dev, key=lambda n: n)
 
     def plain(batches):
@@ -458,7 +463,7 @@ def run_serve(args, dev, dist, rank, ws):
         r = np.zeros(int(R["r_len"].sum()), np.uint32)
         st = np.full(n_req, -9, np.int32)
         lat = np.zeros(n_req, np.int64)
-        mp.mpdiv_serve_start(ctx, pool_digits=256 << 20, max_batch=args.max_batch, max_inflight=3)
+        mp.mpdiv_serve_start(ctx, pool_digits=256 << 20, max_batch=args.max_batch, max_inflight=args.max_inflight)
         with ClockSampler(dev.index or 0) as clk:
             t0 = time.perf_counter()
             rej = mp.mpdiv_serve_replay(ctx, arr, R["u_flat"], uo, ul, R["v_flat"], vo, vl, q, qo, ul.copy(), r,
@@ -567,7 +572,8 @@ def main():
     ap.add_argument("--workload", default="sweep", choices=["sweep", "mixed", "serve", "stress"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=200000, help="serve workload: number of requests")
-    ap.add_argument("--max-batch", type=int, default=1024, help="serve workload: most requests per launch")
+    ap.add_argument("--max-batch", type=int, default=1024, help="serve workload: most requests per batch")
+    ap.add_argument("--max-inflight", type=int, default=16, help="serve workload: batches in flight")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -56,6 +56,10 @@ extern "C" {
 
 /* flags of mpdiv_config.flags */
 #define MPDIV_FLAG_INJECT_LAMBDA 1 /* test only: use shinv + 1, forcing Theorem 2's delta = -1 path */
+#define MPDIV_FLAG_FULL_PRODUCTS 2 /* Algorithm 3 with the paper's full products u*shinv and v*q
+                                      (default: clipped products, Section 5: the quotient from the
+                                      columns at or above h-2 of u*shinv, the remainder from
+                                      v*q mod B^(prec(v)+1); same results, fewer products) */
 
 typedef struct mpdiv_ctx mpdiv_ctx; /* opaque; owned by the library */
 
@@ -133,9 +137,12 @@ int mpdiv_autotune(mpdiv_ctx *ctx, int32_t u_limbs, int32_t v_limbs, int32_t n_i
  * run join the next launch. */
 typedef struct mpdiv_serve_config {
   int64_t pool_digits;  /* digits of device operand/result pool (0: 64 Mi digits) */
-  int32_t max_batch;    /* most requests per launch (0: 4096) */
-  int32_t max_inflight; /* launches in flight at once (0: 3) */
+  int32_t max_batch;    /* most requests per batch (0: 4096) */
+  int32_t max_inflight; /* batches in flight at once, each on its own stream (0: 16) */
   int32_t max_pending;  /* submitted-but-unfinished requests before EBUSY (0: 1<<20) */
+  int32_t low_water;    /* below this many requests on the GPU, queued requests launch at
+                           once; above it they gather into larger batches (0: 1024) */
+  int32_t max_wait_us;  /* longest a queued request waits for its batch to grow (0: 2000) */
 } mpdiv_serve_config;
 
 /* Start the server on ctx (cfg may be NULL). MPDIV_ESTATE if one is running.

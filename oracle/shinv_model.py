@@ -66,22 +66,21 @@ class Trace:
     products: list = field(default_factory=list)  # (tag, prec a, prec b)
     iterates: list = field(default_factory=list)  # w after each Refine step
 
-    def mult(self, tag: str, a: int, b: int, B: int, keep: int | None = None) -> int:
+    def mult(self, tag: str, a: int, b: int, B: int, keep: int | None = None, lo: int = 0) -> int:
         """Record a product of prec(a) x prec(b) digits; ``keep`` is the number of
-        low digits a close product (MultMod) keeps."""
-        self.products.append((tag, prec(a, B), prec(b, B), keep))
+        low digits a close product (MultMod) keeps, ``lo`` the lowest column a
+        clipped product computes."""
+        self.products.append((tag, prec(a, B), prec(b, B), keep, lo))
         return a * b
 
     def digit_products(self) -> int:
-        """Digit products of the multiplications made: a full product of m x n
-        digits costs m n; one kept modulo B^L costs the pairs (i, j) with
-        i + j < L."""
+        """Digit products of the multiplications made: the digit pairs (i, j) of
+        an m x n product with lo <= i + j < keep (keep = m + n for a full product,
+        L for one kept modulo B^L; lo = 0 unless the product is clipped)."""
         total = 0
-        for _, m, n, keep in self.products:
-            if keep is None or keep >= m + n - 1:
-                total += m * n
-            else:
-                total += sum(max(0, min(n, keep - i)) for i in range(m))
+        for _, m, n, keep, lo in self.products:
+            hi = m + n if keep is None else keep
+            total += sum(max(0, min(n, hi - i) - max(0, lo - i)) for i in range(m))
         return total
 
 
@@ -193,3 +192,40 @@ def div(u: int, v: int, B: int, tr: Trace | None = None) -> tuple[int, int, int]
 def newton_shift_step(w: int, v: int, h: int, B: int) -> int:
     """The whole-shifted Newton step of Eq. (3): w + shift_{-h}(shift_h(w) - v w^2)."""
     return w + shift(-h, shift(h, w, B) - v * w * w, B)
+
+
+def div_clipped(u: int, v: int, B: int, tr: Trace | None = None, guard: int = 2) -> tuple[int, int]:
+    """Algorithm 3 with clipped products (the refinement Section 5 proposes):
+
+    * q0 is formed from the digit products of u * shinv_h(v) at columns
+      h - guard and above only (the carries of the lower columns are dropped),
+      which leaves q0 at most one short of shift_{-h}(u * shinv_h(v));
+    * u - v q0 then lies in (-2v, 2v), so it is taken from v q0 modulo B^(k+2)
+      (k + 1 = prec(v)) and read as a two's-complement number;
+    * the corrections of Theorem 2 finish the division.
+    """
+    if tr is None:
+        tr = Trace()
+    if v <= 0:
+        raise ZeroDivisionError("division by zero")
+    h = prec(u, B)
+    w = shinv(v, h, B, tr)
+    lo = max(0, h - guard)
+    full = tr.mult("quotient_clipped", u, w, B, lo=lo)
+    low = 0  # the digit products below column lo, summed exactly
+    for j in range(prec(w, B)):
+        if lo - j <= 0:
+            break
+        low += ((w // B**j) % B) * (u % B ** (lo - j)) * B**j
+    q = (full - low) // B**h
+    K1 = prec(v, B) + 1
+    t = (u - tr.mult("remainder_low", v, q, B, keep=K1)) % B**K1
+    if t >= B**K1 // 2:
+        t -= B**K1
+    while t < 0:
+        q -= 1
+        t += v
+    while t >= v:
+        q += 1
+        t -= v
+    return q, t

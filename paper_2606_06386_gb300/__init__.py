@@ -32,6 +32,7 @@ MPDIV_EBUSY, MPDIV_ETIMEDOUT, MPDIV_ESTATE = -5, -6, -7
 MPDIV_ST_OK, MPDIV_ST_DIV_BY_ZERO, MPDIV_ST_CORRECTION_OVERFLOW = 0, 1, 2
 MPDIV_ST_Q_OVERFLOW, MPDIV_ST_INTERNAL = 3, 4
 MPDIV_FLAG_INJECT_LAMBDA = 1
+MPDIV_FLAG_FULL_PRODUCTS = 2
 MPDIV_MAX_LIMBS = 8192
 MPDIV_NOALLOC_MAX_ITEMS = 65536
 
@@ -85,6 +86,8 @@ class mpdiv_serve_config(ctypes.Structure):
         ("max_batch", ctypes.c_int32),
         ("max_inflight", ctypes.c_int32),
         ("max_pending", ctypes.c_int32),
+        ("low_water", ctypes.c_int32),
+        ("max_wait_us", ctypes.c_int32),
     ]
 
 
@@ -250,8 +253,9 @@ def mpdiv_autotune(ctx, u_limbs: int, v_limbs: int, n_items: int) -> int:
 
 
 # ---------------------------------------------------------------- serving
-def mpdiv_serve_start(ctx, pool_digits: int = 0, max_batch: int = 0, max_inflight: int = 0, max_pending: int = 0):
-    cfg = mpdiv_serve_config(pool_digits, max_batch, max_inflight, max_pending)
+def mpdiv_serve_start(ctx, pool_digits: int = 0, max_batch: int = 0, max_inflight: int = 0, max_pending: int = 0,
+                      low_water: int = 0, max_wait_us: int = 0):
+    cfg = mpdiv_serve_config(pool_digits, max_batch, max_inflight, max_pending, low_water, max_wait_us)
     _check(ctx, lib().mpdiv_serve_start(ctx, ctypes.byref(cfg)))
 
 

@@ -39,6 +39,7 @@ struct RaggedArgs {
   int64_t n;
   int smem_words;
   int flags;
+  int split_digits[2];  // k_div_persistent: largest dividend for 4 and for 8 warps
 };
 
 struct ShinvArgs {

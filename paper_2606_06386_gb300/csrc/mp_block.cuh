@@ -323,20 +323,45 @@ __device__ __forceinline__ void mul_strip(const Blk& b, uint32_t* C, int npos, c
 
 // Digit pairs (i, j) with i < na, j < nb and i + j < npos: the digit products
 // of a product kept modulo B^npos (all na nb of them for a full product).
-__device__ __forceinline__ unsigned long long pair_count(int na, int nb, int npos) {
+__host__ __device__ __forceinline__ unsigned long long pair_count(int na, int nb, int npos) {
   if (na <= 0 || nb <= 0 || npos <= 0) return 0ull;
-  const long long c1 = max(0, min(na, npos - nb + 1));
+  const long long c1 = npos - nb + 1 < 0 ? 0 : (npos - nb + 1 < na ? npos - nb + 1 : na);
   unsigned long long s = (unsigned long long)c1 * nb;
-  const long long a = c1, e = min(na, npos);
+  const long long a = c1, e = na < npos ? na : npos;
   if (e > a) s += (unsigned long long)((e - a) * npos - (a + e - 1) * (e - a) / 2);
   return s;
 }
 
-// C[0..npos) = (X * Y) mod B^npos. X (nx digits) and Y (ny digits) are
+// Order of warp strips, heaviest first: strips on the plateau of the
+// trapezoid of row counts (every row of the shorter operand) come first, then
+// strips alternately left and right of it by distance. The band [ws0, nws) is
+// the part of the product that is computed.
+__device__ __forceinline__ int strip_order(int idx, int ws0, int nws, int na, int nb) {
+  int lo = (nb - WSPAN + WSPAN - 1) / WSPAN;  // first strip whose rows reach nb
+  if (lo < 0) lo = 0;
+  int hi = (na - 1) / WSPAN;  // last strip before the ramp down
+  lo = min(max(lo, ws0), nws - 1);
+  hi = min(max(hi, ws0), nws - 1);
+  if (hi < lo) hi = lo;
+  const int np = hi - lo + 1;
+  if (idx < np) return lo + idx;
+  const int k = idx - np;
+  const int nl = lo - ws0, nr = nws - 1 - hi;
+  const int m = min(nl, nr);
+  if (k < 2 * m) return (k & 1) ? hi + (k >> 1) + 1 : lo - (k >> 1) - 1;
+  const int d = m + 1 + (k - 2 * m);
+  return (nl > nr) ? lo - d : hi + d;
+}
+
+// C[plo..npos) of X * Y: the digits of (X * Y) mod B^npos at positions plo
+// and above, from the digit products at positions at or above the warp strip
+// holding plo; carries from products below that strip are dropped (plo = 0:
+// the exact product modulo B^npos). X (nx digits) and Y (ny digits) are
 // multiply operands: PAD zero digits must be addressable below index 0 and
 // above the digit count (the high pads are zeroed here). OV needs
 // 2 * 32 * ceil(npos / WSPAN) words. C must not alias X or Y.
-__device__ inline void mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int nx, uint32_t* Y, int ny, uint32_t* OV) {
+__device__ inline void mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int nx, uint32_t* Y, int ny, uint32_t* OV,
+                           int plo = 0) {
   uint32_t* A = X;
   uint32_t* Bv = Y;
   int na = nx, nb = ny;
@@ -346,9 +371,11 @@ __device__ inline void mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int
     na = ny;
     nb = nx;
   }
-  if (b.work != nullptr && b.tid == 0) *b.work += pair_count(na, nb, npos);
-  if (nb <= 0 || npos <= 0) {
-    for (int i = b.tid; i < npos; i += b.nt) C[i] = 0u;
+  if (plo < 0) plo = 0;
+  if (b.work != nullptr && b.tid == 0)
+    *b.work += pair_count(na, nb, npos) - pair_count(na, nb, min(plo, npos));
+  if (nb <= 0 || npos <= plo) {
+    for (int i = plo + b.tid; i < npos; i += b.nt) C[i] = 0u;
     b.sync();
     return;
   }
@@ -358,25 +385,25 @@ __device__ inline void mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int
   }
   if (b.tid == 0) b.red[RED_CNT] = 0;
   b.sync();
+  const int ws0 = plo / WSPAN;
   const int nws = (npos + WSPAN - 1) / WSPAN;
-  const int mid = (nws - 1) / 2;
+  const int cnt = nws - ws0;
   while (true) {
     int idx = 0;
     if (b.lane == 0) idx = atomicAdd(&b.red[RED_CNT], 1);
     idx = __shfl_sync(FULL, idx, 0);
-    if (idx >= nws) break;
-    // centre-out order: the strips of a full product carry a trapezoid of work
-    const int ws = (idx == 0) ? mid : ((idx & 1) ? mid + (idx + 1) / 2 : mid - idx / 2);
-    mul_strip(b, C, npos, A, na, Bv, nb, OV, ws);
+    if (idx >= cnt) break;
+    mul_strip(b, C, npos, A, na, Bv, nb, OV, strip_order(idx, ws0, nws, na, nb));
   }
   b.sync();
   // fold each strip's overflow digits into the next strip's first two columns
+  const int p0 = ws0 * WSPAN, s0 = ws0 * 32;
   addsub<false>(
-      b, C, npos, [&](int i) { return C[i]; },
+      b, C + p0, npos - p0, [&](int i) { return C[p0 + i]; },
       [&](int i) -> uint32_t {
-        const int s = i / T;
-        const int off = i - s * T;
-        return (s >= 1 && off < 2) ? OV[2 * (s - 1) + off] : 0u;
+        const int s = (p0 + i) / T;
+        const int off = p0 + i - s * T;
+        return (s > s0 && off < 2) ? OV[2 * (s - 1) + off] : 0u;
       },
       0u);
 }

@@ -26,7 +26,12 @@
 namespace mp {
 
 enum : int { ST_OK = 0, ST_DIV_BY_ZERO = 1, ST_CORR = 2, ST_QOVF = 3, ST_INTERNAL = 4 };
-enum : int { FLAG_INJECT_LAMBDA = 1 };
+enum : int { FLAG_INJECT_LAMBDA = 1, FLAG_FULL_PRODUCTS = 2 };
+
+// Guard digits of the clipped quotient product: the digit products below
+// position h - QGUARD are skipped, which drops less than min(h, |w|) B^(h-1)
+// < B^h from u w and so leaves q0 at most one short.
+constexpr int QGUARD = 2;
 
 struct Layout {
   uint32_t *V, *W, *X, *R, *U, *P, *OV;
@@ -316,34 +321,57 @@ __device__ inline int div_item(const Blk& b, uint32_t* sm, int smem_words, const
   // ---- q0 = shift_{-h}(u * w)
   uint32_t* U = L.U;
   uint32_t* P = L.P;
+  const bool full = (flags & FLAG_FULL_PRODUCTS) != 0;
   load_global(b, U, h, [&](int i) { return gu[i]; });
   const int np = h + lw;
   if (np > L.capP) return ST_INTERNAL;
-  mul(b, P, np, U, h, W, lw, L.OV);
+  // full: the exact product; clipped (Section 5's clipped products): only the
+  // columns at or above h - QGUARD, so q0 may come out one short
+  mul(b, P, np, U, h, W, lw, L.OV, full ? 0 : max(0, h - QGUARD));
   int lq = np - h;
   if (lq + 1 > L.capW) return ST_INTERNAL;
   copy(b, W, lq, [&](int i) { return P[h + i]; });  // q lives in W from here
   if (b.tid == 0) W[lq] = 0u;
   lq = prec(b, W, lq);
-  // ---- m = v * q
   uint32_t* V = L.V;
-  int nm = kl + lq;
-  if (nm > L.capP) return ST_INTERNAL;
-  mul(b, P, nm, V, kl, W, lq, L.OV);
-  nm = prec(b, P, nm);
-  // ---- if u < m: q -= 1, m -= v   (Theorem 2: delta = -1)
-  for (int t = 0;; t++) {
-    if (cmp(b, U, h, P, nm) >= 0) break;
-    if (t == 2) return ST_CORR;
-    if (!sub_pow(b, W, 0, lq)) return ST_INTERNAL;
-    addsub<true>(b, P, nm, [&](int i) { return P[i]; }, [&](int i) { return i < kl ? V[i] : 0u; }, 0u);
-    lq = prec(b, W, lq);
+  int lr;
+  if (full) {
+    // ---- m = v * q
+    int nm = kl + lq;
+    if (nm > L.capP) return ST_INTERNAL;
+    mul(b, P, nm, V, kl, W, lq, L.OV);
     nm = prec(b, P, nm);
+    // ---- if u < m: q -= 1, m -= v   (Theorem 2: delta = -1)
+    for (int t = 0;; t++) {
+      if (cmp(b, U, h, P, nm) >= 0) break;
+      if (t == 2) return ST_CORR;
+      if (!sub_pow(b, W, 0, lq)) return ST_INTERNAL;
+      addsub<true>(b, P, nm, [&](int i) { return P[i]; }, [&](int i) { return i < kl ? V[i] : 0u; }, 0u);
+      lq = prec(b, W, lq);
+      nm = prec(b, P, nm);
+    }
+    // ---- r = u - m (into P, in place)
+    addsub<true>(b, P, h, [&](int i) { return U[i]; }, [&](int i) { return i < nm ? P[i] : 0u; }, 0u);
+    lr = prec(b, P, h);
+  } else {
+    // ---- t = u - v q0 is in (-2v, 2v) (Theorem 2 and the clipped q0), so it is
+    // determined by its value modulo B^(kl+1): only the low product is needed.
+    const int K1 = kl + 1;
+    if (K1 > L.capP) return ST_INTERNAL;
+    mul(b, P, K1, V, kl, W, lq, L.OV);  // v q0 mod B^(kl+1)
+    addsub<true>(b, P, K1, [&](int i) { return i < h ? U[i] : 0u; }, [&](int i) { return P[i]; }, 0u);
+    // ---- while t < 0 (top digit of the two's complement): q -= 1, t += v
+    for (int t = 0;; t++) {
+      if (P[K1 - 1] < 0x80000000u) break;
+      if (t == 2) return ST_CORR;
+      if (!sub_pow(b, W, 0, lq)) return ST_INTERNAL;
+      addsub<false>(b, P, K1, [&](int i) { return P[i]; }, [&](int i) { return i < kl ? V[i] : 0u; }, 0u);
+      lq = prec(b, W, lq);
+    }
+    lr = K1;
   }
-  // ---- r = u - m (into P, in place)
-  addsub<true>(b, P, h, [&](int i) { return U[i]; }, [&](int i) { return i < nm ? P[i] : 0u; }, 0u);
-  int lr = prec(b, P, h);
   // ---- if r >= v: q += 1, r -= v   (Theorem 2: delta = +1)
+  lr = prec(b, P, lr);
   for (int t = 0;; t++) {
     if (cmp(b, P, lr, V, kl) < 0) break;
     if (t == 2) return ST_CORR;

@@ -74,6 +74,79 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_ragged(RaggedArgs a) {
   }
 }
 
+// Persistent launch that splits itself for smaller items. The block starts as
+// one group of all its warps over all of its dynamic shared memory and takes
+// items largest-first from the queue. When a group draws an item that fits in
+// half of its shared memory and wants at most half of its warps (a.split_digits
+// gives the largest dividend per warp count), the group splits into two
+// independent halves, each with its own named barrier and scratch: the first
+// half divides the drawn item, the second draws the next one. Groups split down
+// to kMinGroupWarps warps. Results are those of the plain launch: the division
+// code is the same, only the number of cooperating warps differs.
+constexpr int kMinGroupWarps = 4;
+constexpr int kMaxGroups = 7;  // binary tree of groups: 16 -> 8 -> 4 warps
+
+template <int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_div_persistent(RaggedArgs a) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ int red[kMaxGroups][RED_WORDS];
+  int node = 0, w0 = 0, nw = NW;
+  uint32_t* base = sm;
+  int words = a.smem_words;
+  int pending = -1;
+  while (true) {
+    const Blk b = make_group(red[node], w0, nw, node);
+    int idx;
+    if (pending >= 0) {
+      idx = pending;
+      pending = -1;
+    } else {
+      if (b.tid == 0) b.red[RED_AUX] = atomicAdd(a.head, 1);
+      b.sync();
+      idx = b.red[RED_AUX];
+      b.sync();
+    }
+    if ((int64_t)idx >= a.n) break;
+    const int item = a.order[idx];
+    const int ul = a.u_len[item];
+    const int half_words = (words / 2) & ~3;
+    const int want = ul <= a.split_digits[0] ? 4 : (ul <= a.split_digits[1] ? 8 : 16);
+    if (nw >= 2 * kMinGroupWarps && 2 * node + 2 < kMaxGroups && want <= nw / 2 &&
+        smem_words_for(ul) <= half_words) {
+      const bool left = b.warp < nw / 2;
+      node = 2 * node + (left ? 1 : 2);
+      nw /= 2;
+      if (!left) {
+        w0 += nw;
+        base += half_words;
+      }
+      words = half_words;
+      if (left) pending = idx;
+      continue;
+    }
+    ItemIO io;
+    io.u = a.u + a.u_off[item];
+    io.un = ul;
+    io.v = a.v + a.v_off[item];
+    io.vn = a.v_len[item];
+    io.q = a.q + a.q_off[item];
+    io.qn = a.q_len[item];
+    io.r = a.r + a.r_off[item];
+    io.rn = a.r_len[item];
+    int it = 0;
+    unsigned long long work = 0ull;
+    Blk bw = b;
+    bw.work = a.products ? &work : nullptr;
+    const int st = div_item(bw, base, words, io, a.flags, &it, nullptr, 0, 0);
+    if (b.tid == 0) {
+      a.status[item] = st;
+      if (a.iters) a.iters[item] = it;
+      if (a.products) a.products[item] = (int64_t)work;
+    }
+    b.sync();
+  }
+}
+
 // Test entry: shinv_h(v) as the division path computes it.
 template <int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_shinv(ShinvArgs a) {

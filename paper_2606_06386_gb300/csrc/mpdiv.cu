@@ -34,11 +34,12 @@ struct Kern {
   }
 };
 
-enum KernKind { KK_UNIFORM = 0, KK_RAGGED = 1, KK_SHINV = 2 };
+enum KernKind { KK_UNIFORM = 0, KK_RAGGED = 1, KK_SHINV = 2, KK_PERSIST = 3 };
 
 // Instantiations by block size; the minimum-blocks bound caps registers at 64
 // per thread so that several blocks of the smaller size classes share an SM.
 void* kernel_for(KernKind kk, int warps) {
+  if (kk == KK_PERSIST) return (void*)k_div_persistent<16, 1>;  // splits itself: always 16 warps
   if (warps <= 4) return Kern<128, 8>::get(kk);
   if (warps <= 8) return Kern<256, 4>::get(kk);
   if (warps <= 16) return Kern<512, 2>::get(kk);
@@ -228,8 +229,8 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
   const int smem = mpdiv_smem_bytes(max_u);
   if (smem > ctx->max_smem)
     return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory", smem);
-  const int warps = L.warps > 0 ? L.warps : mpdiv_default_warps(ctx, max_u);
-  void* k = kernel_for(KK_RAGGED, warps);
+  const int warps = L.split ? 16 : (L.warps > 0 ? L.warps : mpdiv_default_warps(ctx, max_u));
+  void* k = kernel_for(L.split ? KK_PERSIST : KK_RAGGED, warps);
   int rc = prepare_kernel(ctx, k, smem);
   if (rc) return rc;
   // size-sorted order (cached by content of the shape list)
@@ -245,7 +246,12 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
     std::iota(order.begin(), order.end(), 0);
     std::vector<double> cost(L.n);
     for (int64_t i = 0; i < L.n; i++) cost[i] = item_cost(L.u_len_host[i], L.v_len_host[i]);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    // largest dividend first (shared-memory need, which decides when a block
+    // splits), then the most expensive division first
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      if (L.u_len_host[a] != L.u_len_host[b]) return L.u_len_host[a] > L.u_len_host[b];
+      return cost[a] > cost[b];
+    });
     if ((size_t)L.n > ctx->order_cap) {
       if (ctx->d_order) cudaFree(ctx->d_order);
       ctx->d_order = nullptr;
@@ -290,6 +296,8 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
   a.n = L.n;
   a.smem_words = smem / 4;
   a.flags = ctx->cfg.flags;
+  a.split_digits[0] = ctx->split_digits[0];
+  a.split_digits[1] = ctx->split_digits[1];
   if (!L.use_graph) {
     if ((rc = mpdiv_cuda_check(ctx, cudaMemsetAsync(a.head, 0, sizeof(int32_t), stream), "queue reset"))) return rc;
     void* args[] = {&a};
@@ -375,6 +383,7 @@ extern "C" int mpdiv_batch_ragged(mpdiv_ctx* ctx, int64_t n_items, const uint32_
   L.v_len_host = v_len_host;
   L.n = n_items;
   L.use_graph = true;
+  L.split = true;
   return mpdiv_launch_ragged(ctx, L, (cudaStream_t)stream);
 }
 

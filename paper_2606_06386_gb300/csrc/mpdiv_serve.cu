@@ -1,22 +1,26 @@
 // Continuous-batching server for divisions of mixed precision.
 //
-// A scheduler thread owns a device operand pool and a pinned host mirror of
-// it. Requests are admitted first-in first-out into batches: each batch takes
-// one contiguous range of the pool holding its operands, its per-item
-// offsets, lengths and queue order (largest first), its queue head and its
-// results. A batch is one host-to-device copy, one launch of the persistent
-// division kernel with one block per item (so blocks of the next batch fill
-// SMs as blocks of the current one retire), and one device-to-host copy, on
-// its own stream. Up to max_inflight batches run at once; requests that arrive
-// meanwhile wait for the next free slot and pool range. The kernel is the
-// same division path as the plain launch, so a result does not depend on the
-// batch an item lands in.
+// Operands travel through two pinned host rings mirrored on the device: an
+// input ring (u and v of every request, in arrival order) and an output ring
+// (q and r of every launched request). mpdiv_serve_submit reserves the
+// request's digits at the tail of the input ring and copies its operands there
+// itself, outside the server lock. A scheduler thread turns the oldest ready
+// requests into a batch: a contiguous run of the input ring (one host-to-device
+// copy), per-item offsets and a largest-first order (one more copy), one launch
+// per dividend size class (each sized for its class, one block per item, so
+// blocks of the next batch fill SMs as blocks of this one retire), and one
+// device-to-host copy of the batch's results, all on the batch's own stream.
+// Up to max_inflight batches run at once. While fewer than low_water requests
+// are on the GPU, queued requests launch at once; under load they gather into
+// larger batches (up to max_batch, or until the oldest has waited max_wait_us).
+// The kernel is the division path of the plain launch, so a result does not
+// depend on the batch a request lands in.
 #include <algorithm>
 #include <atomic>
-#include <map>
 #include <chrono>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <numeric>
 #include <thread>
@@ -36,297 +40,285 @@ int64_t now_ns() {
 enum ReqState { RQ_QUEUED = 0, RQ_RUNNING = 1, RQ_DONE = 2 };
 
 struct Request {
-  uint64_t ticket;
-  int32_t u_len, v_len, q_len, r_len;
-  std::vector<uint32_t> u, v;  // operands until launch
-  std::vector<uint32_t> q, r;  // results once done
+  uint64_t ticket = 0;
+  int32_t u_len = 0, v_len = 0, q_len = 0, r_len = 0;
+  int64_t in_off = -1;            // u at in_off, v at in_off + u_len (input ring digits)
+  int64_t in_seq = -1;            // its input-ring allocation
+  std::atomic<int> ready{0};      // operands copied into the ring
+  std::vector<uint32_t> q, r;     // results once done
   int32_t status = 0;
   int state = RQ_QUEUED;
   int64_t t_submit = 0, t_done = 0;
 };
 
-// first-fit allocator over [0, size) in digit units; ranges are 4-digit aligned
-struct RangeAlloc {
-  std::map<int64_t, int64_t> free_;  // offset -> length
-  explicit RangeAlloc(int64_t size = 0) {
-    if (size > 0) free_[0] = size;
-  }
-  int64_t largest() const {
-    int64_t m = 0;
-    for (auto& kv : free_) m = std::max(m, kv.second);
-    return m;
-  }
-  int64_t alloc(int64_t n) {
+// Ring allocator in digits with first-in first-out release; an allocation
+// that would cross the end starts again at 0 and the skipped tail counts as
+// used until it is released with its allocation.
+struct Ring {
+  int64_t cap = 0, tail = 0, used = 0;
+  struct Entry {
+    int64_t len;  // includes any skipped gap before the allocation
+    bool done;
+  };
+  std::deque<Entry> live;
+  int64_t front_seq = 0;  // sequence number of live.front()
+  // returns the offset (or -1) and the allocation's sequence number in *seq
+  int64_t alloc(int64_t n, int64_t* seq) {
     n = (n + 3) & ~int64_t(3);
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= n) {
-        const int64_t off = it->first, len = it->second;
-        free_.erase(it);
-        if (len > n) free_[off + n] = len - n;
-        return off;
-      }
+    if (n > cap) return -1;
+    int64_t off = tail, gap = 0;
+    if (off + n > cap) {
+      gap = cap - off;
+      off = 0;
     }
-    return -1;
+    if (used + gap + n > cap) return -1;
+    tail = off + n;
+    if (tail == cap) tail = 0;
+    used += gap + n;
+    *seq = front_seq + (int64_t)live.size();
+    live.push_back({gap + n, false});
+    return off;
   }
-  void release(int64_t off, int64_t n) {
-    n = (n + 3) & ~int64_t(3);
-    auto it = free_.emplace(off, n).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
+  // mark allocation `seq` finished, then free finished ones from the front
+  void release(int64_t seq) {
+    live[(size_t)(seq - front_seq)].done = true;
+    while (!live.empty() && live.front().done) {
+      used -= live.front().len;
+      live.pop_front();
+      front_seq++;
     }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
-      }
+    if (live.empty()) {
+      tail = 0;
+      used = 0;
     }
   }
 };
 
-// digits needed by a batch of requests: operands, metadata (int64 offsets as
-// two digits), head, results
-int64_t batch_layout(const std::vector<Request*>& rs, std::vector<int64_t>& offs) {
-  const int64_t n = (int64_t)rs.size();
-  int64_t a = 0;
-  offs.assign(16, 0);
-  offs[0] = a;  // u digits
-  for (auto* r : rs) a += r->u_len;
-  a = (a + 3) & ~3;
-  offs[1] = a;  // v digits
-  for (auto* r : rs) a += r->v_len;
-  a = (a + 3) & ~3;
-  offs[2] = a;  // u_off, v_off, q_off, r_off: int64 each
-  a += 4 * 2 * n;
-  offs[3] = a;  // u_len, v_len, q_len, r_len, order: int32 each
-  a += 5 * n;
-  offs[4] = a;  // head (+ padding)
-  a += 4;
-  offs[5] = a;  // end of what is copied to the device
-  a = (a + 3) & ~3;
-  offs[6] = a;  // status
-  a += n;
-  a = (a + 3) & ~3;
-  offs[7] = a;  // q digits
-  for (auto* r : rs) a += r->q_len;
-  a = (a + 3) & ~3;
-  offs[8] = a;  // r digits
-  for (auto* r : rs) a += r->r_len;
-  offs[9] = a;  // total
-  return a;
-}
+int size_class(int32_t ul) { return ul <= 1024 ? 0 : ul <= 2048 ? 1 : ul <= 4096 ? 2 : 3; }
 
 }  // namespace
 
 struct MpServer {
-  mpdiv_ctx* ctx;
-  mpdiv_serve_config cfg;
-  uint32_t* d_pool = nullptr;
-  uint32_t* h_pool = nullptr;  // pinned mirror
-  RangeAlloc alloc;
+  mpdiv_ctx* ctx = nullptr;
+  mpdiv_serve_config cfg{};
+  uint32_t *d_in = nullptr, *h_in = nullptr, *d_out = nullptr, *h_out = nullptr;
+  Ring in_ring, out_ring;
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
   std::deque<Request*> queue;
   std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
   uint64_t next_ticket = 1;
-  int64_t pending = 0;  // queued + running
+  int64_t pending = 0, inflight_items = 0;
   bool stopping = false, quit = false;
-  std::thread th;
+  int sched_error = 0;
   int64_t completed = 0, launches = 0, batched_items = 0;
+  std::thread th;
   struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
+    uint32_t *h_meta = nullptr, *d_meta = nullptr;  // offsets, lengths, order, heads, status
     bool busy = false;
-    int64_t range_off = 0, range_len = 0;
+    int64_t out_off = -1, out_seq = -1;
     std::vector<Request*> reqs;
-    std::vector<int64_t> offs;
   };
   std::vector<Slot> slots;
-  int sched_error = 0;
+  int64_t meta_words = 0;
 
   void run();
-  bool launch(Slot& s, std::vector<Request*>& batch, int64_t off, int64_t len);
-  void finish(Slot& s);
+  bool launch(Slot& s);
 };
 
-bool MpServer::launch(Slot& s, std::vector<Request*>& batch, int64_t off, int64_t len) {
-  const int64_t n = (int64_t)batch.size();
-  std::vector<int64_t> o;
-  batch_layout(batch, o);
-  uint32_t* H = h_pool + off;
-  uint32_t* D = d_pool + off;
-  int64_t* h_off = reinterpret_cast<int64_t*>(H + o[2]);
-  int32_t* h_len = reinterpret_cast<int32_t*>(H + o[3]);
-  int64_t pu = o[0], pv = o[1], pq = o[7], pr = o[8];
+// metadata layout of a slot for n items: int64 offsets (u, v, q, r) as digit
+// pairs, int32 lengths (u, v, q, r), order, queue heads, status
+static int64_t meta_words_for(int64_t n) { return 8 * n + 5 * n + 8 + n + 8; }
+
+bool MpServer::launch(Slot& s) {
+  const int64_t n = (int64_t)s.reqs.size();
+  uint32_t* H = s.h_meta;
+  int64_t* h_off = reinterpret_cast<int64_t*>(H);
+  int32_t* h_len = reinterpret_cast<int32_t*>(H + 8 * n);
+  int32_t* order = h_len + 4 * n;
+  int32_t* heads = order + n;
+  const int64_t status_w = 13 * n + 8;  // status after the heads
   std::vector<double> cost(n);
+  int64_t pq = s.out_off;
   for (int64_t i = 0; i < n; i++) {
-    Request* r = batch[i];
-    std::memcpy(H + pu, r->u.data(), 4 * (size_t)r->u_len);
-    std::memcpy(H + pv, r->v.data(), 4 * (size_t)r->v_len);
-    h_off[0 * n + i] = pu - o[0];
-    h_off[1 * n + i] = pv - o[1];
-    h_off[2 * n + i] = pq - o[7];
-    h_off[3 * n + i] = pr - o[8];
-    h_len[0 * n + i] = r->u_len;
-    h_len[1 * n + i] = r->v_len;
+    Request* r = s.reqs[i];
+    h_off[i] = r->in_off;
+    h_off[n + i] = r->in_off + r->u_len;
+    h_off[2 * n + i] = pq;
+    h_off[3 * n + i] = pq + r->q_len;
+    pq += r->q_len + r->r_len;
+    h_len[i] = r->u_len;
+    h_len[n + i] = r->v_len;
     h_len[2 * n + i] = r->q_len;
     h_len[3 * n + i] = r->r_len;
-    pu += r->u_len;
-    pv += r->v_len;
-    pq += r->q_len;
-    pr += r->r_len;
     const double a = std::max(1, r->u_len - r->v_len + 1);
     cost[i] = a * (r->u_len + r->v_len) + 2.0 * a * std::min<double>(a, r->v_len);
-    r->u.clear();
-    r->u.shrink_to_fit();
-    r->v.clear();
-    r->v.shrink_to_fit();
-    r->state = RQ_RUNNING;
   }
-  int32_t* order = h_len + 4 * n;
   std::iota(order, order + n, 0);
-  std::stable_sort(order, order + n, [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
-  std::memset(H + o[4], 0, 16);  // queue head
-  cudaError_t e = cudaMemcpyAsync(D, H, 4 * (size_t)o[5], cudaMemcpyHostToDevice, s.stream);
-  std::vector<int32_t> ulh(n), vlh(n);
-  for (int64_t i = 0; i < n; i++) {
-    ulh[i] = batch[i]->u_len;
-    vlh[i] = batch[i]->v_len;
+  std::stable_sort(order, order + n, [&](int32_t a, int32_t b) {
+    const int ca = size_class(s.reqs[a]->u_len), cb = size_class(s.reqs[b]->u_len);
+    if (ca != cb) return ca > cb;
+    return cost[a] > cost[b];
+  });
+  std::memset(heads, 0, 8 * sizeof(int32_t));
+  // operands: one contiguous run of the input ring
+  const int64_t in_lo = s.reqs.front()->in_off;
+  const int64_t in_hi = s.reqs.back()->in_off + s.reqs.back()->u_len + s.reqs.back()->v_len;
+  cudaError_t e = cudaMemcpyAsync(d_in + in_lo, h_in + in_lo, 4 * (size_t)(in_hi - in_lo), cudaMemcpyHostToDevice,
+                                  s.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_meta, H, 4 * (size_t)status_w, cudaMemcpyHostToDevice, s.stream);
+  const int64_t* d_off = reinterpret_cast<const int64_t*>(s.d_meta);
+  const int32_t* d_len = reinterpret_cast<const int32_t*>(s.d_meta + 8 * n);
+  int32_t* d_status = reinterpret_cast<int32_t*>(s.d_meta + status_w);
+  int rc = (e == cudaSuccess) ? MPDIV_OK : MPDIV_ECUDA;
+  for (int64_t beg = 0; beg < n && rc == MPDIV_OK;) {
+    const int c = size_class(s.reqs[order[beg]]->u_len);
+    int64_t end = beg;
+    std::vector<int32_t> ulh;
+    while (end < n && size_class(s.reqs[order[end]]->u_len) == c) ulh.push_back(s.reqs[order[end++]]->u_len);
+    RaggedLaunch L{};
+    L.u = d_in;
+    L.u_off = d_off;
+    L.u_len = d_len;
+    L.v = d_in;
+    L.v_off = d_off + n;
+    L.v_len = d_len + n;
+    L.q = d_out;
+    L.q_off = d_off + 2 * n;
+    L.q_len = d_len + 2 * n;
+    L.r = d_out;
+    L.r_off = d_off + 3 * n;
+    L.r_len = d_len + 3 * n;
+    L.status = d_status;
+    L.u_len_host = ulh.data();
+    L.v_len_host = ulh.data();
+    L.order = d_len + 4 * n + beg;
+    L.head = const_cast<int32_t*>(d_len + 5 * n) + c;
+    L.n = end - beg;
+    L.use_graph = false;
+    L.grid_items = true;
+    rc = mpdiv_launch_ragged(ctx, L, s.stream);
+    beg = end;
   }
-  RaggedLaunch L{};
-  const int64_t* d_off = reinterpret_cast<const int64_t*>(D + o[2]);
-  const int32_t* d_len = reinterpret_cast<const int32_t*>(D + o[3]);
-  L.u = D + o[0];
-  L.u_off = d_off;
-  L.u_len = d_len;
-  L.v = D + o[1];
-  L.v_off = d_off + n;
-  L.v_len = d_len + n;
-  L.q = D + o[7];
-  L.q_off = d_off + 2 * n;
-  L.q_len = d_len + 2 * n;
-  L.r = D + o[8];
-  L.r_off = d_off + 3 * n;
-  L.r_len = d_len + 3 * n;
-  L.status = reinterpret_cast<int32_t*>(D + o[6]);
-  L.iters = nullptr;
-  L.u_len_host = ulh.data();
-  L.v_len_host = vlh.data();
-  L.order = d_len + 4 * n;
-  L.head = reinterpret_cast<int32_t*>(D + o[4]);
-  L.n = n;
-  L.use_graph = false;
-  L.grid_items = true;
-  int rc = (e == cudaSuccess) ? mpdiv_launch_ragged(ctx, L, s.stream) : MPDIV_ECUDA;
   if (rc == MPDIV_OK)
-    e = cudaMemcpyAsync(H + o[6], D + o[6], 4 * (size_t)(o[9] - o[6]), cudaMemcpyDeviceToHost, s.stream);
+    e = cudaMemcpyAsync(h_out + s.out_off, d_out + s.out_off, 4 * (size_t)(pq - s.out_off), cudaMemcpyDeviceToHost,
+                        s.stream);
+  if (rc == MPDIV_OK && e == cudaSuccess)
+    e = cudaMemcpyAsync(H + status_w, d_status, 4 * (size_t)n, cudaMemcpyDeviceToHost, s.stream);
   if (rc == MPDIV_OK && e == cudaSuccess) e = cudaEventRecord(s.ev, s.stream);
-  if (rc != MPDIV_OK || e != cudaSuccess) {
-    // the operands are consumed: fail these requests instead of requeueing them
-    sched_error = rc != MPDIV_OK ? rc : MPDIV_ECUDA;
-    const int64_t t = now_ns();
-    for (Request* r : batch) {
-      r->q.assign(r->q_len, 0u);
-      r->r.assign(r->r_len, 0u);
-      r->status = MPDIV_ST_INTERNAL;
-      r->state = RQ_DONE;
-      r->t_done = t;
-    }
-    pending -= n;
-    cv_done.notify_all();
-    return false;
-  }
-  s.busy = true;
-  s.range_off = off;
-  s.range_len = len;
-  s.reqs = batch;
-  s.offs = o;
-  launches++;
-  batched_items += n;
-  return true;
-}
-
-void MpServer::finish(Slot& s) {
-  const std::vector<int64_t>& o = s.offs;
-  const uint32_t* H = h_pool + s.range_off;
-  const int32_t* st = reinterpret_cast<const int32_t*>(H + o[6]);
-  int64_t pq = o[7], pr = o[8];
-  const int64_t t = now_ns();
-  for (size_t i = 0; i < s.reqs.size(); i++) {
-    Request* r = s.reqs[i];
-    r->q.assign(H + pq, H + pq + r->q_len);
-    r->r.assign(H + pr, H + pr + r->r_len);
-    pq += r->q_len;
-    pr += r->r_len;
-    r->status = st[i];
-    r->state = RQ_DONE;
-    r->t_done = t;
-  }
-  completed += (int64_t)s.reqs.size();
-  pending -= (int64_t)s.reqs.size();
-  alloc.release(s.range_off, s.range_len);
-  s.reqs.clear();
-  s.busy = false;
+  return rc == MPDIV_OK && e == cudaSuccess;
 }
 
 void MpServer::run() {
   cudaSetDevice(ctx->device);
-  std::unique_lock<std::mutex> lk(mu);
+  std::vector<Slot*> finished;
   while (true) {
-    bool progressed = false;
-    int busy = 0;
-    for (auto& s : slots) {
-      if (!s.busy) continue;
-      if (cudaEventQuery(s.ev) == cudaSuccess) {
-        finish(s);
-        progressed = true;
-      } else {
-        busy++;
+    // ---- completions: copy results out without the lock, then publish
+    finished.clear();
+    for (auto& s : slots)
+      if (s.busy && cudaEventQuery(s.ev) == cudaSuccess) finished.push_back(&s);
+    for (Slot* s : finished) {
+      const int64_t n = (int64_t)s->reqs.size();
+      const int32_t* st = reinterpret_cast<const int32_t*>(s->h_meta + 13 * n + 8);
+      int64_t pq = s->out_off;
+      for (int64_t i = 0; i < n; i++) {
+        Request* r = s->reqs[i];
+        r->q.assign(h_out + pq, h_out + pq + r->q_len);
+        r->r.assign(h_out + pq + r->q_len, h_out + pq + r->q_len + r->r_len);
+        pq += r->q_len + r->r_len;
+        r->status = st[i];
       }
     }
-    if (progressed) cv_done.notify_all();
-    // admit the next batch into a free slot
-    Slot* free_slot = nullptr;
-    for (auto& s : slots)
-      if (!s.busy) {
-        free_slot = &s;
-        break;
+    std::unique_lock<std::mutex> lk(mu);
+    const int64_t t = now_ns();
+    for (Slot* s : finished) {
+      for (Request* r : s->reqs) {
+        r->state = RQ_DONE;
+        r->t_done = t;
+        in_ring.release(r->in_seq);
       }
-    if (free_slot && !queue.empty() && sched_error == 0) {
-      std::vector<Request*> batch;
-      std::vector<int64_t> o;
-      const int64_t room = alloc.largest();
-      while (!queue.empty() && (int)batch.size() < cfg.max_batch) {
-        batch.push_back(queue.front());
-        if (batch_layout(batch, o) > room) {
-          batch.pop_back();
-          break;
-        }
+      out_ring.release(s->out_seq);
+      const int64_t n = (int64_t)s->reqs.size();
+      completed += n;
+      pending -= n;
+      inflight_items -= n;
+      s->reqs.clear();
+      s->busy = false;
+    }
+    if (!finished.empty()) cv_done.notify_all();
+    int busy = 0;
+    Slot* free_slot = nullptr;
+    for (auto& s : slots) {
+      if (s.busy)
+        busy++;
+      else if (!free_slot)
+        free_slot = &s;
+    }
+    // ---- admission
+    bool admit = false;
+    if (free_slot && !queue.empty() && queue.front()->ready.load(std::memory_order_acquire) && sched_error == 0) {
+      const int64_t waited_us = (t - queue.front()->t_submit) / 1000;
+      admit = inflight_items < cfg.low_water || (int64_t)queue.size() >= cfg.max_batch ||
+              waited_us >= cfg.max_wait_us || quit;
+    }
+    if (admit) {
+      // the oldest ready requests, contiguous in the input ring, within the output ring
+      std::vector<Request*>& b = free_slot->reqs;
+      int64_t out_need = 0;
+      const int64_t out_room = out_ring.cap - out_ring.used - 4;
+      while (!queue.empty() && (int64_t)b.size() < cfg.max_batch) {
+        Request* r = queue.front();
+        if (!r->ready.load(std::memory_order_acquire)) break;
+        if (!b.empty() && r->in_off != b.back()->in_off + ((b.back()->u_len + b.back()->v_len + 3) & ~3)) break;
+        const int64_t need = r->q_len + r->r_len;
+        if (out_need + need > out_room) break;
+        out_need += need;
+        b.push_back(r);
         queue.pop_front();
       }
-      if (!batch.empty()) {
-        const int64_t len = batch_layout(batch, o);
-        const int64_t off = alloc.alloc(len);
-        if (off < 0) {
-          for (auto it = batch.rbegin(); it != batch.rend(); ++it) queue.push_front(*it);
-        } else if (launch(*free_slot, batch, off, len)) {
-          progressed = true;
-          busy++;
-        } else {
-          alloc.release(off, len);
-          progressed = true;
+      int64_t oseq = -1;
+      const int64_t off = b.empty() ? -1 : out_ring.alloc(out_need, &oseq);
+      if (off < 0) {
+        for (auto it = b.rbegin(); it != b.rend(); ++it) queue.push_front(*it);
+        b.clear();
+      } else {
+        free_slot->out_off = off;
+        free_slot->out_seq = oseq;
+        free_slot->busy = true;
+        for (Request* r : b) r->state = RQ_RUNNING;
+        const int64_t nb = (int64_t)b.size();
+        inflight_items += nb;
+        launches++;
+        batched_items += nb;
+        lk.unlock();
+        const bool ok = launch(*free_slot);
+        lk.lock();
+        if (!ok) {  // fail these requests and refuse further work
+          sched_error = MPDIV_ECUDA;
+          const int64_t tf = now_ns();
+          for (Request* r : b) {
+            r->q.assign(r->q_len, 0u);
+            r->r.assign(r->r_len, 0u);
+            r->status = MPDIV_ST_INTERNAL;
+            r->state = RQ_DONE;
+            r->t_done = tf;
+            in_ring.release(r->in_seq);
+          }
+          out_ring.release(oseq);
+          pending -= nb;
+          inflight_items -= nb;
+          b.clear();
+          free_slot->busy = false;
+          cv_done.notify_all();
         }
+        continue;
       }
     }
     if (quit && busy == 0 && (queue.empty() || sched_error)) break;
-    if (!progressed) {
-      if (busy > 0)
-        cv_sched.wait_for(lk, std::chrono::microseconds(20));
-      else
-        cv_sched.wait_for(lk, std::chrono::milliseconds(5));
-    }
+    cv_sched.wait_for(lk, (busy > 0 || !queue.empty()) ? std::chrono::microseconds(20)
+                                                       : std::chrono::microseconds(5000));
   }
 }
 
@@ -345,32 +337,36 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
   cudaSetDevice(ctx->device);
   auto* S = new MpServer();
   S->ctx = ctx;
-  S->cfg = cfg ? *cfg : mpdiv_serve_config{0, 0, 0, 0};
+  if (cfg) S->cfg = *cfg;
   if (S->cfg.pool_digits <= 0) S->cfg.pool_digits = 64ll << 20;
   if (S->cfg.max_batch <= 0) S->cfg.max_batch = 4096;
-  if (S->cfg.max_inflight <= 0) S->cfg.max_inflight = 3;
+  if (S->cfg.max_inflight <= 0) S->cfg.max_inflight = 16;
   if (S->cfg.max_pending <= 0) S->cfg.max_pending = 1 << 20;
-  int rc = mpdiv_cuda_check(ctx, cudaMalloc(&S->d_pool, 4 * (size_t)S->cfg.pool_digits), "server pool");
-  if (rc == MPDIV_OK)
-    rc = mpdiv_cuda_check(ctx, cudaMallocHost(&S->h_pool, 4 * (size_t)S->cfg.pool_digits), "server host pool");
-  if (rc != MPDIV_OK) {
-    cudaFree(S->d_pool);
-    delete S;
-    return rc;
-  }
-  S->alloc = RangeAlloc(S->cfg.pool_digits);
+  if (S->cfg.low_water <= 0) S->cfg.low_water = 1024;
+  if (S->cfg.max_wait_us <= 0) S->cfg.max_wait_us = 2000;
+  const int64_t half = (S->cfg.pool_digits / 2) & ~int64_t(3);
+  S->in_ring.cap = half;
+  S->out_ring.cap = half;
+  S->meta_words = meta_words_for(S->cfg.max_batch);
+  int rc = mpdiv_cuda_check(ctx, cudaMalloc(&S->d_in, 4 * (size_t)half), "server input ring");
+  if (!rc) rc = mpdiv_cuda_check(ctx, cudaMalloc(&S->d_out, 4 * (size_t)half), "server output ring");
+  if (!rc) rc = mpdiv_cuda_check(ctx, cudaMallocHost(&S->h_in, 4 * (size_t)half), "server pinned input ring");
+  if (!rc) rc = mpdiv_cuda_check(ctx, cudaMallocHost(&S->h_out, 4 * (size_t)half), "server pinned output ring");
   S->slots.resize(S->cfg.max_inflight);
   for (auto& s : S->slots) {
-    cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
-    cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
+    if (rc) break;
+    rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking), "server stream");
+    if (!rc) rc = mpdiv_cuda_check(ctx, cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming), "server event");
+    if (!rc) rc = mpdiv_cuda_check(ctx, cudaMallocHost(&s.h_meta, 4 * (size_t)S->meta_words), "server metadata");
+    if (!rc) rc = mpdiv_cuda_check(ctx, cudaMalloc(&s.d_meta, 4 * (size_t)S->meta_words), "server metadata");
   }
   ctx->server = S;
+  if (rc) {
+    mpdiv_serve_shutdown(ctx);
+    return rc;
+  }
   S->th = std::thread([S] { S->run(); });
   return MPDIV_OK;
-}
-
-static int64_t footprint(int32_t u_len, int32_t v_len) {
-  return 2 * (int64_t)u_len + 2 * (int64_t)v_len + 16 + 16;
 }
 
 extern "C" int mpdiv_serve_submit(mpdiv_ctx* ctx, const uint32_t* u_host, int32_t u_len, const uint32_t* v_host,
@@ -381,26 +377,34 @@ extern "C" int mpdiv_serve_submit(mpdiv_ctx* ctx, const uint32_t* u_host, int32_
   if (u_len < 1 || v_len < 1) return mpdiv_set_error(ctx, MPDIV_EINVAL, "digit counts must be positive");
   if (u_len > MPDIV_MAX_LIMBS || v_len > MPDIV_MAX_LIMBS)
     return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "at most %d digits", MPDIV_MAX_LIMBS);
-  if (footprint(u_len, v_len) > S->cfg.pool_digits)
-    return mpdiv_set_error(ctx, MPDIV_EBUSY, "request larger than the device pool");
+  if (2 * (int64_t)(u_len + v_len) + 8 > S->in_ring.cap)
+    return mpdiv_set_error(ctx, MPDIV_EBUSY, "request larger than the server's rings");
   auto r = std::make_unique<Request>();
   r->u_len = u_len;
   r->v_len = v_len;
   r->q_len = u_len;  // enough for any quotient
   r->r_len = v_len;
-  r->u.assign(u_host, u_host + u_len);
-  r->v.assign(v_host, v_host + v_len);
+  Request* rp = r.get();
   {
     std::lock_guard<std::mutex> g(S->mu);
     if (S->stopping) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server stopping");
     if (S->pending >= S->cfg.max_pending) return MPDIV_EBUSY;
+    int64_t seq = -1;
+    const int64_t off = S->in_ring.alloc(u_len + v_len, &seq);
+    if (off < 0) return MPDIV_EBUSY;  // input ring full: retry later
+    r->in_off = off;
+    r->in_seq = seq;
     r->ticket = S->next_ticket++;
     r->t_submit = now_ns();
     *ticket = r->ticket;
-    S->queue.push_back(r.get());
-    S->reqs.emplace(r->ticket, std::move(r));
+    S->queue.push_back(rp);
+    S->reqs.emplace(rp->ticket, std::move(r));
     S->pending++;
   }
+  // the operands go straight into the pinned ring; the scheduler waits for `ready`
+  std::memcpy(S->h_in + rp->in_off, u_host, 4 * (size_t)u_len);
+  std::memcpy(S->h_in + rp->in_off + u_len, v_host, 4 * (size_t)v_len);
+  rp->ready.store(1, std::memory_order_release);
   S->cv_sched.notify_one();
   return MPDIV_OK;
 }
@@ -409,35 +413,38 @@ static int poll_impl(mpdiv_ctx* ctx, uint64_t ticket, uint32_t* q_host, int32_t 
                      int32_t r_cap, int32_t* status, int64_t timeout_us, int64_t* t_done) {
   MpServer* S = ctx->server;
   if (!S) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server not running");
-  std::unique_lock<std::mutex> lk(S->mu);
-  auto it = S->reqs.find(ticket);
-  if (it == S->reqs.end()) return mpdiv_set_error(ctx, MPDIV_EINVAL, "unknown ticket");
-  Request* r = it->second.get();
-  if (r->state != RQ_DONE) {
-    if (timeout_us <= 0) return MPDIV_PENDING;
-    const auto until = Clock::now() + std::chrono::microseconds(timeout_us);
-    while (r->state != RQ_DONE) {
-      if (S->sched_error && r->state == RQ_QUEUED)
-        return mpdiv_set_error(ctx, S->sched_error, "the server stopped after a failed launch");
-      if (S->cv_done.wait_until(lk, until) == std::cv_status::timeout && r->state != RQ_DONE)
-        return MPDIV_ETIMEDOUT;
+  std::unique_ptr<Request> done;
+  {
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return mpdiv_set_error(ctx, MPDIV_EINVAL, "unknown ticket");
+    Request* r = it->second.get();
+    if (r->state != RQ_DONE) {
+      if (timeout_us <= 0) return MPDIV_PENDING;
+      const auto until = Clock::now() + std::chrono::microseconds(timeout_us);
+      while (r->state != RQ_DONE) {
+        if (S->sched_error && r->state == RQ_QUEUED)
+          return mpdiv_set_error(ctx, S->sched_error, "the server stopped after a failed launch");
+        if (S->cv_done.wait_until(lk, until) == std::cv_status::timeout && r->state != RQ_DONE)
+          return MPDIV_ETIMEDOUT;
+      }
     }
-  }
-  int qs = (int)r->q.size();
-  while (qs > 0 && r->q[qs - 1] == 0u) qs--;
-  if (q_host) {
-    if (qs > q_cap) return mpdiv_set_error(ctx, MPDIV_EINVAL, "q_cap too small (%d digits needed)", qs);
-    for (int i = 0; i < q_cap; i++) q_host[i] = i < qs ? r->q[i] : 0u;
-  }
-  if (r_host) {
+    int qs = (int)r->q.size();
+    while (qs > 0 && r->q[qs - 1] == 0u) qs--;
     int rs = (int)r->r.size();
     while (rs > 0 && r->r[rs - 1] == 0u) rs--;
-    if (rs > r_cap) return mpdiv_set_error(ctx, MPDIV_EINVAL, "r_cap too small");
-    for (int i = 0; i < r_cap; i++) r_host[i] = i < rs ? r->r[i] : 0u;
+    if (q_host && qs > q_cap) return mpdiv_set_error(ctx, MPDIV_EINVAL, "q_cap too small (%d digits needed)", qs);
+    if (r_host && rs > r_cap) return mpdiv_set_error(ctx, MPDIV_EINVAL, "r_cap too small");
+    done = std::move(it->second);
+    S->reqs.erase(it);
   }
+  const Request* r = done.get();
+  if (q_host)
+    for (int i = 0; i < q_cap; i++) q_host[i] = i < (int)r->q.size() ? r->q[i] : 0u;
+  if (r_host)
+    for (int i = 0; i < r_cap; i++) r_host[i] = i < (int)r->r.size() ? r->r[i] : 0u;
   if (status) *status = r->status;
   if (t_done) *t_done = r->t_done;
-  S->reqs.erase(it);
   return MPDIV_OK;
 }
 
@@ -484,9 +491,13 @@ void mpdiv_serve_shutdown(mpdiv_ctx* ctx) {
     if (s.stream) cudaStreamSynchronize(s.stream);
     if (s.ev) cudaEventDestroy(s.ev);
     if (s.stream) cudaStreamDestroy(s.stream);
+    if (s.h_meta) cudaFreeHost(s.h_meta);
+    if (s.d_meta) cudaFree(s.d_meta);
   }
-  cudaFree(S->d_pool);
-  cudaFreeHost(S->h_pool);
+  cudaFree(S->d_in);
+  cudaFree(S->d_out);
+  if (S->h_in) cudaFreeHost(S->h_in);
+  if (S->h_out) cudaFreeHost(S->h_out);
   delete S;
   ctx->server = nullptr;
 }
@@ -506,12 +517,16 @@ extern "C" int mpdiv_serve_replay(mpdiv_ctx* ctx, int64_t n, const int64_t* arri
   if (!ctx || !ctx->server || n < 0) return MPDIV_EINVAL;
   std::vector<uint64_t> tickets((size_t)n);
   std::vector<int64_t> t_arr((size_t)n);
-  int64_t rej = 0;
-  int err = MPDIV_OK;
+  std::atomic<int64_t> rej{0};
+  std::atomic<int> err{MPDIV_OK};
   const int64_t t0 = now_ns();
-  std::atomic<int64_t> submitted{0};
-  std::thread submitter([&] {
-    for (int64_t i = 0; i < n; i++) {
+  // several submitter threads (request i goes to thread i mod kSub) so that
+  // the offered rate is not capped by one thread's operand copies
+  constexpr int kSub = 4;
+  std::vector<std::atomic<int64_t>> sub_next(kSub);
+  for (auto& x : sub_next) x.store(0);
+  auto submitter_fn = [&](int tid) {
+    for (int64_t i = tid; i < n; i += kSub) {
       const int64_t due = t0 + arrival_ns[i];
       while (now_ns() < due) {
         const int64_t gap = due - now_ns();
@@ -522,18 +537,22 @@ extern "C" int mpdiv_serve_replay(mpdiv_ctx* ctx, int64_t n, const int64_t* arri
         const int rc = mpdiv_serve_submit(ctx, u + u_off[i], u_len[i], v + v_off[i], v_len[i], &tickets[i]);
         if (rc == MPDIV_OK) break;
         if (rc != MPDIV_EBUSY) {
-          err = rc;
+          int expect = MPDIV_OK;
+          err.compare_exchange_strong(expect, rc);
           tickets[i] = 0;
           break;
         }
         rej++;
         std::this_thread::sleep_for(std::chrono::microseconds(20));
       }
-      submitted.store(i + 1, std::memory_order_release);
+      sub_next[tid].store(i + kSub, std::memory_order_release);
     }
-  });
+  };
+  std::vector<std::thread> submitters;
+  for (int t = 0; t < kSub; t++) submitters.emplace_back(submitter_fn, t);
   for (int64_t i = 0; i < n; i++) {
-    while (submitted.load(std::memory_order_acquire) <= i) std::this_thread::sleep_for(std::chrono::microseconds(5));
+    while (sub_next[i % kSub].load(std::memory_order_acquire) <= i)
+      std::this_thread::sleep_for(std::chrono::microseconds(5));
     if (tickets[i] == 0) {
       status[i] = -1;
       latency_ns[i] = -1;
@@ -544,10 +563,16 @@ extern "C" int mpdiv_serve_replay(mpdiv_ctx* ctx, int64_t n, const int64_t* arri
     while ((rc = poll_impl(ctx, tickets[i], q + q_off[i], q_len[i], r + r_off[i], r_len[i], &status[i], 1000000,
                            &td)) == MPDIV_ETIMEDOUT) {
     }
-    if (rc != MPDIV_OK && err == MPDIV_OK) err = rc;
+    if (rc != MPDIV_OK) {
+      int expect = MPDIV_OK;
+      err.compare_exchange_strong(expect, rc);
+      status[i] = -1;
+      latency_ns[i] = -1;
+      continue;
+    }
     latency_ns[i] = td - t_arr[i];
   }
-  submitter.join();
-  if (rejected) *rejected = rej;
-  return err;
+  for (auto& th : submitters) th.join();
+  if (rejected) *rejected = rej.load();
+  return err.load();
 }

@@ -99,9 +99,11 @@ def test_shinv_equals_model_and_theorem2():
         assert I_[i] == tr.iterations
 
 
+@pytest.mark.parametrize("full", [False, True])
 @pytest.mark.parametrize("n,kl", [(64, 32), (300, 37), (1024, 512), (97, 96), (500, 2)])
-def test_product_counter_equals_model(n, kl):
-    # the kernel's count of algorithmic digit products equals the exact model's
+def test_product_counter_equals_model(n, kl, full):
+    # the kernel's count of algorithmic digit products equals the exact model's,
+    # for the paper's full products and for the clipped quotient/remainder
     import torch
     import paper_2606_06386_gb300 as mp
 
@@ -111,10 +113,27 @@ def test_product_counter_equals_model(n, kl):
     r = torch.zeros((4, kl), dtype=torch.int32, device="cuda:0")
     st = torch.zeros(4, dtype=torch.int32, device="cuda:0")
     pr = torch.zeros(4, dtype=torch.int64, device="cuda:0")
-    mp.mpdiv_batch(ctx(), dev(U), dev(V), q, r, st, None, pr)
+    mp.mpdiv_batch(ctx(flags=mp.MPDIV_FLAG_FULL_PRODUCTS if full else 0), dev(U), dev(V), q, r, st, None, pr)
     torch.cuda.synchronize()
     P = pr.cpu().numpy()
     for i in range(4):
         tr = M.Trace()
-        M.div(oracle.to_int(U[i]), oracle.to_int(V[i]), B, tr)
+        u, v = oracle.to_int(U[i]), oracle.to_int(V[i])
+        if full:
+            M.div(u, v, B, tr)
+        else:
+            assert M.div_clipped(u, v, B, tr) == divmod(u, v)
         assert P[i] == tr.digit_products()
+
+
+def test_full_products_mode_is_exact():
+    import paper_2606_06386_gb300 as mp
+
+    U, V, names = I.plain_1024(n_random=64)
+    Q, R, S, _ = run_uniform(U, V, flags=mp.MPDIV_FLAG_FULL_PRODUCTS)
+    Qo, Ro, So = oracle_uniform(U, V)
+    assert_same(Q, R, S, Qo, Ro, So, names)
+    U, V = I.sweep(8192, 4096, 8)
+    Q, R, S, _ = run_uniform(U, V, flags=mp.MPDIV_FLAG_FULL_PRODUCTS)
+    Qo, Ro, So = oracle_uniform(U, V)
+    assert_same(Q, R, S, Qo, Ro, So)

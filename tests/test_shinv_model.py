@@ -171,3 +171,36 @@ def test_product_sizes_stay_near_cost_model(n, kl):
     assert (q, r) == divmod(u, v)
     total = tr.digit_products()
     assert total <= 7 * n * (n + 1) / 2
+
+
+def test_clipped_division_is_exact_and_cheaper():
+    # Section 5's clipped products: the quotient from the top columns only and
+    # the remainder modulo B^(k+2); the corrections restore the exact result
+    rnd = random.Random(26)
+    for _ in range(300):
+        u, v = _rand_pair(rnd, 24)
+        tr = M.Trace()
+        assert M.div_clipped(u, v, B32, tr) == divmod(u, v)
+    n, kl = 512, 256
+    u = rnd.getrandbits(32 * n) | (1 << (32 * n - 1))
+    v = rnd.getrandbits(32 * kl) | (1 << (32 * kl - 1))
+    tf, tc = M.Trace(), M.Trace()
+    M.div(u, v, B32, tf)
+    M.div_clipped(u, v, B32, tc)
+    assert tc.digit_products() < 0.7 * tf.digit_products()
+
+
+def test_clipped_quotient_is_at_most_one_short():
+    rnd = random.Random(27)
+    for _ in range(200):
+        n = rnd.randint(3, 30)
+        kl = rnd.randint(2, n)
+        u = rnd.getrandbits(32 * n) | (1 << (32 * n - 1))
+        v = rnd.getrandbits(32 * kl) | (1 << (32 * kl - 1))
+        h = M.prec(u, B32)
+        w = M.shinv(v, h, B32)
+        lo = h - 2
+        low = sum(((w >> (32 * j)) & (B32 - 1)) * (u % B32 ** (lo - j)) * B32**j for j in range(M.prec(w, B32)) if lo - j > 0)
+        q_full = (u * w) // B32**h
+        q_clip = (u * w - low) // B32**h
+        assert q_full - q_clip in (0, 1)
