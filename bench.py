@@ -272,6 +272,7 @@ def run_sweep(args, dev, dist, rank, ws):
             "cost_units_per_div": d["products"] / d["b"] / (d["n"] * (d["n"] + 1) / 2),
             "Tprod_per_s": d["products"] / (per_size_ms[i] / 1e3) / 1e12,
             "warps_per_block": tuned[d["n"]],
+            "mul_columns": mp.mpdiv_tuning(ctx, d["n"])[1],
         }
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
@@ -463,7 +464,8 @@ def run_serve(args, dev, dist, rank, ws):
         r = np.zeros(int(R["r_len"].sum()), np.uint32)
         st = np.full(n_req, -9, np.int32)
         lat = np.zeros(n_req, np.int64)
-        mp.mpdiv_serve_start(ctx, pool_digits=256 << 20, max_batch=args.max_batch, max_inflight=args.max_inflight)
+        mp.mpdiv_serve_start(ctx, pool_digits=256 << 20, max_batch=args.max_batch, max_inflight=args.max_inflight,
+                             low_water=args.low_water)
         with ClockSampler(dev.index or 0) as clk:
             t0 = time.perf_counter()
             rej = mp.mpdiv_serve_replay(ctx, arr, R["u_flat"], uo, ul, R["v_flat"], vo, vl, q, qo, ul.copy(), r,
@@ -573,7 +575,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=200000, help="serve workload: number of requests")
     ap.add_argument("--max-batch", type=int, default=1024, help="serve workload: most requests per batch")
-    ap.add_argument("--max-inflight", type=int, default=16, help="serve workload: batches in flight")
+    ap.add_argument("--max-inflight", type=int, default=32, help="serve workload: batches in flight")
+    ap.add_argument("--low-water", type=int, default=2048, help="serve workload: requests on the GPU below "
+                    "which queued requests launch at once")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -67,6 +67,8 @@ typedef struct mpdiv_config {
   int warps_per_block; /* 0: per size class from the tuning table (mpdiv_autotune) */
   int blocks_per_sm;   /* persistent kernels: resident blocks per SM; 0: from occupancy */
   int flags;           /* MPDIV_FLAG_* */
+  int mul_columns;     /* output columns per lane of the strip multiply: 3, 5 or 7; 0: per
+                          size class from the tuning table */
 } mpdiv_config;
 
 /* Create a context on CUDA device `device` (cfg may be NULL for defaults).
@@ -124,10 +126,17 @@ int mpdiv_debug_shinv(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *v, int32_
                       int32_t *iters, int32_t *status, void *stream);
 
 /* Tuning: time the plain kernel for the given (u_limbs, v_limbs) shape at each
- * candidate block size on `n_items` synthetic divisions and keep the fastest in
- * the context's tuning table (used when cfg->warps_per_block == 0). Returns the
- * chosen warps per block (> 0) or a negative error code. Synchronous. */
+ * candidate block size (4, 8, 16, 32 warps) and strip width (3, 5, 7 columns
+ * per lane) on `n_items` synthetic divisions and keep the fastest in the
+ * context's tuning table for that size class (used where cfg leaves the
+ * choice open). Returns the chosen warps per block (> 0) or a negative error
+ * code. Synchronous. */
 int mpdiv_autotune(mpdiv_ctx *ctx, int32_t u_limbs, int32_t v_limbs, int32_t n_items);
+
+/* The launch shape the context uses for dividends of u_limbs digits: warps per
+ * block and output columns per lane of the strip multiply (tuned, configured
+ * or default). Either pointer may be NULL. */
+int mpdiv_tuning(mpdiv_ctx *ctx, int32_t u_limbs, int32_t *warps, int32_t *mul_columns);
 
 /* ---------------------------------------------------------------- serving
  * Continuous batching: a host scheduler thread admits submitted requests into
@@ -138,10 +147,10 @@ int mpdiv_autotune(mpdiv_ctx *ctx, int32_t u_limbs, int32_t v_limbs, int32_t n_i
 typedef struct mpdiv_serve_config {
   int64_t pool_digits;  /* digits of device operand/result pool (0: 64 Mi digits) */
   int32_t max_batch;    /* most requests per batch (0: 4096) */
-  int32_t max_inflight; /* batches in flight at once, each on its own stream (0: 16) */
+  int32_t max_inflight; /* batches in flight at once, each on its own stream (0: 32) */
   int32_t max_pending;  /* submitted-but-unfinished requests before EBUSY (0: 1<<20) */
   int32_t low_water;    /* below this many requests on the GPU, queued requests launch at
-                           once; above it they gather into larger batches (0: 1024) */
+                           once; above it they gather into larger batches (0: 2048) */
   int32_t max_wait_us;  /* longest a queued request waits for its batch to grow (0: 2000) */
 } mpdiv_serve_config;
 

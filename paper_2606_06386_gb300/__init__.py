@@ -22,7 +22,8 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 SO_PATH = os.path.join(_BUILD, "libmpdiv.so")
 HEADER = os.path.join(_ROOT, "include", "mpdiv.h")
-SOURCES = ["mpdiv.cu", "mpdiv_tune.cu", "mpdiv_serve.cu", "mpdiv_noalloc.cu"]
+SOURCES = ["mpdiv.cu", "mpdiv_tune.cu", "mpdiv_serve.cu", "mpdiv_noalloc.cu", "mpdiv_k4.cu", "mpdiv_k8.cu",
+           "mpdiv_k16.cu", "mpdiv_k32.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 # return codes and statuses (include/mpdiv.h)
@@ -77,7 +78,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 class mpdiv_config(ctypes.Structure):
-    _fields_ = [("warps_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("flags", ctypes.c_int)]
+    _fields_ = [("warps_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("flags", ctypes.c_int),
+                ("mul_columns", ctypes.c_int)]
 
 
 class mpdiv_serve_config(ctypes.Structure):
@@ -101,6 +103,7 @@ _SIGS = {
     "mpdiv_batch_ragged": (ctypes.c_int, [_P, _I64] + [_P] * 18),
     "mpdiv_debug_shinv": (ctypes.c_int, [_P, _I64, _P, _I32, _I64, _P, _P, _I32, _I64, _P, _P, _P]),
     "mpdiv_autotune": (ctypes.c_int, [_P, _I32, _I32, _I32]),
+    "mpdiv_tuning": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "mpdiv_serve_start": (ctypes.c_int, [_P, ctypes.POINTER(mpdiv_serve_config)]),
     "mpdiv_serve_submit": (ctypes.c_int, [_P, _P, _I32, _P, _I32, ctypes.POINTER(_U64)]),
     "mpdiv_serve_poll": (ctypes.c_int, [_P, _U64, _P, _I32, _P, _I32, ctypes.POINTER(_I32), _I64]),
@@ -169,8 +172,9 @@ def _check_dev(*ts):
 
 
 # ---------------------------------------------------------------- context
-def mpdiv_init(device: int = 0, warps_per_block: int = 0, blocks_per_sm: int = 0, flags: int = 0):
-    cfg = mpdiv_config(warps_per_block, blocks_per_sm, flags)
+def mpdiv_init(device: int = 0, warps_per_block: int = 0, blocks_per_sm: int = 0, flags: int = 0,
+               mul_columns: int = 0):
+    cfg = mpdiv_config(warps_per_block, blocks_per_sm, flags, mul_columns)
     h = _P()
     _check(None, lib().mpdiv_init(ctypes.byref(h), device, ctypes.byref(cfg)))
     return h
@@ -250,6 +254,13 @@ def mpdiv_debug_shinv(ctx, v, h_digits, out, iters, status, stream=None) -> None
 
 def mpdiv_autotune(ctx, u_limbs: int, v_limbs: int, n_items: int) -> int:
     return _check(ctx, lib().mpdiv_autotune(ctx, u_limbs, v_limbs, n_items))
+
+
+def mpdiv_tuning(ctx, u_limbs: int):
+    """(warps per block, columns per lane) used for dividends of u_limbs digits."""
+    w, t = _I32(), _I32()
+    _check(ctx, lib().mpdiv_tuning(ctx, u_limbs, ctypes.byref(w), ctypes.byref(t)))
+    return w.value, t.value
 
 
 # ---------------------------------------------------------------- serving

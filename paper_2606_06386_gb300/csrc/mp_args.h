@@ -16,6 +16,7 @@ struct UniformArgs {
   int un, vn, qn, rn;
   int smem_words;
   int flags;
+  int tcols;  // columns per lane of the strip multiply
 };
 
 struct RaggedArgs {
@@ -40,6 +41,9 @@ struct RaggedArgs {
   int smem_words;
   int flags;
   int split_digits[2];  // k_div_persistent: largest dividend for 4 and for 8 warps
+  int tcols;            // columns per lane (0 in k_div_persistent: chosen per item)
+  int tcols_class[4];   // k_div_persistent: columns per lane for dividends of <= 1024,
+                        // 2048, 4096 and more digits
 };
 
 struct ShinvArgs {
@@ -51,6 +55,7 @@ struct ShinvArgs {
   int64_t n, vs, os;
   int vn, on;
   int smem_words;
+  int tcols;
 };
 
 }  // namespace mp

@@ -29,10 +29,13 @@
 namespace mp {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int T = 7;                // output columns per lane (odd: conflict-free window loads)
-constexpr int WSPAN = 32 * T;       // output columns per warp strip
-constexpr int PAD = WSPAN + T;      // zero digits kept on each side of a multiply operand
-constexpr int RED_WORDS = 96;       // block scratch: per-warp slots + counters
+// Output columns per lane of the strip multiply: 3, 5 or 7, chosen per launch
+// (odd, so that the lanes' window loads fall in distinct banks). Fewer columns
+// waste fewer digit products in the triangular ends of a product; more columns
+// reuse each loaded digit more often.
+constexpr int T_MIN = 3, T_MAX = 7;
+constexpr int PAD = 32 * T_MAX + T_MAX;  // zero digits kept on each side of a multiply operand
+constexpr int RED_WORDS = 96;            // block scratch: per-warp slots + counters
 
 // block scratch layout
 constexpr int RED_CNT = 64;   // multiply work counter
@@ -45,6 +48,7 @@ struct Blk {
   int bar;   // named barrier id (0: the whole block)
   int* red;  // RED_WORDS ints of shared scratch owned by this group
   unsigned long long* work;  // thread 0's running count of algorithmic digit products (may be null)
+  int tcols;                 // columns per lane of the strip multiply (3, 5 or 7)
 
   __device__ __forceinline__ void sync() const {
     asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
@@ -62,6 +66,7 @@ __device__ __forceinline__ Blk make_group(int* red, int w0, int nw, int bar) {
   b.bar = bar;
   b.red = red;
   b.work = nullptr;
+  b.tcols = 5;
   return b;
 }
 
@@ -273,8 +278,10 @@ __device__ __forceinline__ void mac3(uint32_t& c0, uint32_t& c1, uint32_t& c2, u
 // One warp strip: lane owns columns [p0, p0+T) of A*B restricted to rows
 // j in [jlo, jhi) of B. Writes the lane's low T digits to C (columns < npos)
 // and its two overflow digits to OV[2s], OV[2s+1] with s = p0 / T.
+template <int T>
 __device__ __forceinline__ void mul_strip(const Blk& b, uint32_t* C, int npos, const uint32_t* A, int na,
                                           const uint32_t* Bv, int nb, uint32_t* OV, int ws) {
+  constexpr int WSPAN = 32 * T;
   const int P0 = ws * WSPAN;
   const int jlo = max(0, P0 - na + 1);
   const int jhi = min(nb, P0 + WSPAN);
@@ -336,8 +343,8 @@ __host__ __device__ __forceinline__ unsigned long long pair_count(int na, int nb
 // trapezoid of row counts (every row of the shorter operand) come first, then
 // strips alternately left and right of it by distance. The band [ws0, nws) is
 // the part of the product that is computed.
-__device__ __forceinline__ int strip_order(int idx, int ws0, int nws, int na, int nb) {
-  int lo = (nb - WSPAN + WSPAN - 1) / WSPAN;  // first strip whose rows reach nb
+__device__ __forceinline__ int strip_order(int idx, int ws0, int nws, int na, int nb, int WSPAN) {
+  int lo = (nb - 1) / WSPAN;  // first strip whose rows reach nb
   if (lo < 0) lo = 0;
   int hi = (na - 1) / WSPAN;  // last strip before the ramp down
   lo = min(max(lo, ws0), nws - 1);
@@ -353,13 +360,41 @@ __device__ __forceinline__ int strip_order(int idx, int ws0, int nws, int na, in
   return (nl > nr) ? lo - d : hi + d;
 }
 
+// The strip multiply for T columns per lane (see mul).
+template <int T>
+__device__ __forceinline__ void mul_t(const Blk& b, uint32_t* C, int npos, uint32_t* A, int na, uint32_t* Bv, int nb,
+                                      uint32_t* OV, int plo) {
+  constexpr int WSPAN = 32 * T;
+  const int ws0 = plo / WSPAN;
+  const int nws = (npos + WSPAN - 1) / WSPAN;
+  const int cnt = nws - ws0;
+  while (true) {
+    int idx = 0;
+    if (b.lane == 0) idx = atomicAdd(&b.red[RED_CNT], 1);
+    idx = __shfl_sync(FULL, idx, 0);
+    if (idx >= cnt) break;
+    mul_strip<T>(b, C, npos, A, na, Bv, nb, OV, strip_order(idx, ws0, nws, na, nb, WSPAN));
+  }
+  b.sync();
+  // fold each strip's overflow digits into the next strip's first two columns
+  const int p0 = ws0 * WSPAN, s0 = ws0 * 32;
+  addsub<false>(
+      b, C + p0, npos - p0, [&](int i) { return C[p0 + i]; },
+      [&](int i) -> uint32_t {
+        const int s = (p0 + i) / T;
+        const int off = p0 + i - s * T;
+        return (s > s0 && off < 2) ? OV[2 * (s - 1) + off] : 0u;
+      },
+      0u);
+}
+
 // C[plo..npos) of X * Y: the digits of (X * Y) mod B^npos at positions plo
 // and above, from the digit products at positions at or above the warp strip
 // holding plo; carries from products below that strip are dropped (plo = 0:
 // the exact product modulo B^npos). X (nx digits) and Y (ny digits) are
 // multiply operands: PAD zero digits must be addressable below index 0 and
 // above the digit count (the high pads are zeroed here). OV needs
-// 2 * 32 * ceil(npos / WSPAN) words. C must not alias X or Y.
+// 2 * (ceil(npos / T_MIN) + 32) words. C must not alias X or Y.
 __device__ inline void mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int nx, uint32_t* Y, int ny, uint32_t* OV,
                            int plo = 0) {
   uint32_t* A = X;
@@ -381,31 +416,16 @@ __device__ inline void mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int
   }
   for (int i = b.tid; i < PAD; i += b.nt) {
     A[na + i] = 0u;
-    if (i < T) Bv[nb + i] = 0u;
+    if (i < T_MAX) Bv[nb + i] = 0u;
   }
   if (b.tid == 0) b.red[RED_CNT] = 0;
   b.sync();
-  const int ws0 = plo / WSPAN;
-  const int nws = (npos + WSPAN - 1) / WSPAN;
-  const int cnt = nws - ws0;
-  while (true) {
-    int idx = 0;
-    if (b.lane == 0) idx = atomicAdd(&b.red[RED_CNT], 1);
-    idx = __shfl_sync(FULL, idx, 0);
-    if (idx >= cnt) break;
-    mul_strip(b, C, npos, A, na, Bv, nb, OV, strip_order(idx, ws0, nws, na, nb));
-  }
-  b.sync();
-  // fold each strip's overflow digits into the next strip's first two columns
-  const int p0 = ws0 * WSPAN, s0 = ws0 * 32;
-  addsub<false>(
-      b, C + p0, npos - p0, [&](int i) { return C[p0 + i]; },
-      [&](int i) -> uint32_t {
-        const int s = (p0 + i) / T;
-        const int off = p0 + i - s * T;
-        return (s > s0 && off < 2) ? OV[2 * (s - 1) + off] : 0u;
-      },
-      0u);
+  if (b.tcols == 3)
+    mul_t<3>(b, C, npos, A, na, Bv, nb, OV, plo);
+  else if (b.tcols == 7)
+    mul_t<7>(b, C, npos, A, na, Bv, nb, OV, plo);
+  else
+    mul_t<5>(b, C, npos, A, na, Bv, nb, OV, plo);
 }
 
 }  // namespace mp

@@ -18,7 +18,7 @@
 //   X  [kl+32]         divisor prefix v' and PowDiff result x      } u overlays
 //   R  [h-kl+16]       Step result before its shift                } X..R later
 //   P  [max(h+41, 2h-kl+9)]  products
-//   OV [2 (ceil(|P|/T) + 64)] multiply overflow digits
+//   OV [2 (ceil(|P|/3) + 64)] multiply overflow digits
 // The total does not depend on kl and grows as ~4.6 h digits.
 #pragma once
 #include "mp_block.cuh"
@@ -43,9 +43,11 @@ __host__ __device__ __forceinline__ int cap_p(int h, int kl) {
   return a > c ? a : c;
 }
 
+__host__ __device__ __forceinline__ int cap_ov(int capP) { return 2 * ((capP + T_MIN - 1) / T_MIN + 64); }
+
 __host__ __device__ __forceinline__ int layout_words(int h, int kl) {
   const int capP = cap_p(h, kl);
-  const int capOV = 2 * ((capP + T - 1) / T + 64);
+  const int capOV = cap_ov(capP);
   return 5 * PAD + kl + (h - kl + 9) + (kl + 32) + (h - kl + 16) + capP + capOV;
 }
 
@@ -59,7 +61,7 @@ __device__ __forceinline__ Layout make_layout(uint32_t* sm, int h, int kl) {
   L.capX = kl + 32;
   L.capR = h - kl + 16;
   L.capP = cap_p(h, kl);
-  L.capOV = 2 * ((L.capP + T - 1) / T + 64);
+  L.capOV = cap_ov(L.capP);
   int off = PAD;
   L.V = sm + off;
   off += L.capV + PAD;

@@ -12,7 +12,8 @@ template <int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_div_uniform(UniformArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int red[RED_WORDS];
-  const Blk b = make_blk(red);
+  Blk b = make_blk(red);
+  b.tcols = a.tcols;
   for (int64_t item = blockIdx.x; item < a.n; item += gridDim.x) {
     ItemIO io;
     io.u = a.u + item * a.us;
@@ -43,7 +44,8 @@ template <int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_div_ragged(RaggedArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int red[RED_WORDS];
-  const Blk b = make_blk(red);
+  Blk b = make_blk(red);
+  b.tcols = a.tcols > 0 ? a.tcols : 5;
   while (true) {
     if (b.tid == 0) red[RED_AUX] = atomicAdd(a.head, 1);
     b.sync();
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_persistent(RaggedArgs a) 
   int words = a.smem_words;
   int pending = -1;
   while (true) {
-    const Blk b = make_group(red[node], w0, nw, node);
+    Blk b = make_group(red[node], w0, nw, node);
     int idx;
     if (pending >= 0) {
       idx = pending;
@@ -137,6 +139,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_persistent(RaggedArgs a) 
     unsigned long long work = 0ull;
     Blk bw = b;
     bw.work = a.products ? &work : nullptr;
+    bw.tcols = a.tcols > 0 ? a.tcols : a.tcols_class[ul <= 1024 ? 0 : ul <= 2048 ? 1 : ul <= 4096 ? 2 : 3];
     const int st = div_item(bw, base, words, io, a.flags, &it, nullptr, 0, 0);
     if (b.tid == 0) {
       a.status[item] = st;
@@ -152,7 +155,8 @@ template <int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_shinv(ShinvArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int red[RED_WORDS];
-  const Blk b = make_blk(red);
+  Blk b = make_blk(red);
+  b.tcols = a.tcols > 0 ? a.tcols : 5;
   for (int64_t item = blockIdx.x; item < a.n; item += gridDim.x) {
     ItemIO io;
     io.u = nullptr;

@@ -14,7 +14,8 @@
 
 #include <cuda_runtime.h>
 
-#include "mp_kernels.cuh"
+#include "mp_div.cuh"
+#include "mpdiv_kernels.h"
 #include "mpdiv.h"
 #include "mpdiv_internal.h"
 
@@ -23,27 +24,17 @@ using namespace mp;
 // ------------------------------------------------------------------ kernels
 namespace {
 
-template <int MAXT, int MINB>
-struct Kern {
-  static void* get(int kk) {
-    switch (kk) {
-      case 0: return (void*)k_div_uniform<MAXT / 32, MINB>;
-      case 1: return (void*)k_div_ragged<MAXT / 32, MINB>;
-      default: return (void*)k_shinv<MAXT / 32, MINB>;
-    }
-  }
-};
+enum KernKind { KK_UNIFORM = MP_K_UNIFORM, KK_RAGGED = MP_K_RAGGED, KK_SHINV = MP_K_SHINV, KK_PERSIST = MP_K_PERSIST };
 
-enum KernKind { KK_UNIFORM = 0, KK_RAGGED = 1, KK_SHINV = 2, KK_PERSIST = 3 };
-
-// Instantiations by block size; the minimum-blocks bound caps registers at 64
-// per thread so that several blocks of the smaller size classes share an SM.
+// Instantiations by block size (mpdiv_k*.cu); the minimum-blocks bound caps
+// registers at 64 per thread so that several blocks of the smaller size
+// classes share an SM. The persistent kernel always runs 16-warp blocks.
 void* kernel_for(KernKind kk, int warps) {
-  if (kk == KK_PERSIST) return (void*)k_div_persistent<16, 1>;  // splits itself: always 16 warps
-  if (warps <= 4) return Kern<128, 8>::get(kk);
-  if (warps <= 8) return Kern<256, 4>::get(kk);
-  if (warps <= 16) return Kern<512, 2>::get(kk);
-  return Kern<1024, 1>::get(kk);
+  if (kk == KK_PERSIST) return mp_kernel_w16(MP_K_PERSIST);
+  if (warps <= 4) return mp_kernel_w4(kk);
+  if (warps <= 8) return mp_kernel_w8(kk);
+  if (warps <= 16) return mp_kernel_w16(kk);
+  return mp_kernel_w32(kk);
 }
 
 }  // namespace
@@ -75,11 +66,21 @@ int mpdiv_default_warps(mpdiv_ctx* ctx, int max_digits) {
     std::lock_guard<std::mutex> g(ctx->tune_mu);
     const int cls = mpdiv_size_class(max_digits);
     auto it = ctx->tuned.find(cls);
-    if (it != ctx->tuned.end()) return it->second;
+    if (it != ctx->tuned.end()) return it->second.first;
   }
-  if (max_digits <= 1536) return 8;
-  if (max_digits <= 3072) return 8;
+  if (max_digits <= 2048) return 4;
+  if (max_digits <= 4096) return 8;
   return 16;
+}
+
+int mpdiv_default_tcols(mpdiv_ctx* ctx, int max_digits) {
+  if (ctx->cfg.mul_columns > 0) return ctx->cfg.mul_columns;
+  {
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    auto it = ctx->tuned.find(mpdiv_size_class(max_digits));
+    if (it != ctx->tuned.end()) return it->second.second;
+  }
+  return 3;  // measured fastest at every size class on GB300 (mpdiv_autotune)
 }
 
 int mpdiv_size_class(int digits) {
@@ -169,6 +170,7 @@ int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t st
   a.rn = L.rn;
   a.smem_words = smem / 4;
   a.flags = ctx->cfg.flags;
+  a.tcols = L.tcols > 0 ? L.tcols : mpdiv_default_tcols(ctx, max_digits);
   const int64_t grid = std::min<int64_t>(L.n, 0x7fffffff);
   void* args[] = {&a};
   cudaError_t e = cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * warps), args, smem, stream);
@@ -209,6 +211,7 @@ extern "C" int mpdiv_batch(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* u, i
   L.qn = q_limbs;
   L.rn = r_limbs;
   L.warps = 0;
+  L.tcols = 0;
   return mpdiv_launch_uniform(ctx, L, (cudaStream_t)stream);
 }
 
@@ -298,6 +301,8 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
   a.flags = ctx->cfg.flags;
   a.split_digits[0] = ctx->split_digits[0];
   a.split_digits[1] = ctx->split_digits[1];
+  a.tcols = L.split ? ctx->cfg.mul_columns : mpdiv_default_tcols(ctx, max_u);
+  for (int c = 0; c < 4; c++) a.tcols_class[c] = mpdiv_default_tcols(ctx, 1024 << c);
   if (!L.use_graph) {
     if ((rc = mpdiv_cuda_check(ctx, cudaMemsetAsync(a.head, 0, sizeof(int32_t), stream), "queue reset"))) return rc;
     void* args[] = {&a};
@@ -417,9 +422,17 @@ extern "C" int mpdiv_debug_shinv(mpdiv_ctx* ctx, int64_t n_items, const uint32_t
   a.vn = v_limbs;
   a.on = out_limbs;
   a.smem_words = smem / 4;
+  a.tcols = ctx->cfg.mul_columns > 0 ? ctx->cfg.mul_columns : 5;
   void* args[] = {&a};
   const int64_t grid = std::min<int64_t>(n_items, 0x7fffffff);
   return mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * warps), args, smem,
                                                 (cudaStream_t)stream),
                           "launch of the shifted-inverse kernel");
+}
+
+extern "C" int mpdiv_tuning(mpdiv_ctx* ctx, int32_t u_limbs, int32_t* warps, int32_t* mul_columns) {
+  if (!ctx || u_limbs < 1) return MPDIV_EINVAL;
+  if (warps) *warps = mpdiv_default_warps(ctx, u_limbs);
+  if (mul_columns) *mul_columns = mpdiv_default_tcols(ctx, u_limbs);
+  return MPDIV_OK;
 }

@@ -1,0 +1,14 @@
+// Division kernels instantiated for 512-thread blocks (compiled as a
+// separate translation unit so that the block sizes build in parallel).
+#include "mp_kernels.cuh"
+#include "mpdiv_kernels.h"
+
+void* mp_kernel_w16(int kind) {
+  switch (kind) {
+    case MP_K_UNIFORM: return (void*)mp::k_div_uniform<16, 2>;
+    case MP_K_RAGGED: return (void*)mp::k_div_ragged<16, 2>;
+    case MP_K_SHINV: return (void*)mp::k_shinv<16, 2>;
+    case MP_K_PERSIST: return (void*)mp::k_div_persistent<16, 1>;
+    default: return nullptr;
+  }
+}

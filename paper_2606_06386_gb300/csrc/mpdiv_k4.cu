@@ -1,0 +1,13 @@
+// Division kernels instantiated for 128-thread blocks (compiled as a
+// separate translation unit so that the block sizes build in parallel).
+#include "mp_kernels.cuh"
+#include "mpdiv_kernels.h"
+
+void* mp_kernel_w4(int kind) {
+  switch (kind) {
+    case MP_K_UNIFORM: return (void*)mp::k_div_uniform<4, 8>;
+    case MP_K_RAGGED: return (void*)mp::k_div_ragged<4, 8>;
+    case MP_K_SHINV: return (void*)mp::k_shinv<4, 8>;
+    default: return nullptr;
+  }
+}

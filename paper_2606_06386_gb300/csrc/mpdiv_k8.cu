@@ -1,0 +1,13 @@
+// Division kernels instantiated for 256-thread blocks (compiled as a
+// separate translation unit so that the block sizes build in parallel).
+#include "mp_kernels.cuh"
+#include "mpdiv_kernels.h"
+
+void* mp_kernel_w8(int kind) {
+  switch (kind) {
+    case MP_K_UNIFORM: return (void*)mp::k_div_uniform<8, 4>;
+    case MP_K_RAGGED: return (void*)mp::k_div_ragged<8, 4>;
+    case MP_K_SHINV: return (void*)mp::k_shinv<8, 4>;
+    default: return nullptr;
+  }
+}

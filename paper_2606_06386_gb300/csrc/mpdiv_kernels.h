@@ -1,0 +1,9 @@
+// Getters for the kernel instantiations of each block size (mpdiv_k*.cu).
+#pragma once
+
+enum { MP_K_UNIFORM = 0, MP_K_RAGGED = 1, MP_K_SHINV = 2, MP_K_PERSIST = 3 };
+
+void* mp_kernel_w4(int kind);
+void* mp_kernel_w8(int kind);
+void* mp_kernel_w16(int kind);  // also the self-splitting persistent kernel (16 warps)
+void* mp_kernel_w32(int kind);

@@ -39,13 +39,21 @@ int64_t now_ns() {
 
 enum ReqState { RQ_QUEUED = 0, RQ_RUNNING = 1, RQ_DONE = 2 };
 
+// The output-ring allocation of one batch; released when every request of
+// the batch has been polled.
+struct OutBatch {
+  int64_t seq = -1;
+  int remaining = 0;
+};
+
 struct Request {
   uint64_t ticket = 0;
   int32_t u_len = 0, v_len = 0, q_len = 0, r_len = 0;
   int64_t in_off = -1;            // u at in_off, v at in_off + u_len (input ring digits)
   int64_t in_seq = -1;            // its input-ring allocation
+  int64_t out_off = -1;           // q at out_off, r at out_off + q_len (output ring digits)
+  std::shared_ptr<OutBatch> out;  // the batch's output allocation
   std::atomic<int> ready{0};      // operands copied into the ring
-  std::vector<uint32_t> q, r;     // results once done
   int32_t status = 0;
   int state = RQ_QUEUED;
   int64_t t_submit = 0, t_done = 0;
@@ -142,8 +150,13 @@ bool MpServer::launch(Slot& s) {
   const int64_t status_w = 13 * n + 8;  // status after the heads
   std::vector<double> cost(n);
   int64_t pq = s.out_off;
+  auto ob = std::make_shared<OutBatch>();
+  ob->seq = s.out_seq;
+  ob->remaining = (int)n;
   for (int64_t i = 0; i < n; i++) {
     Request* r = s.reqs[i];
+    r->out_off = pq;
+    r->out = ob;
     h_off[i] = r->in_off;
     h_off[n + i] = r->in_off + r->u_len;
     h_off[2 * n + i] = pq;
@@ -215,32 +228,22 @@ void MpServer::run() {
   cudaSetDevice(ctx->device);
   std::vector<Slot*> finished;
   while (true) {
-    // ---- completions: copy results out without the lock, then publish
+    // ---- completions: results stay in the pinned output ring until polled
     finished.clear();
     for (auto& s : slots)
       if (s.busy && cudaEventQuery(s.ev) == cudaSuccess) finished.push_back(&s);
-    for (Slot* s : finished) {
-      const int64_t n = (int64_t)s->reqs.size();
-      const int32_t* st = reinterpret_cast<const int32_t*>(s->h_meta + 13 * n + 8);
-      int64_t pq = s->out_off;
-      for (int64_t i = 0; i < n; i++) {
-        Request* r = s->reqs[i];
-        r->q.assign(h_out + pq, h_out + pq + r->q_len);
-        r->r.assign(h_out + pq + r->q_len, h_out + pq + r->q_len + r->r_len);
-        pq += r->q_len + r->r_len;
-        r->status = st[i];
-      }
-    }
     std::unique_lock<std::mutex> lk(mu);
     const int64_t t = now_ns();
     for (Slot* s : finished) {
-      for (Request* r : s->reqs) {
+      const int64_t n = (int64_t)s->reqs.size();
+      const int32_t* st = reinterpret_cast<const int32_t*>(s->h_meta + 13 * n + 8);
+      for (int64_t i = 0; i < n; i++) {
+        Request* r = s->reqs[i];
+        r->status = st[i];
         r->state = RQ_DONE;
         r->t_done = t;
         in_ring.release(r->in_seq);
       }
-      out_ring.release(s->out_seq);
-      const int64_t n = (int64_t)s->reqs.size();
       completed += n;
       pending -= n;
       inflight_items -= n;
@@ -299,8 +302,8 @@ void MpServer::run() {
           sched_error = MPDIV_ECUDA;
           const int64_t tf = now_ns();
           for (Request* r : b) {
-            r->q.assign(r->q_len, 0u);
-            r->r.assign(r->r_len, 0u);
+            r->out.reset();  // no results: the output allocation is released below
+            r->out_off = -1;
             r->status = MPDIV_ST_INTERNAL;
             r->state = RQ_DONE;
             r->t_done = tf;
@@ -340,9 +343,9 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
   if (cfg) S->cfg = *cfg;
   if (S->cfg.pool_digits <= 0) S->cfg.pool_digits = 64ll << 20;
   if (S->cfg.max_batch <= 0) S->cfg.max_batch = 4096;
-  if (S->cfg.max_inflight <= 0) S->cfg.max_inflight = 16;
+  if (S->cfg.max_inflight <= 0) S->cfg.max_inflight = 32;
   if (S->cfg.max_pending <= 0) S->cfg.max_pending = 1 << 20;
-  if (S->cfg.low_water <= 0) S->cfg.low_water = 1024;
+  if (S->cfg.low_water <= 0) S->cfg.low_water = 2048;
   if (S->cfg.max_wait_us <= 0) S->cfg.max_wait_us = 2000;
   const int64_t half = (S->cfg.pool_digits / 2) & ~int64_t(3);
   S->in_ring.cap = half;
@@ -429,22 +432,37 @@ static int poll_impl(mpdiv_ctx* ctx, uint64_t ticket, uint32_t* q_host, int32_t 
           return MPDIV_ETIMEDOUT;
       }
     }
-    int qs = (int)r->q.size();
-    while (qs > 0 && r->q[qs - 1] == 0u) qs--;
-    int rs = (int)r->r.size();
-    while (rs > 0 && r->r[rs - 1] == 0u) rs--;
-    if (q_host && qs > q_cap) return mpdiv_set_error(ctx, MPDIV_EINVAL, "q_cap too small (%d digits needed)", qs);
-    if (r_host && rs > r_cap) return mpdiv_set_error(ctx, MPDIV_EINVAL, "r_cap too small");
+    const uint32_t* qd = r->out_off >= 0 ? S->h_out + r->out_off : nullptr;
+    if (qd && ((q_host && q_cap < r->q_len) || (r_host && r_cap < r->r_len))) {
+      // a short buffer is fine when the digits it drops are zero
+      int qs = r->q_len, rs = r->r_len;
+      while (qs > 0 && qd[qs - 1] == 0u) qs--;
+      while (rs > 0 && qd[r->q_len + rs - 1] == 0u) rs--;
+      if (q_host && qs > q_cap) return mpdiv_set_error(ctx, MPDIV_EINVAL, "q_cap too small (%d digits needed)", qs);
+      if (r_host && rs > r_cap) return mpdiv_set_error(ctx, MPDIV_EINVAL, "r_cap too small");
+    }
     done = std::move(it->second);
     S->reqs.erase(it);
   }
+  // the digits stay valid until this request's share of its batch is released below
   const Request* r = done.get();
-  if (q_host)
-    for (int i = 0; i < q_cap; i++) q_host[i] = i < (int)r->q.size() ? r->q[i] : 0u;
-  if (r_host)
-    for (int i = 0; i < r_cap; i++) r_host[i] = i < (int)r->r.size() ? r->r[i] : 0u;
+  const uint32_t* qd = r->out_off >= 0 ? S->h_out + r->out_off : nullptr;
+  if (q_host) {
+    const int n = qd ? std::min(q_cap, r->q_len) : 0;
+    if (n) std::memcpy(q_host, qd, 4 * (size_t)n);
+    for (int i = n; i < q_cap; i++) q_host[i] = 0u;
+  }
+  if (r_host) {
+    const int n = qd ? std::min(r_cap, r->r_len) : 0;
+    if (n) std::memcpy(r_host, qd + r->q_len, 4 * (size_t)n);
+    for (int i = n; i < r_cap; i++) r_host[i] = 0u;
+  }
   if (status) *status = r->status;
   if (t_done) *t_done = r->t_done;
+  if (r->out) {
+    std::lock_guard<std::mutex> g(S->mu);
+    if (--r->out->remaining == 0) S->out_ring.release(r->out->seq);
+  }
   return MPDIV_OK;
 }
 
@@ -550,28 +568,36 @@ extern "C" int mpdiv_serve_replay(mpdiv_ctx* ctx, int64_t n, const int64_t* arri
   };
   std::vector<std::thread> submitters;
   for (int t = 0; t < kSub; t++) submitters.emplace_back(submitter_fn, t);
-  for (int64_t i = 0; i < n; i++) {
-    while (sub_next[i % kSub].load(std::memory_order_acquire) <= i)
-      std::this_thread::sleep_for(std::chrono::microseconds(5));
-    if (tickets[i] == 0) {
-      status[i] = -1;
-      latency_ns[i] = -1;
-      continue;
+  // several pollers too (request i is polled by thread i mod kPoll); each
+  // copies its results straight from the server's pinned output ring
+  constexpr int kPoll = 4;
+  auto poller_fn = [&](int tid) {
+    for (int64_t i = tid; i < n; i += kPoll) {
+      while (sub_next[i % kSub].load(std::memory_order_acquire) <= i)
+        std::this_thread::sleep_for(std::chrono::microseconds(5));
+      if (tickets[i] == 0) {
+        status[i] = -1;
+        latency_ns[i] = -1;
+        continue;
+      }
+      int64_t td = 0;
+      int rc;
+      while ((rc = poll_impl(ctx, tickets[i], q + q_off[i], q_len[i], r + r_off[i], r_len[i], &status[i], 1000000,
+                             &td)) == MPDIV_ETIMEDOUT) {
+      }
+      if (rc != MPDIV_OK) {
+        int expect = MPDIV_OK;
+        err.compare_exchange_strong(expect, rc);
+        status[i] = -1;
+        latency_ns[i] = -1;
+        continue;
+      }
+      latency_ns[i] = td - t_arr[i];
     }
-    int64_t td = 0;
-    int rc;
-    while ((rc = poll_impl(ctx, tickets[i], q + q_off[i], q_len[i], r + r_off[i], r_len[i], &status[i], 1000000,
-                           &td)) == MPDIV_ETIMEDOUT) {
-    }
-    if (rc != MPDIV_OK) {
-      int expect = MPDIV_OK;
-      err.compare_exchange_strong(expect, rc);
-      status[i] = -1;
-      latency_ns[i] = -1;
-      continue;
-    }
-    latency_ns[i] = td - t_arr[i];
-  }
+  };
+  std::vector<std::thread> pollers;
+  for (int t = 0; t < kPoll; t++) pollers.emplace_back(poller_fn, t);
+  for (auto& th : pollers) th.join();
   for (auto& th : submitters) th.join();
   if (rejected) *rejected = rej.load();
   return err.load();

@@ -1,8 +1,10 @@
-// Block-size tuner for the division kernels (Section 5 of arXiv 2606.06386
-// names autotuning of block size and sequentialisation as future work): for a
-// size class it times the plain kernel at each candidate warps-per-block on
-// synthetic divisions and records the fastest in the context's table, which
-// can be saved to and loaded from a text file (MPDIV_TUNE_FILE).
+// Tuner for the division kernels (Section 5 of arXiv 2606.06386 names
+// autotuning of block size, sequentialisation and multiplication
+// specialisation as future work): for a size class it times the plain kernel
+// at each candidate warps per block (4, 8, 16, 32) and columns per lane of the
+// strip multiply (3, 5, 7) on synthetic divisions, and records the fastest in
+// the context's table, which can be saved to and loaded from a text file
+// (MPDIV_TUNE_FILE).
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -32,10 +34,10 @@ __global__ void k_fill(uint32_t* x, int64_t n_items, int digits, int64_t stride,
 void mpdiv_tune_load(mpdiv_ctx* ctx, const char* path) {
   FILE* f = fopen(path, "r");
   if (!f) return;
-  int cls, w;
+  int cls, w, t;
   std::lock_guard<std::mutex> g(ctx->tune_mu);
-  while (fscanf(f, "%d %d", &cls, &w) == 2)
-    if (cls > 0 && w > 0 && w <= 32) ctx->tuned[cls] = w;
+  while (fscanf(f, "%d %d %d", &cls, &w, &t) == 3)
+    if (cls > 0 && w > 0 && w <= 32 && (t == 3 || t == 5 || t == 7)) ctx->tuned[cls] = {w, t};
   fclose(f);
 }
 
@@ -43,7 +45,7 @@ static void tune_save(mpdiv_ctx* ctx, const char* path) {
   FILE* f = fopen(path, "w");
   if (!f) return;
   std::lock_guard<std::mutex> g(ctx->tune_mu);
-  for (auto& kv : ctx->tuned) fprintf(f, "%d %d\n", kv.first, kv.second);
+  for (auto& kv : ctx->tuned) fprintf(f, "%d %d %d\n", kv.first, kv.second.first, kv.second.second);
   fclose(f);
 }
 
@@ -58,7 +60,7 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
   const size_t n = (size_t)n_items;
   int rc = MPDIV_OK;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  int best_w = 0;
+  int best_w = 0, best_t = 5;
   float best_ms = 1e30f;
   if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&u, n * u_limbs * 4), "autotune alloc"))) goto done;
   if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&v, n * v_limbs * 4), "autotune alloc"))) goto done;
@@ -69,7 +71,9 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
   k_fill<<<256, 256>>>(v, n_items, v_limbs, v_limbs, 0x7654321ull);
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int w : {4, 8, 16, 32}) {
+  for (int cand = 0; cand < 12; cand++) {
+    const int w = 4 << (cand / 3);
+    const int tc = 3 + 2 * (cand % 3);
     UniformLaunch L{};
     L.u = u;
     L.v = v;
@@ -85,6 +89,7 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
     L.qn = u_limbs;
     L.rn = v_limbs;
     L.warps = w;
+    L.tcols = tc;
     if (mpdiv_launch_uniform(ctx, L, 0) != MPDIV_OK) continue;  // e.g. does not fit
     cudaEventRecord(e0, 0);
     mpdiv_launch_uniform(ctx, L, 0);
@@ -96,6 +101,7 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
     if (ms < best_ms) {
       best_ms = ms;
       best_w = w;
+      best_t = tc;
     }
   }
   if (best_w == 0) {
@@ -104,7 +110,7 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
   }
   {
     std::lock_guard<std::mutex> g(ctx->tune_mu);
-    ctx->tuned[mpdiv_size_class(u_limbs)] = best_w;
+    ctx->tuned[mpdiv_size_class(u_limbs)] = {best_w, best_t};
   }
   if (const char* tf = getenv("MPDIV_TUNE_FILE")) tune_save(ctx, tf);
   rc = best_w;

@@ -93,20 +93,29 @@ def test_inject_lambda_keeps_results_exact():
     assert_same(Q, R, S, Qo, Ro, So, names)
 
 
+@pytest.mark.parametrize("cols", [3, 5, 7])
 @pytest.mark.parametrize("warps", [4, 8, 16, 32])
-def test_every_block_size_is_exact(warps):
+def test_every_launch_shape_is_exact(warps, cols):
     U, V = I.sweep(2048, 1024, 16)
-    Q, R, S, _ = run_uniform(U, V, warps=warps)
+    Q, R, S, _ = run_uniform(U, V, warps=warps, cols=cols)
+    Qo, Ro, So = oracle_uniform(U, V)
+    assert_same(Q, R, S, Qo, Ro, So)
+    # ragged small shapes with several strips and tails, at every strip width
+    U = I.uniform_batch(16, 333, seed=5, stream=cols)
+    V = I.uniform_batch(16, 131, seed=6, stream=cols)
+    Q, R, S, _ = run_uniform(U, V, warps=warps, cols=cols)
     Qo, Ro, So = oracle_uniform(U, V)
     assert_same(Q, R, S, Qo, Ro, So)
 
 
-def test_autotune_picks_a_block_size():
+def test_autotune_picks_a_launch_shape():
     import paper_2606_06386_gb300 as mp
 
     c = mp.mpdiv_init(0)
     try:
         w = mp.mpdiv_autotune(c, 1024, 512, 1024)
         assert w in (4, 8, 16, 32)
+        tw, tc = mp.mpdiv_tuning(c, 1000)
+        assert tw == w and tc in (3, 5, 7)
     finally:
         mp.mpdiv_destroy(c)
