@@ -35,11 +35,11 @@ constexpr unsigned FULL = 0xffffffffu;
 // reuse each loaded digit more often.
 constexpr int T_MIN = 3, T_MAX = 7;
 constexpr int PAD = 32 * T_MAX + T_MAX;  // zero digits kept on each side of a multiply operand
-constexpr int RED_WORDS = 96;            // block scratch: per-warp slots + counters
+constexpr int RED_WORDS = 100;           // block scratch: 3 x 32 per-warp slots + counters
 
 // block scratch layout
-constexpr int RED_CNT = 64;   // multiply work counter
-constexpr int RED_AUX = 65;   // misc broadcast
+constexpr int RED_CNT = 96;   // multiply work counter
+constexpr int RED_AUX = 97;   // misc broadcast
 
 // A group of whole warps that cooperates on one division: the whole thread
 // block, or a slice of it synchronised by its own named barrier.
@@ -229,6 +229,72 @@ __device__ inline void copy(const Blk& b, uint32_t* C, int len, FX X) {
   b.sync();
 }
 
+// C[i] = X(i) for i < len, returning the number of significant digits
+// written (one reduction instead of a copy followed by prec). C must not
+// alias what X reads at other indices.
+template <class FX>
+__device__ inline int copy_prec(const Blk& b, uint32_t* C, int len, FX X) {
+  int lo, hi;
+  warp_range(b, len, lo, hi);
+  int best = -1;
+  for (int base = lo; base < hi; base += 32) {
+    const int i = base + b.lane;
+    uint32_t d = 0u;
+    if (i < hi) {
+      d = X(i);
+      C[i] = d;
+    }
+    const uint32_t m = __ballot_sync(FULL, d != 0u);
+    if (m) best = base + 31 - __clz(m);
+  }
+  if (b.lane == 0) b.red[b.warp] = best;
+  b.sync();
+  int r = (b.lane < b.nw) ? b.red[b.lane] : -1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r = max(r, __shfl_xor_sync(FULL, r, o));
+  b.sync();
+  return r + 1;
+}
+
+// One pass over P[0..len): the lowest nonzero digit (*z), the highest
+// nonzero digit (*t1) and the highest digit that is not all ones (*t2);
+// -1 where there is none.
+__device__ inline void scan3(const Blk& b, const uint32_t* P, int len, int* z, int* t1, int* t2) {
+  int lo, hi;
+  warp_range(b, len, lo, hi);
+  int bz = 0x7fffffff, b1 = -1, b2 = -1;
+  for (int base = lo; base < hi; base += 32) {
+    const int i = base + b.lane;
+    const uint32_t d = (i < hi) ? P[i] : 0u;
+    const uint32_t mn = __ballot_sync(FULL, d != 0u);
+    const uint32_t mf = __ballot_sync(FULL, (i < hi) && d != FULL);
+    if (mn) {
+      if (bz == 0x7fffffff) bz = base + __ffs(mn) - 1;
+      b1 = base + 31 - __clz(mn);
+    }
+    if (mf) b2 = base + 31 - __clz(mf);
+  }
+  if (b.lane == 0) {
+    b.red[b.warp] = bz;
+    b.red[32 + b.warp] = b1;
+    b.red[64 + b.warp] = b2;
+  }
+  b.sync();
+  int rz = (b.lane < b.nw) ? b.red[b.lane] : 0x7fffffff;
+  int r1 = (b.lane < b.nw) ? b.red[32 + b.lane] : -1;
+  int r2 = (b.lane < b.nw) ? b.red[64 + b.lane] : -1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rz = min(rz, __shfl_xor_sync(FULL, rz, o));
+    r1 = max(r1, __shfl_xor_sync(FULL, r1, o));
+    r2 = max(r2, __shfl_xor_sync(FULL, r2, o));
+  }
+  b.sync();
+  *z = rz == 0x7fffffff ? -1 : rz;
+  *t1 = r1;
+  *t2 = r2;
+}
+
 // X <- X - B^e, digits [e, len); requires X >= B^e. Returns false if no digit
 // at or above e was nonzero (X < B^e).
 __device__ inline bool sub_pow(const Blk& b, uint32_t* X, int e, int len) {
@@ -246,6 +312,16 @@ __device__ inline bool add_pow(const Blk& b, uint32_t* X, int e, int cap) {
   for (int i = e + b.tid; i <= z; i += b.nt) X[i] = (i == z) ? X[i] + 1u : 0u;
   b.sync();
   return true;
+}
+
+// C <- B^L - P over L digits, P (np digits, zero-extended) nonzero below L,
+// z its lowest nonzero digit. C may alias P.
+__device__ inline void negate_at(const Blk& b, uint32_t* C, int L, const uint32_t* P, int np, int z) {
+  for (int i = b.tid; i < L; i += b.nt) {
+    const uint32_t p = i < np ? P[i] : 0u;
+    C[i] = (i < z) ? 0u : ((i == z) ? (0u - p) : ~p);
+  }
+  b.sync();
 }
 
 // C <- B^L - P over L digits, P (np digits, zero-extended) nonzero below L.
@@ -344,9 +420,9 @@ __host__ __device__ __forceinline__ unsigned long long pair_count(int na, int nb
 // strips alternately left and right of it by distance. The band [ws0, nws) is
 // the part of the product that is computed.
 __device__ __forceinline__ int strip_order(int idx, int ws0, int nws, int na, int nb, int WSPAN) {
-  int lo = (nb - 1) / WSPAN;  // first strip whose rows reach nb
+  int lo = (min(na, nb) - 1) / WSPAN;  // first strip whose rows reach the shorter length
   if (lo < 0) lo = 0;
-  int hi = (na - 1) / WSPAN;  // last strip before the ramp down
+  int hi = (max(na, nb) - 1) / WSPAN;  // last strip before the ramp down
   lo = min(max(lo, ws0), nws - 1);
   hi = min(max(hi, ws0), nws - 1);
   if (hi < lo) hi = lo;
@@ -393,14 +469,17 @@ __device__ __forceinline__ void mul_t(const Blk& b, uint32_t* C, int npos, uint3
 // holding plo; carries from products below that strip are dropped (plo = 0:
 // the exact product modulo B^npos). X (nx digits) and Y (ny digits) are
 // multiply operands: PAD zero digits must be addressable below index 0 and
-// above the digit count (the high pads are zeroed here). OV needs
+// above the digit count (the high pads are zeroed here); an operand passed
+// with x_rows needs only T_MAX zero digits above its count. OV needs
 // 2 * (ceil(npos / T_MIN) + 32) words. C must not alias X or Y.
 __device__ inline void mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int nx, uint32_t* Y, int ny, uint32_t* OV,
-                           int plo = 0) {
+                           int plo = 0, bool x_rows = false) {
+  // the longer operand is the window operand unless X must be the row operand
+  // (x_rows: X has no zero digits below index 0, only T_MAX above nx)
   uint32_t* A = X;
   uint32_t* Bv = Y;
   int na = nx, nb = ny;
-  if (nb > na) {
+  if (x_rows || nb > na) {
     A = Y;
     Bv = X;
     na = ny;

@@ -172,16 +172,18 @@ __device__ inline int shinv(const Blk& b, const Layout& L, int h, int kl, int* l
   uint32_t* X = L.X;
   uint32_t* P = L.P;
   uint32_t* R = L.R;
+  int pw = prec(b, W, lw);
   for (int it = 0; it < nit; it++) {
     const int m = min(h - k + 1 - ell, ell);
     const int s = max(0, k - 2 * ell + 1 - g);
     const int hh = k + ell + m - s + g;  // Step's h
     const int e = hh - 2 * m;            // digits Step drops from w*x
     if (m < 0 || e < 1) return ST_INTERNAL;
-    const int pv = kl - s;               // prec of v' = shift_{-s}(v)
+    // v' = shift_{-s}(v), copied so that it can be the product's window
+    // operand (zero digits below it); its top digit is v's: prec(v') = kl - s
+    const int pv = kl - s;
     if (pv > L.capX) return ST_INTERNAL;
     copy(b, X, pv, [&](int i) { return V[s + i]; });
-    const int pw = prec(b, W, lw);
     // ---- PowDiff(v', w, hp, ellp): (sign, |B^hp - v' w|)
     const int hp = hh - m;
     const int ellp = ell - g;
@@ -208,24 +210,26 @@ __device__ inline int shinv(const Blk& b, const Layout& L, int h, int kl, int* l
         sub_pow(b, X, hp, np);
         px = np;
       }
+      px = (px > 0) ? prec(b, X, px) : 0;
     } else {
       if (Lc > L.capP || Lc > L.capX) return ST_INTERNAL;
       mul(b, P, Lc, X, pv, W, pw, L.OV);  // MultMod: v' w mod B^L
-      const int top = find_last(b, 0, Lc, [&](int i) { return P[i] != 0u; });
-      if (top < 0) {
+      // one pass gives the sign test, the negation's pivot and |x|'s length
+      int z, t1, t2;
+      scan3(b, P, Lc, &z, &t1, &t2);
+      if (t1 < 0) {
         sign = 1;
         px = 0;
-      } else if (top < Lc - 1) {
+      } else if (t1 < Lc - 1) {  // top digit P_{L-1} = 0: v' w > B^hp, x = P
         sign = 0;
-        copy(b, X, Lc, [&](int i) { return P[i]; });
-        px = Lc;
-      } else {
+        copy(b, X, t1 + 1, [&](int i) { return P[i]; });
+        px = t1 + 1;
+      } else {  // x = B^L - P: digits above z are the complements of P's
         sign = 1;
-        negate(b, X, Lc, P, Lc);
-        px = Lc;
+        negate_at(b, X, Lc, P, Lc, z);
+        px = max(t2, z) + 1;
       }
     }
-    px = (px > 0) ? prec(b, X, px) : 0;
     // ---- Step: res = w B^m +/- shift_{2m-hh}(w x), floor semantics
     int lr;
     if (px == 0) {
@@ -252,7 +256,7 @@ __device__ inline int shinv(const Blk& b, const Layout& L, int h, int kl, int* l
     const int d = (it < 2) ? m : 1;
     lw = max(lr - d, 0);
     if (lw > L.capW) return ST_INTERNAL;
-    copy(b, W, lw, [&](int i) { return R[i + d]; });
+    pw = copy_prec(b, W, lw, [&](int i) { return R[i + d]; });
     if (it >= 2) ell = ell + m - 1;
   }
   // final shift of Refine: h-k-4 digits when h-k < 2, else -2
@@ -332,9 +336,8 @@ __device__ inline int div_item(const Blk& b, uint32_t* sm, int smem_words, const
   mul(b, P, np, U, h, W, lw, L.OV, full ? 0 : max(0, h - QGUARD));
   int lq = np - h;
   if (lq + 1 > L.capW) return ST_INTERNAL;
-  copy(b, W, lq, [&](int i) { return P[h + i]; });  // q lives in W from here
-  if (b.tid == 0) W[lq] = 0u;
-  lq = prec(b, W, lq);
+  // q lives in W from here (one zero digit above it for a later +1)
+  lq = copy_prec(b, W, lq + 1, [&](int i) { return i < np - h ? P[h + i] : 0u; });
   uint32_t* V = L.V;
   int lr;
   if (full) {
@@ -368,9 +371,20 @@ __device__ inline int div_item(const Blk& b, uint32_t* sm, int smem_words, const
       if (t == 2) return ST_CORR;
       if (!sub_pow(b, W, 0, lq)) return ST_INTERNAL;
       addsub<false>(b, P, K1, [&](int i) { return P[i]; }, [&](int i) { return i < kl ? V[i] : 0u; }, 0u);
-      lq = prec(b, W, lq);
     }
-    lr = K1;
+    // ---- if r >= v: q += 1, r -= v   (Theorem 2: delta = +1); r < B^(kl+1)
+    for (int t = 0;; t++) {
+      if (cmp(b, P, K1, V, kl) < 0) break;
+      if (t == 2) return ST_CORR;
+      if (!add_pow(b, W, 0, lq + 1)) return ST_INTERNAL;
+      lq = lq + 1;  // a bound: q may have grown by a digit
+      addsub<true>(b, P, K1, [&](int i) { return P[i]; }, [&](int i) { return i < kl ? V[i] : 0u; }, 0u);
+    }
+    // r < v has at most kl <= rn digits; q's digits above its bound lq are zero
+    if (lq > io.qn) lq = prec(b, W, lq);
+    store_digits(b, io.q, io.qn, W, lq);
+    store_digits(b, io.r, io.rn, P, min(K1, io.rn));
+    return lq > io.qn ? ST_QOVF : ST_OK;
   }
   // ---- if r >= v: q += 1, r -= v   (Theorem 2: delta = +1)
   lr = prec(b, P, lr);
