@@ -273,6 +273,7 @@ def run_sweep(args, dev, dist, rank, ws):
             "Tprod_per_s": d["products"] / (per_size_ms[i] / 1e3) / 1e12,
             "warps_per_block": tuned[d["n"]],
             "mul_columns": mp.mpdiv_tuning(ctx, d["n"])[1],
+            "karatsuba_cutoff": mp.mpdiv_tuning(ctx, d["n"])[2],
         }
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,

@@ -69,6 +69,9 @@ typedef struct mpdiv_config {
   int flags;           /* MPDIV_FLAG_* */
   int mul_columns;     /* output columns per lane of the strip multiply: 3, 5 or 7; 0: per
                           size class from the tuning table */
+  int karatsuba_cutoff; /* one Karatsuba level for full products whose shorter operand has
+                           at least this many digits (> 0); -1: never; 0: per size class from
+                           the tuning table (never if untuned) */
 } mpdiv_config;
 
 /* Create a context on CUDA device `device` (cfg may be NULL for defaults).
@@ -127,16 +130,18 @@ int mpdiv_debug_shinv(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *v, int32_
 
 /* Tuning: time the plain kernel for the given (u_limbs, v_limbs) shape at each
  * candidate block size (4, 8, 16, 32 warps) and strip width (3, 5, 7 columns
- * per lane) on `n_items` synthetic divisions and keep the fastest in the
- * context's tuning table for that size class (used where cfg leaves the
+ * per lane), then at Karatsuba cutoffs (never, 2048, 1024, 512 digits), on
+ * `n_items` synthetic divisions and keep the fastest in the context's tuning
+ * table for that size class (used where cfg leaves the
  * choice open). Returns the chosen warps per block (> 0) or a negative error
  * code. Synchronous. */
 int mpdiv_autotune(mpdiv_ctx *ctx, int32_t u_limbs, int32_t v_limbs, int32_t n_items);
 
 /* The launch shape the context uses for dividends of u_limbs digits: warps per
- * block and output columns per lane of the strip multiply (tuned, configured
- * or default). Either pointer may be NULL. */
-int mpdiv_tuning(mpdiv_ctx *ctx, int32_t u_limbs, int32_t *warps, int32_t *mul_columns);
+ * block, output columns per lane of the strip multiply and the Karatsuba
+ * cutoff (0: never), tuned, configured or default. Any pointer may be NULL. */
+int mpdiv_tuning(mpdiv_ctx *ctx, int32_t u_limbs, int32_t *warps, int32_t *mul_columns,
+                 int32_t *karatsuba_cutoff);
 
 /* ---------------------------------------------------------------- serving
  * Continuous batching: a host scheduler thread admits submitted requests into

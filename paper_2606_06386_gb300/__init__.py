@@ -79,7 +79,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 class mpdiv_config(ctypes.Structure):
     _fields_ = [("warps_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("flags", ctypes.c_int),
-                ("mul_columns", ctypes.c_int)]
+                ("mul_columns", ctypes.c_int), ("karatsuba_cutoff", ctypes.c_int)]
 
 
 class mpdiv_serve_config(ctypes.Structure):
@@ -103,7 +103,7 @@ _SIGS = {
     "mpdiv_batch_ragged": (ctypes.c_int, [_P, _I64] + [_P] * 18),
     "mpdiv_debug_shinv": (ctypes.c_int, [_P, _I64, _P, _I32, _I64, _P, _P, _I32, _I64, _P, _P, _P]),
     "mpdiv_autotune": (ctypes.c_int, [_P, _I32, _I32, _I32]),
-    "mpdiv_tuning": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "mpdiv_tuning": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "mpdiv_serve_start": (ctypes.c_int, [_P, ctypes.POINTER(mpdiv_serve_config)]),
     "mpdiv_serve_submit": (ctypes.c_int, [_P, _P, _I32, _P, _I32, ctypes.POINTER(_U64)]),
     "mpdiv_serve_poll": (ctypes.c_int, [_P, _U64, _P, _I32, _P, _I32, ctypes.POINTER(_I32), _I64]),
@@ -173,8 +173,8 @@ def _check_dev(*ts):
 
 # ---------------------------------------------------------------- context
 def mpdiv_init(device: int = 0, warps_per_block: int = 0, blocks_per_sm: int = 0, flags: int = 0,
-               mul_columns: int = 0):
-    cfg = mpdiv_config(warps_per_block, blocks_per_sm, flags, mul_columns)
+               mul_columns: int = 0, karatsuba_cutoff: int = 0):
+    cfg = mpdiv_config(warps_per_block, blocks_per_sm, flags, mul_columns, karatsuba_cutoff)
     h = _P()
     _check(None, lib().mpdiv_init(ctypes.byref(h), device, ctypes.byref(cfg)))
     return h
@@ -257,10 +257,10 @@ def mpdiv_autotune(ctx, u_limbs: int, v_limbs: int, n_items: int) -> int:
 
 
 def mpdiv_tuning(ctx, u_limbs: int):
-    """(warps per block, columns per lane) used for dividends of u_limbs digits."""
-    w, t = _I32(), _I32()
-    _check(ctx, lib().mpdiv_tuning(ctx, u_limbs, ctypes.byref(w), ctypes.byref(t)))
-    return w.value, t.value
+    """(warps per block, columns per lane, Karatsuba cutoff) used for dividends of u_limbs digits."""
+    w, t, k = _I32(), _I32(), _I32()
+    _check(ctx, lib().mpdiv_tuning(ctx, u_limbs, ctypes.byref(w), ctypes.byref(t), ctypes.byref(k)))
+    return w.value, t.value, k.value
 
 
 # ---------------------------------------------------------------- serving

@@ -17,6 +17,7 @@ struct UniformArgs {
   int smem_words;
   int flags;
   int tcols;  // columns per lane of the strip multiply
+  int kcut;   // Karatsuba cutoff for full products (0: schoolbook only)
 };
 
 struct RaggedArgs {
@@ -44,6 +45,8 @@ struct RaggedArgs {
   int tcols;            // columns per lane (0 in k_div_persistent: chosen per item)
   int tcols_class[4];   // k_div_persistent: columns per lane for dividends of <= 1024,
                         // 2048, 4096 and more digits
+  int kcut;             // Karatsuba cutoff for full products (0: schoolbook only)
+  int kcut_class[4];    // k_div_persistent: the cutoff per size class (when kcut < 0)
 };
 
 struct ShinvArgs {
@@ -56,6 +59,7 @@ struct ShinvArgs {
   int vn, on;
   int smem_words;
   int tcols;
+  int kcut;
 };
 
 }  // namespace mp

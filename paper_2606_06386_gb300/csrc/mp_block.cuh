@@ -49,6 +49,7 @@ struct Blk {
   int* red;  // RED_WORDS ints of shared scratch owned by this group
   unsigned long long* work;  // thread 0's running count of algorithmic digit products (may be null)
   int tcols;                 // columns per lane of the strip multiply (3, 5 or 7)
+  int kcut;                  // Karatsuba for full products whose shorter operand has >= kcut digits (0: never)
 
   __device__ __forceinline__ void sync() const {
     asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
@@ -67,6 +68,7 @@ __device__ __forceinline__ Blk make_group(int* red, int w0, int nw, int bar) {
   b.red = red;
   b.work = nullptr;
   b.tcols = 5;
+  b.kcut = 0;
   return b;
 }
 
@@ -505,6 +507,114 @@ __device__ inline void mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int
     mul_t<7>(b, C, npos, A, na, Bv, nb, OV, plo);
   else
     mul_t<5>(b, C, npos, A, na, Bv, nb, OV, plo);
+}
+
+// ---------------------------------------------------------------- Karatsuba
+// Save n digits at p into sv and zero them (and the reverse).
+__device__ inline void save_zero(const Blk& b, uint32_t* sv, uint32_t* p, int n) {
+  for (int i = b.tid; i < n; i += b.nt) {
+    sv[i] = p[i];
+    p[i] = 0u;
+  }
+  b.sync();
+}
+__device__ inline void restore(const Blk& b, uint32_t* p, const uint32_t* sv, int n) {
+  for (int i = b.tid; i < n; i += b.nt) p[i] = sv[i];
+  b.sync();
+}
+
+// Scratch words kara() needs when its longer operand has n digits.
+__host__ __device__ __forceinline__ int kara_words(int n) { return 3 * PAD + 4 * ((n + 1) / 2) + 2 * T_MAX + 16; }
+
+// C[0..na+nb) = A * B by one level of Karatsuba: with m = ceil(na/2) and
+// A = A1 B^m + A0, B = B1 B^m + B0, C = Z2 B^2m + (Z1 - Z0 - Z2) B^m + Z0 with
+// Z0 = A0 B0, Z2 = A1 B1, Z1 = (A0 + A1)(B0 + B1); the three products are
+// strip products with A's parts as row operands and B's as window operands.
+// Requires m < nb <= na and m >= PAD. A needs T_MAX zero digits above it, B
+// PAD zero digits on both sides; the views B0, B1 and A0 borrow theirs by
+// saving, zeroing and restoring the digits around the split.
+// S: kara_words(na) scratch words.
+__device__ inline void kara(const Blk& b, uint32_t* C, uint32_t* A, int na, uint32_t* B, int nb, uint32_t* OV,
+                            uint32_t* S) {
+  const int m = (na + 1) / 2, ha = na - m, hb = nb - m;
+  uint32_t* SB = S + PAD;                  // B0 + B1: m + 1 digits, PAD zeros each side
+  uint32_t* SA = SB + m + 1 + PAD;         // A0 + A1: m + 1 digits, T_MAX zeros above
+  uint32_t* TZ = SA + m + 1 + T_MAX;       // Z1: 2m + 2 digits
+  uint32_t* SV = TZ + 2 * m + 2 + 4;       // saved digits: PAD + T_MAX
+  for (int i = b.tid; i < PAD; i += b.nt) S[i] = 0u;
+  const uint32_t ca = addsub<false>(b, SA, m, [&](int i) { return A[i]; },
+                                    [&](int i) { return i < ha ? A[m + i] : 0u; }, 0u);
+  const uint32_t cb = addsub<false>(b, SB, m, [&](int i) { return B[i]; },
+                                    [&](int i) { return i < hb ? B[m + i] : 0u; }, 0u);
+  if (b.tid == 0) {
+    SA[m] = ca;
+    SB[m] = cb;
+  }
+  b.sync();
+  mul(b, TZ, 2 * m + 2, SA, m + 1, SB, m + 1, OV, 0, true);
+  // Z0 = A0 B0 into C[0, 2m): A0 and B0 end at the split
+  save_zero(b, SV, B + m, PAD);
+  save_zero(b, SV + PAD, A + m, T_MAX);
+  mul(b, C, 2 * m, A, m, B, m, OV, 0, true);
+  restore(b, B + m, SV, PAD);
+  restore(b, A + m, SV + PAD, T_MAX);
+  // Z2 = A1 B1 into C[2m, na + nb): B1 starts at the split
+  save_zero(b, SV, B + m - PAD, PAD);
+  mul(b, C + 2 * m, ha + hb, A + m, ha, B + m, hb, OV, 0, true);
+  restore(b, B + m - PAD, SV, PAD);
+  // Z1 - Z0 - Z2, added at digit m
+  addsub<true>(b, TZ, 2 * m + 2, [&](int i) { return TZ[i]; }, [&](int i) { return i < 2 * m ? C[i] : 0u; }, 0u);
+  addsub<true>(b, TZ, 2 * m + 2, [&](int i) { return TZ[i]; },
+               [&](int i) { return i < ha + hb ? C[2 * m + i] : 0u; }, 0u);
+  addsub<false>(b, C + m, na + nb - m, [&](int i) { return C[m + i]; },
+                [&](int i) { return i < 2 * m + 2 ? TZ[i] : 0u; }, 0u);
+}
+
+// C[0..nx+ny) = X * Y exactly. When the shorter operand has at least b.kcut
+// digits (and 2 PAD), one Karatsuba level replaces the strip product: directly
+// for operands within 4:3 of each other, else on square chunks of the longer
+// operand (each chunk times the shorter, added at its offset). Scratch: S
+// (s_words) for Karatsuba, TC (tc_words) for a chunk product; when either is
+// too small the strip product is used. X and Y are multiply operands (PAD zero
+// digits on both sides). Karatsuba's digit products are counted in b.work.
+__device__ inline void mul_full(const Blk& b, uint32_t* C, uint32_t* X, int nx, uint32_t* Y, int ny, uint32_t* OV,
+                                uint32_t* S, int s_words, uint32_t* TC, int tc_words) {
+  uint32_t* A = X;
+  uint32_t* Bv = Y;
+  int na = nx, nb = ny;
+  if (nb > na) {
+    A = Y;
+    Bv = X;
+    na = ny;
+    nb = nx;
+  }
+  const bool square = 4 * nb >= 3 * na;
+  if (b.kcut <= 0 || nb < b.kcut || nb < 2 * PAD || (square && kara_words(na) > s_words) ||
+      (!square && (kara_words(nb) + T_MAX > s_words || 2 * nb + 2 > tc_words))) {
+    mul(b, C, nx + ny, X, nx, Y, ny, OV);
+    return;
+  }
+  if (square) {
+    kara(b, C, A, na, Bv, nb, OV, S);
+    return;
+  }
+  // chunks A_k = A[k0, k0 + lk), lk = min(nb, na - k0), times B, added at digit k0
+  uint32_t* SV = S + kara_words(nb);  // A's digits above a chunk: T_MAX
+  for (int i = b.tid; i < na + nb; i += b.nt) C[i] = 0u;
+  b.sync();
+  for (int k0 = 0; k0 < na; k0 += nb) {
+    const int lk = min(nb, na - k0);
+    uint32_t* Ak = A + k0;
+    const bool last = k0 + lk >= na;
+    if (!last) save_zero(b, SV, Ak + lk, T_MAX);
+    if (lk == nb)
+      kara(b, TC, Ak, nb, Bv, nb, OV, S);
+    else
+      mul(b, TC, lk + nb, Ak, lk, Bv, nb, OV, 0, true);
+    if (!last) restore(b, Ak + lk, SV, T_MAX);
+    addsub<false>(b, C + k0, na + nb - k0, [&](int i) { return C[k0 + i]; },
+                  [&](int i) { return i < lk + nb ? TC[i] : 0u; }, 0u);
+  }
 }
 
 }  // namespace mp

@@ -239,7 +239,10 @@ __device__ inline int shinv(const Blk& b, const Layout& L, int h, int kl, int* l
     } else {
       const int nt = pw + px;
       if (nt > L.capP) return ST_INTERNAL;
-      mul(b, P, nt, W, pw, X, px, L.OV);
+      // Karatsuba scratch: the product buffer's free tail, and R (free until
+      // Step's sum below) for chunk products
+      const int sa = (nt + 3) & ~3;
+      mul_full(b, P, W, pw, X, px, L.OV, P + sa, L.capP - sa, R, L.capR);
       lr = max(pw + m, nt - e) + 1;
       if (lr > L.capR) return ST_INTERNAL;
       auto wm = [&](int i) -> uint32_t { return (i >= m && i - m < pw) ? W[i - m] : 0u; };

@@ -14,6 +14,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_uniform(UniformArgs a) {
   __shared__ int red[RED_WORDS];
   Blk b = make_blk(red);
   b.tcols = a.tcols;
+  b.kcut = a.kcut;
   for (int64_t item = blockIdx.x; item < a.n; item += gridDim.x) {
     ItemIO io;
     io.u = a.u + item * a.us;
@@ -46,6 +47,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_ragged(RaggedArgs a) {
   __shared__ int red[RED_WORDS];
   Blk b = make_blk(red);
   b.tcols = a.tcols > 0 ? a.tcols : 5;
+  b.kcut = a.kcut > 0 ? a.kcut : 0;
   while (true) {
     if (b.tid == 0) red[RED_AUX] = atomicAdd(a.head, 1);
     b.sync();
@@ -139,7 +141,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_persistent(RaggedArgs a) 
     unsigned long long work = 0ull;
     Blk bw = b;
     bw.work = a.products ? &work : nullptr;
-    bw.tcols = a.tcols > 0 ? a.tcols : a.tcols_class[ul <= 1024 ? 0 : ul <= 2048 ? 1 : ul <= 4096 ? 2 : 3];
+    const int cls = ul <= 1024 ? 0 : ul <= 2048 ? 1 : ul <= 4096 ? 2 : 3;
+    bw.tcols = a.tcols > 0 ? a.tcols : a.tcols_class[cls];
+    bw.kcut = a.kcut >= 0 ? a.kcut : a.kcut_class[cls];
     const int st = div_item(bw, base, words, io, a.flags, &it, nullptr, 0, 0);
     if (b.tid == 0) {
       a.status[item] = st;
@@ -157,6 +161,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_shinv(ShinvArgs a) {
   __shared__ int red[RED_WORDS];
   Blk b = make_blk(red);
   b.tcols = a.tcols > 0 ? a.tcols : 5;
+  b.kcut = a.kcut > 0 ? a.kcut : 0;
   for (int64_t item = blockIdx.x; item < a.n; item += gridDim.x) {
     ItemIO io;
     io.u = nullptr;

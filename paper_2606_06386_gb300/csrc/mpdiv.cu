@@ -66,7 +66,7 @@ int mpdiv_default_warps(mpdiv_ctx* ctx, int max_digits) {
     std::lock_guard<std::mutex> g(ctx->tune_mu);
     const int cls = mpdiv_size_class(max_digits);
     auto it = ctx->tuned.find(cls);
-    if (it != ctx->tuned.end()) return it->second.first;
+    if (it != ctx->tuned.end()) return it->second.warps;
   }
   if (max_digits <= 2048) return 4;
   if (max_digits <= 4096) return 8;
@@ -78,9 +78,19 @@ int mpdiv_default_tcols(mpdiv_ctx* ctx, int max_digits) {
   {
     std::lock_guard<std::mutex> g(ctx->tune_mu);
     auto it = ctx->tuned.find(mpdiv_size_class(max_digits));
-    if (it != ctx->tuned.end()) return it->second.second;
+    if (it != ctx->tuned.end()) return it->second.tcols;
   }
   return 3;  // measured fastest at every size class on GB300 (mpdiv_autotune)
+}
+
+int mpdiv_default_kcut(mpdiv_ctx* ctx, int max_digits) {
+  if (ctx->cfg.karatsuba_cutoff != 0) return ctx->cfg.karatsuba_cutoff < 0 ? 0 : ctx->cfg.karatsuba_cutoff;
+  {
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    auto it = ctx->tuned.find(mpdiv_size_class(max_digits));
+    if (it != ctx->tuned.end()) return it->second.kcut;
+  }
+  return 0;  // untuned: schoolbook only
 }
 
 int mpdiv_size_class(int digits) {
@@ -171,6 +181,7 @@ int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t st
   a.smem_words = smem / 4;
   a.flags = ctx->cfg.flags;
   a.tcols = L.tcols > 0 ? L.tcols : mpdiv_default_tcols(ctx, max_digits);
+  a.kcut = L.kcut >= 0 ? L.kcut : mpdiv_default_kcut(ctx, max_digits);
   const int64_t grid = std::min<int64_t>(L.n, 0x7fffffff);
   void* args[] = {&a};
   cudaError_t e = cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * warps), args, smem, stream);
@@ -212,6 +223,7 @@ extern "C" int mpdiv_batch(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* u, i
   L.rn = r_limbs;
   L.warps = 0;
   L.tcols = 0;
+  L.kcut = -1;
   return mpdiv_launch_uniform(ctx, L, (cudaStream_t)stream);
 }
 
@@ -303,6 +315,8 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
   a.split_digits[1] = ctx->split_digits[1];
   a.tcols = L.split ? ctx->cfg.mul_columns : mpdiv_default_tcols(ctx, max_u);
   for (int c = 0; c < 4; c++) a.tcols_class[c] = mpdiv_default_tcols(ctx, 1024 << c);
+  for (int c = 0; c < 4; c++) a.kcut_class[c] = mpdiv_default_kcut(ctx, 1024 << c);
+  a.kcut = L.split ? -1 : mpdiv_default_kcut(ctx, max_u);
   if (!L.use_graph) {
     if ((rc = mpdiv_cuda_check(ctx, cudaMemsetAsync(a.head, 0, sizeof(int32_t), stream), "queue reset"))) return rc;
     void* args[] = {&a};
@@ -423,6 +437,7 @@ extern "C" int mpdiv_debug_shinv(mpdiv_ctx* ctx, int64_t n_items, const uint32_t
   a.on = out_limbs;
   a.smem_words = smem / 4;
   a.tcols = ctx->cfg.mul_columns > 0 ? ctx->cfg.mul_columns : 5;
+  a.kcut = ctx->cfg.karatsuba_cutoff > 0 ? ctx->cfg.karatsuba_cutoff : 0;
   void* args[] = {&a};
   const int64_t grid = std::min<int64_t>(n_items, 0x7fffffff);
   return mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * warps), args, smem,
@@ -430,9 +445,11 @@ extern "C" int mpdiv_debug_shinv(mpdiv_ctx* ctx, int64_t n_items, const uint32_t
                           "launch of the shifted-inverse kernel");
 }
 
-extern "C" int mpdiv_tuning(mpdiv_ctx* ctx, int32_t u_limbs, int32_t* warps, int32_t* mul_columns) {
+extern "C" int mpdiv_tuning(mpdiv_ctx* ctx, int32_t u_limbs, int32_t* warps, int32_t* mul_columns,
+                            int32_t* karatsuba_cutoff) {
   if (!ctx || u_limbs < 1) return MPDIV_EINVAL;
   if (warps) *warps = mpdiv_default_warps(ctx, u_limbs);
   if (mul_columns) *mul_columns = mpdiv_default_tcols(ctx, u_limbs);
+  if (karatsuba_cutoff) *karatsuba_cutoff = mpdiv_default_kcut(ctx, u_limbs);
   return MPDIV_OK;
 }

@@ -18,13 +18,15 @@ struct mpdiv_ctx {
   int device = 0;
   int num_sms = 0;
   int max_smem = 0;
-  mpdiv_config cfg{0, 0, 0, 0};
+  mpdiv_config cfg{0, 0, 0, 0, 0};
   mutable std::mutex err_mu;
   std::string err;
-  // tuning table: size class (digits, power of two >= 1024) -> (warps per
-  // block, columns per lane of the strip multiply)
+  // tuning table: size class (digits, power of two >= 1024) -> launch shape
   std::mutex tune_mu;
-  std::map<int, std::pair<int, int>> tuned;
+  struct Shape {
+    int warps, tcols, kcut;
+  };
+  std::map<int, Shape> tuned;
   // persistent launch: queue head, cached order, cached graph
   std::mutex ragged_mu;
   int32_t* d_head = nullptr;
@@ -54,6 +56,7 @@ struct UniformLaunch {
   int un, vn, qn, rn;
   int warps;  // 0: from the tuning table
   int tcols;  // 0: from the tuning table
+  int kcut;   // -1: from the tuning table; 0: schoolbook only
 };
 
 struct RaggedLaunch {
@@ -87,6 +90,7 @@ int mpdiv_smem_bytes(int max_digits);
 int mpdiv_size_class(int digits);
 int mpdiv_default_warps(mpdiv_ctx* ctx, int max_digits);
 int mpdiv_default_tcols(mpdiv_ctx* ctx, int max_digits);
+int mpdiv_default_kcut(mpdiv_ctx* ctx, int max_digits);
 int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t stream);
 int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stream);
 void mpdiv_tune_load(mpdiv_ctx* ctx, const char* path);

@@ -2,8 +2,9 @@
 // autotuning of block size, sequentialisation and multiplication
 // specialisation as future work): for a size class it times the plain kernel
 // at each candidate warps per block (4, 8, 16, 32) and columns per lane of the
-// strip multiply (3, 5, 7) on synthetic divisions, and records the fastest in
-// the context's table, which can be saved to and loaded from a text file
+// strip multiply (3, 5, 7), then at Karatsuba cutoffs for the full products
+// (never, 2048, 1024, 512 digits), on synthetic divisions, and records the
+// fastest in the context's table, which can be saved to and loaded from a text file
 // (MPDIV_TUNE_FILE).
 #include <cstdio>
 #include <cstdlib>
@@ -34,10 +35,10 @@ __global__ void k_fill(uint32_t* x, int64_t n_items, int digits, int64_t stride,
 void mpdiv_tune_load(mpdiv_ctx* ctx, const char* path) {
   FILE* f = fopen(path, "r");
   if (!f) return;
-  int cls, w, t;
+  int cls, w, t, kc;
   std::lock_guard<std::mutex> g(ctx->tune_mu);
-  while (fscanf(f, "%d %d %d", &cls, &w, &t) == 3)
-    if (cls > 0 && w > 0 && w <= 32 && (t == 3 || t == 5 || t == 7)) ctx->tuned[cls] = {w, t};
+  while (fscanf(f, "%d %d %d %d", &cls, &w, &t, &kc) == 4)
+    if (cls > 0 && w > 0 && w <= 32 && (t == 3 || t == 5 || t == 7) && kc >= 0) ctx->tuned[cls] = {w, t, kc};
   fclose(f);
 }
 
@@ -45,7 +46,8 @@ static void tune_save(mpdiv_ctx* ctx, const char* path) {
   FILE* f = fopen(path, "w");
   if (!f) return;
   std::lock_guard<std::mutex> g(ctx->tune_mu);
-  for (auto& kv : ctx->tuned) fprintf(f, "%d %d %d\n", kv.first, kv.second.first, kv.second.second);
+  for (auto& kv : ctx->tuned)
+    fprintf(f, "%d %d %d %d\n", kv.first, kv.second.warps, kv.second.tcols, kv.second.kcut);
   fclose(f);
 }
 
@@ -60,7 +62,7 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
   const size_t n = (size_t)n_items;
   int rc = MPDIV_OK;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  int best_w = 0, best_t = 5;
+  int best_w = 0, best_t = 5, best_k = 0;
   float best_ms = 1e30f;
   if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&u, n * u_limbs * 4), "autotune alloc"))) goto done;
   if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&v, n * v_limbs * 4), "autotune alloc"))) goto done;
@@ -71,9 +73,13 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
   k_fill<<<256, 256>>>(v, n_items, v_limbs, v_limbs, 0x7654321ull);
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int cand = 0; cand < 12; cand++) {
-    const int w = 4 << (cand / 3);
-    const int tc = 3 + 2 * (cand % 3);
+  // warps x columns with schoolbook products, then the Karatsuba cutoff
+  // (0 = never, 2048, 1024, 512 digits) at the best shape
+  for (int cand = 0; cand < 15; cand++) {
+    const int w = cand < 12 ? 4 << (cand / 3) : best_w;
+    const int tc = cand < 12 ? 3 + 2 * (cand % 3) : best_t;
+    const int kc = cand < 12 ? 0 : (2048 >> (cand - 12));
+    if (cand >= 12 && best_w == 0) break;
     UniformLaunch L{};
     L.u = u;
     L.v = v;
@@ -90,6 +96,7 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
     L.rn = v_limbs;
     L.warps = w;
     L.tcols = tc;
+    L.kcut = kc;
     if (mpdiv_launch_uniform(ctx, L, 0) != MPDIV_OK) continue;  // e.g. does not fit
     cudaEventRecord(e0, 0);
     mpdiv_launch_uniform(ctx, L, 0);
@@ -102,6 +109,7 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
       best_ms = ms;
       best_w = w;
       best_t = tc;
+      best_k = kc;
     }
   }
   if (best_w == 0) {
@@ -110,7 +118,7 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
   }
   {
     std::lock_guard<std::mutex> g(ctx->tune_mu);
-    ctx->tuned[mpdiv_size_class(u_limbs)] = {best_w, best_t};
+    ctx->tuned[mpdiv_size_class(u_limbs)] = {best_w, best_t, best_k};
   }
   if (const char* tf = getenv("MPDIV_TUNE_FILE")) tune_save(ctx, tf);
   rc = best_w;

@@ -19,14 +19,14 @@ def host_u32(t):
 _ctx = {}
 
 
-def ctx(flags=0, warps=0, cols=0):
-    key = (flags, warps, cols)
+def ctx(flags=0, warps=0, cols=0, kcut=0):
+    key = (flags, warps, cols, kcut)
     if key not in _ctx:
-        _ctx[key] = mp.mpdiv_init(0, warps_per_block=warps, flags=flags, mul_columns=cols)
+        _ctx[key] = mp.mpdiv_init(0, warps_per_block=warps, flags=flags, mul_columns=cols, karatsuba_cutoff=kcut)
     return _ctx[key]
 
 
-def run_uniform(U, V, qn=None, rn=None, flags=0, warps=0, cols=0):
+def run_uniform(U, V, qn=None, rn=None, flags=0, warps=0, cols=0, kcut=0, products=False):
     """Divide row i of U by row i of V on the GPU. Returns (Q, R, status, iters)."""
     import torch
 
@@ -39,8 +39,11 @@ def run_uniform(U, V, qn=None, rn=None, flags=0, warps=0, cols=0):
     r = torch.full((n, rn), -1, dtype=torch.int32, device="cuda:0")
     st = torch.full((n,), -7, dtype=torch.int32, device="cuda:0")
     it = torch.full((n,), -1, dtype=torch.int32, device="cuda:0")
-    mp.mpdiv_batch(ctx(flags, warps, cols), dev(U), dev(V), q, r, st, it)
+    pr = torch.zeros((n,), dtype=torch.int64, device="cuda:0") if products else None
+    mp.mpdiv_batch(ctx(flags, warps, cols, kcut), dev(U), dev(V), q, r, st, it, pr)
     torch.cuda.synchronize()
+    if products:
+        return host_u32(q), host_u32(r), st.cpu().numpy(), it.cpu().numpy(), pr.cpu().numpy()
     return host_u32(q), host_u32(r), st.cpu().numpy(), it.cpu().numpy()
 
 

@@ -2,6 +2,8 @@
 graph replay), stress shapes at 2^18 bits, Theorem 2's delta = -1 path and the
 block-size tuner, all bit-exact against the CPU oracle."""
 
+import random
+
 import numpy as np
 import pytest
 
@@ -108,6 +110,50 @@ def test_every_launch_shape_is_exact(warps, cols):
     assert_same(Q, R, S, Qo, Ro, So)
 
 
+@pytest.mark.parametrize(
+    "n,kl,full,applies",
+    [(2048, 1024, False, False),  # the last step's scratch does not fit: strip products
+     (4096, 2048, False, True), (8192, 4096, False, True),  # 2:1 steps: square chunks
+     (3000, 1000, True, True),  # near-square last step
+     (5000, 2600, True, True), (6000, 3100, False, True), (2500, 2400, True, False)])
+def test_karatsuba_products_are_exact(n, kl, full, applies):
+    # one Karatsuba level on the Newton step's full product, forced on from 512
+    # digits: the same digits as the oracle, and fewer digit products than the
+    # strip products wherever it applies
+    import paper_2606_06386_gb300 as mp
+
+    U = I.uniform_batch(8, n, seed=n, stream=kl)
+    V = I.uniform_batch(8, kl, seed=n + 1, stream=kl)
+    flags = mp.MPDIV_FLAG_FULL_PRODUCTS if full else 0
+    Q, R, S, _, Pk = run_uniform(U, V, flags=flags, kcut=512, products=True)
+    Qo, Ro, So = oracle_uniform(U, V)
+    assert_same(Q, R, S, Qo, Ro, So)
+    _, _, _, _, Ps = run_uniform(U, V, flags=flags, kcut=-1, products=True)
+    if applies:
+        assert (Pk < Ps).all()
+    else:
+        assert (Pk == Ps).all()
+
+
+def test_karatsuba_keeps_the_shifted_inverse_of_the_model():
+    import torch
+    import paper_2606_06386_gb300 as mp
+
+    rnd = random.Random(41)
+    vs = [rnd.getrandbits(32 * 1500) | (1 << (32 * 1500 - 1)) for _ in range(4)]
+    V = np.stack([oracle.from_int(v, 1500) for v in vs])
+    out = torch.zeros((4, 1600), dtype=torch.int32, device="cuda:0")
+    it = torch.zeros(4, dtype=torch.int32, device="cuda:0")
+    st = torch.full((4,), -1, dtype=torch.int32, device="cuda:0")
+    h_t = torch.full((4,), 3000, dtype=torch.int32, device="cuda:0")
+    mp.mpdiv_debug_shinv(ctx(kcut=512), dev(V), h_t, out, it, st)
+    torch.cuda.synchronize()
+    O = host_u32(out)
+    for i, v in enumerate(vs):
+        assert st[i].item() == 0
+        assert oracle.to_int(O[i]) == M.shinv(v, 3000, 1 << 32)
+
+
 def test_autotune_picks_a_launch_shape():
     import paper_2606_06386_gb300 as mp
 
@@ -115,7 +161,7 @@ def test_autotune_picks_a_launch_shape():
     try:
         w = mp.mpdiv_autotune(c, 1024, 512, 1024)
         assert w in (4, 8, 16, 32)
-        tw, tc = mp.mpdiv_tuning(c, 1000)
-        assert tw == w and tc in (3, 5, 7)
+        tw, tc, kc = mp.mpdiv_tuning(c, 1000)
+        assert tw == w and tc in (3, 5, 7) and kc in (0, 512, 1024, 2048)
     finally:
         mp.mpdiv_destroy(c)
