@@ -223,6 +223,15 @@ def run_sweep(args, dev, dist, rank, ws):
                    for i in range(len(sizes))]
     items_step = sum(d["b"] for d in sizes)
     value = items_step * K * ws / (total_ms / 1e3)
+    # the paper's cost unit (Table 1, "Our Mul"): the n-digit product kept to n
+    # digits, same batch and block shape, for the division/multiplication ratio
+    mul_ms = []
+    for d in sizes:
+        vv = _to_dev(I.uniform_batch(d["b"], d["n"], seed=I.SEED_BASE + 5, stream=d["n"]), dev)
+        out_m = torch.empty((d["b"], d["n"]), dtype=torch.int32, device=dev)
+        mp.mpdiv_mul_batch(ctx, d["u"], vv, out_m, stream)
+        mul_ms.append(_time(lambda: mp.mpdiv_mul_batch(ctx, d["u"], vv, out_m, stream), stream, 5))
+        del vv, out_m
 
     # end to end through the C ABI with host buffers: H2D inputs, launches, D2H results
     pinned = []
@@ -271,6 +280,8 @@ def run_sweep(args, dev, dist, rank, ws):
             "digit_products_per_div": d["products"] / d["b"],
             "cost_units_per_div": d["products"] / d["b"] / (d["n"] * (d["n"] + 1) / 2),
             "Tprod_per_s": d["products"] / (per_size_ms[i] / 1e3) / 1e12,
+            "mul_ms": mul_ms[i],
+            "div_over_mul": per_size_ms[i] / mul_ms[i],
             "warps_per_block": tuned[d["n"]],
             "mul_columns": mp.mpdiv_tuning(ctx, d["n"])[1],
             "karatsuba_cutoff": mp.mpdiv_tuning(ctx, d["n"])[2],

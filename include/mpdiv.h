@@ -143,6 +143,15 @@ int mpdiv_autotune(mpdiv_ctx *ctx, int32_t u_limbs, int32_t v_limbs, int32_t n_i
 int mpdiv_tuning(mpdiv_ctx *ctx, int32_t u_limbs, int32_t *warps, int32_t *mul_columns,
                  int32_t *karatsuba_cutoff);
 
+/* The cost unit of the paper's multiplication count (Section 2.3, Fig. 3 and
+ * Table 1's "Our Mul"): out + i*out_stride gets (u_i * v_i) mod B^n, the
+ * product of two n-digit numbers kept to n digits (the digit pairs below n),
+ * one thread block per item, with the division path's strip multiply. u_i,
+ * v_i at u + i*stride, v + i*stride; all device pointers. Asynchronous on
+ * stream. n_limbs <= 2 * MPDIV_MAX_LIMBS. */
+int mpdiv_mul_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, const uint32_t *v, int32_t n_limbs,
+                    int64_t stride, uint32_t *out, int64_t out_stride, void *stream);
+
 /* ---------------------------------------------------------------- serving
  * Continuous batching: a host scheduler thread admits submitted requests into
  * device-resident operand pools (by digit footprint), launches batches of

@@ -103,6 +103,7 @@ _SIGS = {
     "mpdiv_batch_ragged": (ctypes.c_int, [_P, _I64] + [_P] * 18),
     "mpdiv_debug_shinv": (ctypes.c_int, [_P, _I64, _P, _I32, _I64, _P, _P, _I32, _I64, _P, _P, _P]),
     "mpdiv_autotune": (ctypes.c_int, [_P, _I32, _I32, _I32]),
+    "mpdiv_mul_batch": (ctypes.c_int, [_P, _I64, _P, _P, _I32, _I64, _P, _I64, _P]),
     "mpdiv_tuning": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "mpdiv_serve_start": (ctypes.c_int, [_P, ctypes.POINTER(mpdiv_serve_config)]),
     "mpdiv_serve_submit": (ctypes.c_int, [_P, _P, _I32, _P, _I32, ctypes.POINTER(_U64)]),
@@ -250,6 +251,15 @@ def mpdiv_debug_shinv(ctx, v, h_digits, out, iters, status, stream=None) -> None
             _ptr(iters), _ptr(status), _stream(stream),
         ),
     )
+
+
+def mpdiv_mul_batch(ctx, u, v, out, stream=None) -> None:
+    """out[i] = (u[i] * v[i]) mod B^n for (items, n) CUDA tensors (the cost unit)."""
+    _check_dev(u, v, out)
+    if u.shape != v.shape or out.shape[0] != u.shape[0] or out.shape[1] < u.shape[1]:
+        raise ValueError("shape mismatch")
+    _check(ctx, lib().mpdiv_mul_batch(ctx, u.shape[0], _ptr(u), _ptr(v), u.shape[1], u.stride(0), _ptr(out),
+                                      out.stride(0), _stream(stream)))
 
 
 def mpdiv_autotune(ctx, u_limbs: int, v_limbs: int, n_items: int) -> int:

@@ -154,6 +154,29 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_persistent(RaggedArgs a) 
   }
 }
 
+// The cost unit of the paper's multiplication count (Section 2.3, Fig. 3): the
+// product of two n-digit numbers kept to n digits, one per block.
+template <int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_mul_low(UniformArgs a) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ int red[RED_WORDS];
+  Blk b = make_blk(red);
+  b.tcols = a.tcols;
+  const int n = a.un;
+  uint32_t* X = sm + PAD;
+  uint32_t* Y = X + n + PAD;
+  uint32_t* P = Y + n + PAD;
+  uint32_t* OV = P + n + 4;
+  for (int64_t item = blockIdx.x; item < a.n; item += gridDim.x) {
+    for (int i = b.tid; i < PAD; i += b.nt) sm[i] = 0u;
+    load_global(b, X, n, [&](int i) { return a.u[item * a.us + i]; });
+    load_global(b, Y, n, [&](int i) { return a.v[item * a.vs + i]; });
+    mul(b, P, n, X, n, Y, n, OV);
+    store_digits(b, a.q + item * a.qs, n, P, n);
+    b.sync();
+  }
+}
+
 // Test entry: shinv_h(v) as the division path computes it.
 template <int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_shinv(ShinvArgs a) {

@@ -24,7 +24,13 @@ using namespace mp;
 // ------------------------------------------------------------------ kernels
 namespace {
 
-enum KernKind { KK_UNIFORM = MP_K_UNIFORM, KK_RAGGED = MP_K_RAGGED, KK_SHINV = MP_K_SHINV, KK_PERSIST = MP_K_PERSIST };
+enum KernKind {
+  KK_UNIFORM = MP_K_UNIFORM,
+  KK_RAGGED = MP_K_RAGGED,
+  KK_SHINV = MP_K_SHINV,
+  KK_PERSIST = MP_K_PERSIST,
+  KK_MUL = MP_K_MUL
+};
 
 // Instantiations by block size (mpdiv_k*.cu); the minimum-blocks bound caps
 // registers at 64 per thread so that several blocks of the smaller size
@@ -452,4 +458,41 @@ extern "C" int mpdiv_tuning(mpdiv_ctx* ctx, int32_t u_limbs, int32_t* warps, int
   if (mul_columns) *mul_columns = mpdiv_default_tcols(ctx, u_limbs);
   if (karatsuba_cutoff) *karatsuba_cutoff = mpdiv_default_kcut(ctx, u_limbs);
   return MPDIV_OK;
+}
+
+// ------------------------------------------------------------------ multiplication (cost unit)
+extern "C" int mpdiv_mul_batch(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* u, const uint32_t* v, int32_t n_limbs,
+                               int64_t stride, uint32_t* out, int64_t out_stride, void* stream) {
+  if (!ctx) return MPDIV_EINVAL;
+  if (n_items < 0) return mpdiv_set_error(ctx, MPDIV_EINVAL, "n_items < 0");
+  if (n_items == 0) return MPDIV_OK;
+  if (!u || !v || !out) return mpdiv_set_error(ctx, MPDIV_EINVAL, "null pointer argument");
+  if (n_limbs < 1 || stride < n_limbs || out_stride < n_limbs) return mpdiv_set_error(ctx, MPDIV_EINVAL, "bad sizes");
+  if (n_limbs > 2 * MPDIV_MAX_LIMBS) return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "too many digits");
+  cudaSetDevice(ctx->device);
+  const int n = n_limbs;
+  const int tc = mpdiv_default_tcols(ctx, n);
+  const int words = 4 * PAD + 3 * n + 8 + 2 * ((n + T_MIN - 1) / T_MIN + 64);
+  const int smem = (words * 4 + 15) & ~15;
+  if (smem > ctx->max_smem) return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory", smem);
+  const int warps = mpdiv_default_warps(ctx, n);
+  void* k = kernel_for(KK_MUL, warps);
+  int rc = prepare_kernel(ctx, k, smem);
+  if (rc) return rc;
+  UniformArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.u = u;
+  a.v = v;
+  a.q = out;
+  a.n = n_items;
+  a.us = stride;
+  a.vs = stride;
+  a.qs = out_stride;
+  a.un = n;
+  a.tcols = tc;
+  void* args[] = {&a};
+  const int64_t grid = std::min<int64_t>(n_items, 0x7fffffff);
+  return mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * warps), args, smem,
+                                                (cudaStream_t)stream),
+                          "launch of the multiplication kernel");
 }

@@ -1,7 +1,7 @@
 // Getters for the kernel instantiations of each block size (mpdiv_k*.cu).
 #pragma once
 
-enum { MP_K_UNIFORM = 0, MP_K_RAGGED = 1, MP_K_SHINV = 2, MP_K_PERSIST = 3 };
+enum { MP_K_UNIFORM = 0, MP_K_RAGGED = 1, MP_K_SHINV = 2, MP_K_PERSIST = 3, MP_K_MUL = 4 };
 
 void* mp_kernel_w4(int kind);
 void* mp_kernel_w8(int kind);

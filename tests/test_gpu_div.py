@@ -137,3 +137,19 @@ def test_full_products_mode_is_exact():
     Q, R, S, _ = run_uniform(U, V, flags=mp.MPDIV_FLAG_FULL_PRODUCTS)
     Qo, Ro, So = oracle_uniform(U, V)
     assert_same(Q, R, S, Qo, Ro, So)
+
+
+@pytest.mark.parametrize("n", [1, 7, 100, 1024, 3000, 8192])
+def test_multiplication_cost_unit(n):
+    # (u v) mod B^n, the product of Fig. 3 that the cost model counts in
+    import torch
+    import paper_2606_06386_gb300 as mp
+
+    U = I.uniform_batch(6, n, seed=90, stream=n)
+    V = I.uniform_batch(6, n, seed=91, stream=n)
+    out = torch.zeros((6, n), dtype=torch.int32, device="cuda:0")
+    mp.mpdiv_mul_batch(ctx(), dev(U), dev(V), out)
+    torch.cuda.synchronize()
+    O = host_u32(out)
+    for i in range(6):
+        assert oracle.to_int(O[i]) == (oracle.to_int(U[i]) * oracle.to_int(V[i])) % (B**n)
