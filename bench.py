@@ -7,14 +7,16 @@ uniform random operands, one plain launch (one thread block per division) per
 size. One step = the four launches (15,360 divisions). Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sweep|mixed|serve|stress]
+                    [--workload sweep|mixed|serve|stress|paper]
 
 --impl reference times the CPU oracle (Knuth's Algorithm D, C++) on this
 machine's host cores over a bounded sample of the same workload per step.
 Other workloads: mixed (one persistent launch of 8192 mixed-precision
 divisions vs one plain launch per size class), serve (Poisson arrivals at
 50/80/95% of the plain path's capacity through the serving loop), stress
-(2^18-bit adversarial cases). Under torchrun each rank runs the workload on
+(2^18-bit adversarial cases), paper (the paper's own Table 1 datasets,
+2^13..2^18 bits, with the division/multiplication time ratio per dataset).
+Under torchrun each rank runs the workload on
 its own GPU (independent replicas); the value is the total over ranks divided
 by the slowest rank's time.
 """
@@ -549,6 +551,83 @@ def run_stress(args, dev, dist, rank, ws):
     return out
 
 
+# Table 1 of the paper (A100, 64-bit digits): division time / multiplication
+# time per dataset, quoted as context next to the same ratio measured here.
+PAPER_DIV_OVER_MUL = {13: 15.46, 14: 14.74, 15: 9.73, 16: 6.94, 17: 6.66, 18: 6.77}
+
+
+def run_paper(args, dev, dist, rank, ws):
+    """The paper's own datasets (Section 4): 2^13..2^18-bit u of M - 2 digits,
+    v of random precision in [2, M/2] (64-bit digits), 2^32 / bits instances,
+    one plain launch each; beside it the cost unit (an M-digit product kept to
+    M digits) on the same instance count."""
+    import torch
+
+    import paper_2606_06386_gb300 as mp
+
+    mp.build()
+    ctx = mp.mpdiv_init(dev.index or 0)
+    stream = torch.cuda.current_stream(dev)
+    sets = []
+    for bits, n_items in I.PAPER_TABLE:
+        U, V, v_len = I.paper_workload(bits, n_items)
+        un, vn = U.shape[1], V.shape[1]
+        d = dict(bits=bits, b=n_items, un=un, vn=vn, u=_to_dev(U, dev), v=_to_dev(V, dev),
+                 q=torch.empty((n_items, un), dtype=torch.int32, device=dev),
+                 r=torch.empty((n_items, vn), dtype=torch.int32, device=dev),
+                 st=torch.empty((n_items,), dtype=torch.int32, device=dev),
+                 prod=torch.zeros((n_items,), dtype=torch.int64, device=dev))
+        del U, V
+        d["warps"] = mp.mpdiv_autotune(ctx, un, vn, min(n_items, 8192))
+        mp.mpdiv_batch(ctx, d["u"], d["v"], d["q"], d["r"], d["st"], None, d["prod"], stream)
+        torch.cuda.synchronize(dev)
+        bad = int((d["st"] != 0).sum().item())
+        if bad:
+            raise RuntimeError(f"{bad} items of the 2^{bits.bit_length() - 1}-bit dataset returned a nonzero status")
+        d["products"] = int(d["prod"].sum().item())
+        sets.append(d)
+    reps = max(3, args.steps // 4)
+    _barrier(dist, dev)
+    with ClockSampler(dev.index or 0) as clk:
+        for d in sets:
+            d["ms"] = _time(lambda: mp.mpdiv_batch(ctx, d["u"], d["v"], d["q"], d["r"], d["st"], None, None,
+                                                   stream), stream, reps)
+    res, total_items, total_ms = {}, 0, 0.0
+    for d in sets:
+        m32 = d["bits"] // 32
+        a = _to_dev(I.uniform_batch(d["b"], m32, seed=I.SEED_BASE + 7, stream=m32), dev)
+        bb = _to_dev(I.uniform_batch(d["b"], m32, seed=I.SEED_BASE + 7, stream=m32 + 1), dev)
+        out_m = torch.empty((d["b"], m32), dtype=torch.int32, device=dev)
+        mp.mpdiv_mul_batch(ctx, a, bb, out_m, stream)
+        mul_ms = _time(lambda: mp.mpdiv_mul_batch(ctx, a, bb, out_m, stream), stream, reps)
+        del a, bb, out_m
+        lg = d["bits"].bit_length() - 1
+        res[f"2^{lg}"] = {"instances": d["b"], "u_digits": d["un"], "v_digits_max": d["vn"],
+                          "div_ms": d["ms"], "div_per_s": d["b"] / (d["ms"] / 1e3), "mul_ms": mul_ms,
+                          "div_over_mul": d["ms"] / mul_ms, "paper_div_over_mul_A100": PAPER_DIV_OVER_MUL[lg],
+                          "digit_products_per_div": d["products"] / d["b"],
+                          "Tprod_per_s": d["products"] / (d["ms"] / 1e3) / 1e12,
+                          "warps_per_block": d["warps"], "mul_columns": mp.mpdiv_tuning(ctx, d["un"])[1]}
+        total_items += d["b"]
+        total_ms += d["ms"]
+    total_ms = _max_over_ranks(dist, total_ms, dev)
+    out = {
+        "metric": METRIC, "value": total_items * ws / (total_ms / 1e3), "unit": UNIT, "n_gpus": ws,
+        "steps": reps, "warmup": 1, "ms_per_step": total_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "the paper's Table 1 datasets: 2^13..2^18-bit dividends of M-2 64-bit digits, "
+                               "divisors of random precision in [2, M/2] 64-bit digits, 2^32/bits instances, "
+                               "one plain launch per dataset",
+                   "l2": "no flush: every dataset's operands exceed the 129 MB L2"},
+        "datasets": res,
+    }
+    clocks = clk.summary()
+    if clocks is not None:
+        out["clocks"] = clocks
+    mp.mpdiv_destroy(ctx)
+    return out
+
+
 def run_reference(args, rank, ws):
     """The reference arm: the CPU oracle on this machine's host cores."""
     out_sample = []
@@ -583,7 +662,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "mixed", "serve", "stress"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "mixed", "serve", "stress", "paper"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=200000, help="serve workload: number of requests")
     ap.add_argument("--max-batch", type=int, default=1024, help="serve workload: most requests per batch")
@@ -605,7 +684,8 @@ def main():
     dist, rank, ws, local = _dist()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    runner = {"sweep": run_sweep, "mixed": run_mixed, "serve": run_serve, "stress": run_stress}[args.workload]
+    runner = {"sweep": run_sweep, "mixed": run_mixed, "serve": run_serve, "stress": run_stress,
+              "paper": run_paper}[args.workload]
     out = runner(args, dev, dist, rank, ws)
     if rank == 0:
         print(json.dumps(out))

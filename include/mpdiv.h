@@ -129,7 +129,8 @@ int mpdiv_debug_shinv(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *v, int32_
                       int32_t *iters, int32_t *status, void *stream);
 
 /* Tuning: time the plain kernel for the given (u_limbs, v_limbs) shape at each
- * candidate block size (4, 8, 16, 32 warps) and strip width (3, 5, 7 columns
+ * candidate block size (1 and 2 warps for u_limbs <= 1024, then 4, 8, 16 and
+ * 32 warps) and strip width (3, 5, 7 columns
  * per lane), then at Karatsuba cutoffs (never, 2048, 1024, 512 digits), on
  * `n_items` synthetic divisions and keep the fastest in the context's tuning
  * table for that size class (used where cfg leaves the

@@ -37,6 +37,8 @@ enum KernKind {
 // classes share an SM. The persistent kernel always runs 16-warp blocks.
 void* kernel_for(KernKind kk, int warps) {
   if (kk == KK_PERSIST) return mp_kernel_w16(MP_K_PERSIST);
+  if (warps <= 1) return mp_kernel_w1(kk);
+  if (warps <= 2) return mp_kernel_w2(kk);
   if (warps <= 4) return mp_kernel_w4(kk);
   if (warps <= 8) return mp_kernel_w8(kk);
   if (warps <= 16) return mp_kernel_w16(kk);
@@ -100,7 +102,7 @@ int mpdiv_default_kcut(mpdiv_ctx* ctx, int max_digits) {
 }
 
 int mpdiv_size_class(int digits) {
-  int c = 1024;
+  int c = 128;
   while (c < digits) c *= 2;
   return c;
 }

@@ -21,7 +21,7 @@ struct mpdiv_ctx {
   mpdiv_config cfg{0, 0, 0, 0, 0};
   mutable std::mutex err_mu;
   std::string err;
-  // tuning table: size class (digits, power of two >= 1024) -> launch shape
+  // tuning table: size class (digits, power of two >= 128) -> launch shape
   std::mutex tune_mu;
   struct Shape {
     int warps, tcols, kcut;

@@ -1,0 +1,16 @@
+// Division kernels instantiated for one-warp blocks: one division per warp
+// for the small precisions, so that many divisions share an SM and a group
+// barrier spans one warp (a separate translation unit, so that the block
+// sizes build in parallel).
+#include "mp_kernels.cuh"
+#include "mpdiv_kernels.h"
+
+void* mp_kernel_w1(int kind) {
+  switch (kind) {
+    case MP_K_UNIFORM: return (void*)mp::k_div_uniform<1, 32>;
+    case MP_K_RAGGED: return (void*)mp::k_div_ragged<1, 32>;
+    case MP_K_SHINV: return (void*)mp::k_shinv<1, 32>;
+    case MP_K_MUL: return (void*)mp::k_mul_low<1, 32>;
+    default: return nullptr;
+  }
+}

@@ -1,0 +1,16 @@
+// Division kernels instantiated for two-warp blocks: one division per warp
+// pair for the small precisions, so that many divisions share an SM and a
+// group barrier spans two warps (a separate translation unit, so that the
+// block sizes build in parallel).
+#include "mp_kernels.cuh"
+#include "mpdiv_kernels.h"
+
+void* mp_kernel_w2(int kind) {
+  switch (kind) {
+    case MP_K_UNIFORM: return (void*)mp::k_div_uniform<2, 16>;
+    case MP_K_RAGGED: return (void*)mp::k_div_ragged<2, 16>;
+    case MP_K_SHINV: return (void*)mp::k_shinv<2, 16>;
+    case MP_K_MUL: return (void*)mp::k_mul_low<2, 16>;
+    default: return nullptr;
+  }
+}

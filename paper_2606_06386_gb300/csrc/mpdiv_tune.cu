@@ -1,7 +1,8 @@
 // Tuner for the division kernels (Section 5 of arXiv 2606.06386 names
 // autotuning of block size, sequentialisation and multiplication
 // specialisation as future work): for a size class it times the plain kernel
-// at each candidate warps per block (4, 8, 16, 32) and columns per lane of the
+// at each candidate warps per block (1 and 2 for dividends of at most 1024
+// digits, then 4, 8, 16, 32) and columns per lane of the
 // strip multiply (3, 5, 7), then at Karatsuba cutoffs for the full products
 // (never, 2048, 1024, 512 digits), on synthetic divisions, and records the
 // fastest in the context's table, which can be saved to and loaded from a text file
@@ -64,6 +65,8 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int best_w = 0, best_t = 5, best_k = 0;
   float best_ms = 1e30f;
+  const int w_first = u_limbs <= 1024 ? 0 : 2;  // index into 1, 2, 4, 8, 16, 32 warps
+  const int n_shape = (6 - w_first) * 3;
   if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&u, n * u_limbs * 4), "autotune alloc"))) goto done;
   if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&v, n * v_limbs * 4), "autotune alloc"))) goto done;
   if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&q, n * u_limbs * 4), "autotune alloc"))) goto done;
@@ -73,13 +76,15 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
   k_fill<<<256, 256>>>(v, n_items, v_limbs, v_limbs, 0x7654321ull);
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  // warps x columns with schoolbook products, then the Karatsuba cutoff
-  // (0 = never, 2048, 1024, 512 digits) at the best shape
-  for (int cand = 0; cand < 15; cand++) {
-    const int w = cand < 12 ? 4 << (cand / 3) : best_w;
-    const int tc = cand < 12 ? 3 + 2 * (cand % 3) : best_t;
-    const int kc = cand < 12 ? 0 : (2048 >> (cand - 12));
-    if (cand >= 12 && best_w == 0) break;
+  // warps x columns with schoolbook products (one- and two-warp blocks only
+  // for dividends of at most 1024 digits), then the Karatsuba cutoff (0 =
+  // never, 2048, 1024, 512 digits) at the best shape
+  for (int cand = 0; cand < n_shape + 3; cand++) {
+    const bool shape = cand < n_shape;
+    const int w = shape ? 1 << (w_first + cand / 3) : best_w;
+    const int tc = shape ? 3 + 2 * (cand % 3) : best_t;
+    const int kc = shape ? 0 : (2048 >> (cand - n_shape));
+    if (!shape && best_w == 0) break;
     UniformLaunch L{};
     L.u = u;
     L.v = v;

@@ -190,3 +190,28 @@ def stress(variant: str, n_items: int = 1024, n: int = 8192):
     if variant == "e_v_Bk_minus_1":
         return uniform_batch(n_items, n, seed, s), np.full((n_items, half), 0xFFFFFFFF, np.uint32)
     raise ValueError(variant)
+
+
+# The paper's own datasets (Section 4, Datasets and Methodology): precisions of
+# 2^13..2^18 bits with 2^32 / bits instances each; u has precision M - 2 and v
+# a random precision in [2, M/2], in the paper's 64-bit digits (M = bits / 64).
+PAPER_TABLE = [(1 << b, 1 << (32 - b)) for b in (13, 14, 15, 16, 17, 18)]
+
+
+def paper_workload(bits: int, n_items: int, seed: int = SEED_BASE + 6):
+    """Operands of one Table 1 dataset in uint32 digits: u has 2(M - 2) digits
+    (top digit nonzero); v has 2p digits, p uniform in [2, M/2] per item (top
+    digit nonzero), stored zero-padded to M digits (M = bits / 64, so M 32-bit
+    digits = M/2 64-bit digits). Returns (U, V, v_len)."""
+    m64 = bits // 64
+    un = 2 * (m64 - 2)
+    vmax = m64
+    U = uniform_batch(n_items, un, seed, 2 * bits)
+    p = 2 + np.floor(uniform01(seed, 2 * bits + 1, n_items) * (m64 // 2 - 1)).astype(np.int64)
+    v_len = (2 * p).astype(np.int32)
+    V = digits(seed, 2 * bits + 2, n_items * vmax).reshape(n_items, vmax)
+    col = np.arange(vmax)[None, :]
+    V = np.where(col < v_len[:, None], V, 0).astype(np.uint32)
+    rows = np.arange(n_items)
+    V[rows, v_len - 1] = _top_nonzero(V[rows, v_len - 1])
+    return U, V, v_len

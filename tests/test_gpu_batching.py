@@ -96,7 +96,7 @@ def test_inject_lambda_keeps_results_exact():
 
 
 @pytest.mark.parametrize("cols", [3, 5, 7])
-@pytest.mark.parametrize("warps", [4, 8, 16, 32])
+@pytest.mark.parametrize("warps", [1, 2, 4, 8, 16, 32])
 def test_every_launch_shape_is_exact(warps, cols):
     U, V = I.sweep(2048, 1024, 16)
     Q, R, S, _ = run_uniform(U, V, warps=warps, cols=cols)

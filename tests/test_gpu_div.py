@@ -153,3 +153,17 @@ def test_multiplication_cost_unit(n):
     O = host_u32(out)
     for i in range(6):
         assert oracle.to_int(O[i]) == (oracle.to_int(U[i]) * oracle.to_int(V[i])) % (B**n)
+
+
+@pytest.mark.parametrize("bits", [b for b, _ in I.PAPER_TABLE])
+def test_paper_table1_datasets(bits):
+    # the paper's datasets (u of M-2 64-bit digits, v of random precision in
+    # [2, M/2] 64-bit digits, zero-padded), 2^13..2^18 bits: every item exact,
+    # and the Refine count of Algorithm 1 at each item's own precisions
+    n_items = 64 if bits <= 1 << 16 else 32
+    U, V, v_len = I.paper_workload(bits, n_items)
+    Q, R, S, it = run_uniform(U, V)
+    Qo, Ro, So = oracle_uniform(U, V)
+    assert_same(Q, R, S, Qo, Ro, So)
+    h = U.shape[1]
+    assert all(it[i] == M.refine_iterations(h, int(v_len[i]) - 1) for i in range(n_items))
