@@ -50,16 +50,20 @@ extern "C" {
 /* per-item status */
 #define MPDIV_ST_OK 0
 #define MPDIV_ST_DIV_BY_ZERO 1          /* v == 0: q and r are written as zero */
-#define MPDIV_ST_CORRECTION_OVERFLOW 2  /* more than the two corrections Theorem 2 allows */
+#define MPDIV_ST_CORRECTION_OVERFLOW 2  /* more corrections than the bound (2 each way with full
+                                           products, 4 with clipped ones) */
 #define MPDIV_ST_Q_OVERFLOW 3           /* the quotient does not fit in q_limbs (low digits written) */
 #define MPDIV_ST_INTERNAL 4             /* an internal working-buffer bound was exceeded */
 
 /* flags of mpdiv_config.flags */
 #define MPDIV_FLAG_INJECT_LAMBDA 1 /* test only: use shinv + 1, forcing Theorem 2's delta = -1 path */
-#define MPDIV_FLAG_FULL_PRODUCTS 2 /* Algorithm 3 with the paper's full products u*shinv and v*q
-                                      (default: clipped products, Section 5: the quotient from the
-                                      columns at or above h-2 of u*shinv, the remainder from
-                                      v*q mod B^(prec(v)+1); same results, fewer products) */
+#define MPDIV_FLAG_FULL_PRODUCTS 2 /* Algorithms 1-3 with the paper's full products w*x in Step,
+                                      u*shinv and v*q (default: clipped products, Section 5: Step's
+                                      w*x from the columns at or above the dropped ones less two,
+                                      the quotient from the columns at or above h-2 of u*shinv,
+                                      the remainder from v*q mod B^(prec(v)+1); same q and r,
+                                      fewer products; the shifted inverse itself can then differ
+                                      from Algorithm 1's by one unit) */
 
 typedef struct mpdiv_ctx mpdiv_ctx; /* opaque; owned by the library */
 
@@ -69,9 +73,10 @@ typedef struct mpdiv_config {
   int flags;           /* MPDIV_FLAG_* */
   int mul_columns;     /* output columns per lane of the strip multiply: 3, 5 or 7; 0: per
                           size class from the tuning table */
-  int karatsuba_cutoff; /* one Karatsuba level for full products whose shorter operand has
-                           at least this many digits (> 0); -1: never; 0: per size class from
-                           the tuning table (never if untuned) */
+  int karatsuba_cutoff; /* one Karatsuba level for the Newton step's full products (only with
+                           MPDIV_FLAG_FULL_PRODUCTS) whose shorter operand has at least this
+                           many digits (> 0); -1: never; 0: per size class from the tuning
+                           table (never if untuned) */
 } mpdiv_config;
 
 /* Create a context on CUDA device `device` (cfg may be NULL for defaults).

@@ -12,6 +12,8 @@ notation, the three algorithms of the paper (arXiv 2606.06386):
 * ``powdiff`` -- Algorithm 2, PowDiff(v, w, h, l, B) with explicit sign.
 * ``div``     -- Algorithm 3, Div(u, v): q = shift_{-h}(u * shinv_h(v)) then
   the two one-step corrections of Theorem 2 (delta in {-1, 0, 1}).
+* ``div_clipped`` -- Algorithm 3 with the clipped products of Section 5
+  (quotient, remainder and, optionally, Newton step), as the GPU computes it.
 
 Nothing here is blocked, fused or reordered: each line is one step of the
 algorithm as printed, with the readings below where the text is ambiguous.
@@ -101,10 +103,43 @@ def powdiff(v: int, w: int, h: int, ell: int, B: int, tr: Trace) -> tuple[int, i
     return 1, B**L - P
 
 
-def step(h: int, v: int, w: int, m: int, ell: int, g: int, B: int, tr: Trace) -> int:
-    """Algorithm 1, Step: one Newton iteration on the shifted inverse."""
+def low_pairs(a: int, b: int, lo: int, B: int) -> int:
+    """Sum of the digit products a_i b_j B^(i+j) with i + j < lo."""
+    total = 0
+    for j in range(prec(b, B)):
+        if lo - j <= 0:
+            break
+        total += ((b // B**j) % B) * (a % B ** (lo - j)) * B**j
+    return total
+
+
+def step(h: int, v: int, w: int, m: int, ell: int, g: int, B: int, tr: Trace,
+         span: int | None = None, guard: int = 2) -> int:
+    """Algorithm 1, Step: one Newton iteration on the shifted inverse.
+
+    With ``span`` set, w * x is clipped the way Section 5 proposes for the
+    quotient: Step keeps only the digits of w * x at and above position
+    e = h - 2m, so the digit products below e - guard are skipped. The
+    skipped columns are rounded down to a multiple of ``span`` (the
+    column-strip width of a GPU multiply that computes whole strips), and the
+    columns from there up are summed exactly. The shifted product is then at
+    most one short (the skipped sum is below B^(e-1) times the shorter
+    operand's digit count), and the floor's sticky digit is read from the
+    summed columns only.
+    """
     sign, x = powdiff(v, w, h - m, ell - g, B, tr)
-    tmp = tr.mult("step", w, x, B)
+    if span is None:
+        tmp = tr.mult("step", w, x, B)
+    else:
+        e = h - 2 * m
+        plo = max(0, e - guard)
+        tmp = tr.mult("step", w, x, B, lo=plo)
+        nt = prec(w, B) + prec(x, B)
+        if plo > 0:
+            if nt <= plo:
+                tmp = 0  # every column lies below the clip: nothing is summed
+            else:
+                tmp -= low_pairs(w, x, (plo // span) * span, B)
     if sign:
         return shift(m, w, B) + shift(2 * m - h, tmp, B)
     res = shift(m, w, B) - (tmp // B ** (h - 2 * m))
@@ -124,15 +159,16 @@ def refine_iterations(h: int, k: int) -> int:
     return c + 2
 
 
-def refine(v: int, h: int, k: int, w: int, ell: int, B: int, tr: Trace) -> int:
-    """Algorithm 1, Refine: shorter iterates with divisor prefixes."""
+def refine(v: int, h: int, k: int, w: int, ell: int, B: int, tr: Trace, span: int | None = None) -> int:
+    """Algorithm 1, Refine: shorter iterates with divisor prefixes (``span``:
+    Step's clipped product, see ``step``)."""
     g = 2
     w = shift(g, w, B)
     n_it = refine_iterations(h, k)
     for i in range(n_it):
         m = min(h - k + 1 - ell, ell)
         s = max(0, k - 2 * ell + 1 - g)
-        w = step(k + ell + m - s + g, shift(-s, v, B), w, m, ell, g, B, tr)
+        w = step(k + ell + m - s + g, shift(-s, v, B), w, m, ell, g, B, tr, span)
         if i < 2:
             w = shift(-m, w, B)
         else:
@@ -144,8 +180,9 @@ def refine(v: int, h: int, k: int, w: int, ell: int, B: int, tr: Trace) -> int:
     return shift(q, w, B)
 
 
-def shinv(v: int, h: int, B: int, tr: Trace | None = None) -> int:
-    """Algorithm 1, Shinv(v, h, B) for B >= 16 and v > 0."""
+def shinv(v: int, h: int, B: int, tr: Trace | None = None, span: int | None = None) -> int:
+    """Algorithm 1, Shinv(v, h, B) for B >= 16 and v > 0 (``span``: Step's
+    clipped product, see ``step``; None: the paper's algorithm)."""
     if tr is None:
         tr = Trace()
     if v <= 0:
@@ -163,7 +200,7 @@ def shinv(v: int, h: int, B: int, tr: Trace | None = None) -> int:
         return B ** (h - k)
     V = (v // B ** (k - 1)) % B + ((v // B**k) % B) * B
     w = B**3 // V
-    return refine(v, h, k, w, 2, B, tr)
+    return refine(v, h, k, w, 2, B, tr, span)
 
 
 def div(u: int, v: int, B: int, tr: Trace | None = None) -> tuple[int, int, int]:
@@ -194,13 +231,16 @@ def newton_shift_step(w: int, v: int, h: int, B: int) -> int:
     return w + shift(-h, shift(h, w, B) - v * w * w, B)
 
 
-def div_clipped(u: int, v: int, B: int, tr: Trace | None = None, guard: int = 2) -> tuple[int, int]:
+def div_clipped(u: int, v: int, B: int, tr: Trace | None = None, guard: int = 2,
+                span: int | None = None) -> tuple[int, int]:
     """Algorithm 3 with clipped products (the refinement Section 5 proposes):
 
-    * q0 is formed from the digit products of u * shinv_h(v) at columns
-      h - guard and above only (the carries of the lower columns are dropped),
-      which leaves q0 at most one short of shift_{-h}(u * shinv_h(v));
-    * u - v q0 then lies in (-2v, 2v), so it is taken from v q0 modulo B^(k+2)
+    * w = shinv_h(v) by Algorithm 1, with Step's product clipped when ``span``
+      is set (see ``step``): w may then differ from Algorithm 1's by one unit;
+    * q0 is formed from the digit products of u * w at columns h - guard and
+      above only (the carries of the lower columns are dropped), which leaves
+      q0 at most one short of shift_{-h}(u * w);
+    * u - v q0 then lies in [-2v, 4v), so it is taken from v q0 modulo B^(k+2)
       (k + 1 = prec(v)) and read as a two's-complement number;
     * the corrections of Theorem 2 finish the division.
     """
@@ -209,15 +249,10 @@ def div_clipped(u: int, v: int, B: int, tr: Trace | None = None, guard: int = 2)
     if v <= 0:
         raise ZeroDivisionError("division by zero")
     h = prec(u, B)
-    w = shinv(v, h, B, tr)
+    w = shinv(v, h, B, tr, span)
     lo = max(0, h - guard)
     full = tr.mult("quotient_clipped", u, w, B, lo=lo)
-    low = 0  # the digit products below column lo, summed exactly
-    for j in range(prec(w, B)):
-        if lo - j <= 0:
-            break
-        low += ((w // B**j) % B) * (u % B ** (lo - j)) * B**j
-    q = (full - low) // B**h
+    q = (full - low_pairs(u, w, lo, B)) // B**h
     K1 = prec(v, B) + 1
     t = (u - tr.mult("remainder_low", v, q, B, keep=K1)) % B**K1
     if t >= B**K1 // 2:

@@ -509,6 +509,17 @@ __device__ inline void mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int
     mul_t<5>(b, C, npos, A, na, Bv, nb, OV, plo);
 }
 
+// Lowest column that mul(b, C, npos, X, nx, Y, ny, OV, plo) writes: the start
+// of the warp strip holding plo (whose columns are complete digit-product sums),
+// or plo itself when the product is empty or lies wholly below plo (then the
+// columns from plo up are written as zeros).
+__device__ __forceinline__ int mul_first_column(const Blk& b, int npos, int nx, int ny, int plo) {
+  if (plo <= 0) return 0;
+  if (nx <= 0 || ny <= 0 || npos <= plo) return min(plo, npos);
+  const int span = 32 * (b.tcols == 3 ? 3 : (b.tcols == 7 ? 7 : 5));
+  return (plo / span) * span;
+}
+
 // ---------------------------------------------------------------- Karatsuba
 // Save n digits at p into sv and zero them (and the reverse).
 __device__ inline void save_zero(const Blk& b, uint32_t* sv, uint32_t* p, int n) {

@@ -7,8 +7,14 @@
 // Shinv handles the special cases of Algorithm 1 (v < B: B^h quo v by a
 // parallel short division; 2v > B^h: 1; v = B^k: B^(h-k)), forms the two-digit
 // initial approximation w = B^3 quo (v_{k-1} + v_k B), and refines it with
-// Refine / Step / PowDiff (Algorithm 2, with the sign kept explicitly). The
-// corrections of Algorithm 3 run at most twice each way (Theorem 2 allows one);
+// Refine / Step / PowDiff (Algorithm 2, with the sign kept explicitly).
+//
+// By default the products are clipped (the refinement Section 5 proposes):
+// Step's w x and the quotient's u w skip the digit products below their kept
+// columns (less two guard digits), and the remainder is taken modulo
+// B^(kl+1). MPDIV_FLAG_FULL_PRODUCTS runs the algorithms with the paper's full
+// products instead. The corrections of Algorithm 3 run at most twice each way
+// with full products (Theorem 2 allows one) and four times with clipped ones;
 // more would set MPDIV_ST_CORRECTION_OVERFLOW.
 //
 // Shared-memory plan for an item with h dividend digits and kl divisor digits
@@ -28,10 +34,17 @@ namespace mp {
 enum : int { ST_OK = 0, ST_DIV_BY_ZERO = 1, ST_CORR = 2, ST_QOVF = 3, ST_INTERNAL = 4 };
 enum : int { FLAG_INJECT_LAMBDA = 1, FLAG_FULL_PRODUCTS = 2 };
 
-// Guard digits of the clipped quotient product: the digit products below
-// position h - QGUARD are skipped, which drops less than min(h, |w|) B^(h-1)
-// < B^h from u w and so leaves q0 at most one short.
+// Guard digits of the clipped products: skipping the digit products below
+// position c - QGUARD of a product whose digits below c are shifted away drops
+// less than min(digit counts) B^(c-1) < B^c, so the shifted result is at most
+// one short.
 constexpr int QGUARD = 2;
+
+// Corrections each way with clipped products: q0 = shift_{-h}(u w) can be one
+// short from the clipped quotient product, and w can differ from shinv_h(v) by
+// -1..+2 (Theorem 2's lambda plus one unit from the clipped Newton steps), so
+// q0 lies in [q - 3, q + 2]; four each way is a bound with room.
+constexpr int CLIP_CORR = 4;
 
 struct Layout {
   uint32_t *V, *W, *X, *R, *U, *P, *OV;
@@ -105,7 +118,8 @@ __device__ __forceinline__ int refine_iters(int h, int k) {
 // Algorithm 1 for v (in L.V, kl digits, top digit nonzero) and h >= kl.
 // Leaves shinv_h(v) in L.W and returns its digit count bound in *lw.
 // Returns a status.
-__device__ inline int shinv(const Blk& b, const Layout& L, int h, int kl, int* lw_out, int* iters_out) {
+__device__ inline int shinv(const Blk& b, const Layout& L, int h, int kl, int* lw_out, int* iters_out,
+                            bool clip_step) {
   const int k = kl - 1;
   uint32_t* V = L.V;
   uint32_t* W = L.W;
@@ -239,10 +253,22 @@ __device__ inline int shinv(const Blk& b, const Layout& L, int h, int kl, int* l
     } else {
       const int nt = pw + px;
       if (nt > L.capP) return ST_INTERNAL;
-      // Karatsuba scratch: the product buffer's free tail, and R (free until
-      // Step's sum below) for chunk products
-      const int sa = (nt + 3) & ~3;
-      mul_full(b, P, W, pw, X, px, L.OV, P + sa, L.capP - sa, R, L.capR);
+      int p0 = 0;  // lowest column of w x in P
+      if (clip_step) {
+        // clipped: only the columns from e - QGUARD up (the strip holding it),
+        // so shift_{-e} of the product may come out one short (and the floor's
+        // sticky digit is read from the computed columns only); the iterate may
+        // then differ from Algorithm 1's by one unit, which Refine's later steps
+        // and the quotient's corrections absorb
+        const int plo = max(0, e - QGUARD);
+        mul(b, P, nt, W, pw, X, px, L.OV, plo);
+        p0 = mul_first_column(b, nt, pw, px, plo);
+      } else {
+        // Karatsuba scratch: the product buffer's free tail, and R (free until
+        // Step's sum below) for chunk products
+        const int sa = (nt + 3) & ~3;
+        mul_full(b, P, W, pw, X, px, L.OV, P + sa, L.capP - sa, R, L.capR);
+      }
       lr = max(pw + m, nt - e) + 1;
       if (lr > L.capR) return ST_INTERNAL;
       auto wm = [&](int i) -> uint32_t { return (i >= m && i - m < pw) ? W[i - m] : 0u; };
@@ -250,7 +276,7 @@ __device__ inline int shinv(const Blk& b, const Layout& L, int h, int kl, int* l
       if (sign) {
         addsub<false>(b, R, lr, wm, pe, 0u);
       } else {
-        const uint32_t c = find_first(b, 0, min(e, nt), [&](int i) { return P[i] != 0u; }) >= 0 ? 1u : 0u;
+        const uint32_t c = find_first(b, p0, min(e, nt), [&](int i) { return P[i] != 0u; }) >= 0 ? 1u : 0u;
         const uint32_t bout = addsub<true>(b, R, lr, wm, pe, c);
         if (bout) return ST_INTERNAL;  // a negative iterate never happens (Theorem 2)
       }
@@ -314,7 +340,7 @@ __device__ inline int div_item(const Blk& b, uint32_t* sm, int smem_words, const
   b.sync();
   load_global(b, L.V, kl, [&](int i) { return gv[i]; });
   int lw = 0, iters = 0;
-  int st = shinv(b, L, h, kl, &lw, &iters);
+  int st = shinv(b, L, h, kl, &lw, &iters, (flags & FLAG_FULL_PRODUCTS) == 0);
   *iters_out = iters;
   if (st != ST_OK) return st;
   uint32_t* W = L.W;
@@ -362,7 +388,7 @@ __device__ inline int div_item(const Blk& b, uint32_t* sm, int smem_words, const
     addsub<true>(b, P, h, [&](int i) { return U[i]; }, [&](int i) { return i < nm ? P[i] : 0u; }, 0u);
     lr = prec(b, P, h);
   } else {
-    // ---- t = u - v q0 is in (-2v, 2v) (Theorem 2 and the clipped q0), so it is
+    // ---- t = u - v q0 is in [-2v, 4v) (q0 in [q - 3, q + 2]), so it is
     // determined by its value modulo B^(kl+1): only the low product is needed.
     const int K1 = kl + 1;
     if (K1 > L.capP) return ST_INTERNAL;
@@ -371,14 +397,14 @@ __device__ inline int div_item(const Blk& b, uint32_t* sm, int smem_words, const
     // ---- while t < 0 (top digit of the two's complement): q -= 1, t += v
     for (int t = 0;; t++) {
       if (P[K1 - 1] < 0x80000000u) break;
-      if (t == 2) return ST_CORR;
+      if (t == CLIP_CORR) return ST_CORR;
       if (!sub_pow(b, W, 0, lq)) return ST_INTERNAL;
       addsub<false>(b, P, K1, [&](int i) { return P[i]; }, [&](int i) { return i < kl ? V[i] : 0u; }, 0u);
     }
     // ---- if r >= v: q += 1, r -= v   (Theorem 2: delta = +1); r < B^(kl+1)
     for (int t = 0;; t++) {
       if (cmp(b, P, K1, V, kl) < 0) break;
-      if (t == 2) return ST_CORR;
+      if (t == CLIP_CORR) return ST_CORR;
       if (!add_pow(b, W, 0, lq + 1)) return ST_INTERNAL;
       lq = lq + 1;  // a bound: q may have grown by a digit
       addsub<true>(b, P, K1, [&](int i) { return P[i]; }, [&](int i) { return i < kl ? V[i] : 0u; }, 0u);

@@ -2,11 +2,11 @@
 // autotuning of block size, sequentialisation and multiplication
 // specialisation as future work): for a size class it times the plain kernel
 // at each candidate warps per block (1 and 2 for dividends of at most 1024
-// digits, then 4, 8, 16, 32) and columns per lane of the
-// strip multiply (3, 5, 7), then at Karatsuba cutoffs for the full products
-// (never, 2048, 1024, 512 digits), on synthetic divisions, and records the
-// fastest in the context's table, which can be saved to and loaded from a text file
-// (MPDIV_TUNE_FILE).
+// digits, then 4, 8, 16, 32) and columns per lane of the strip multiply (3, 5,
+// 7), then, in the full-product mode, at Karatsuba cutoffs for the Newton
+// step's full products (never, 2048, 1024, 512 digits), on synthetic
+// divisions, and records the fastest in the context's table, which can be
+// saved to and loaded from a text file (MPDIV_TUNE_FILE).
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -84,7 +84,9 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
     const int w = shape ? 1 << (w_first + cand / 3) : best_w;
     const int tc = shape ? 3 + 2 * (cand % 3) : best_t;
     const int kc = shape ? 0 : (2048 >> (cand - n_shape));
-    if (!shape && best_w == 0) break;
+    // Karatsuba splits only the full Newton-step products of the paper's
+    // full-product mode; clipped steps leave nothing for it to split
+    if (!shape && (best_w == 0 || !(ctx->cfg.flags & MPDIV_FLAG_FULL_PRODUCTS))) break;
     UniformLaunch L{};
     L.u = u;
     L.v = v;

@@ -112,10 +112,11 @@ def test_every_launch_shape_is_exact(warps, cols):
 
 @pytest.mark.parametrize(
     "n,kl,full,applies",
-    [(2048, 1024, False, False),  # the last step's scratch does not fit: strip products
-     (4096, 2048, False, True), (8192, 4096, False, True),  # 2:1 steps: square chunks
+    [(2048, 1024, True, False),  # the last step's scratch does not fit: strip products
+     (4096, 2048, True, True), (8192, 4096, True, True),  # 2:1 steps: square chunks
      (3000, 1000, True, True),  # near-square last step
-     (5000, 2600, True, True), (6000, 3100, False, True), (2500, 2400, True, False)])
+     (5000, 2600, True, True), (6000, 3100, True, True), (2500, 2400, True, False),
+     (8192, 4096, False, False)])  # clipped Newton steps have no full product to split
 def test_karatsuba_products_are_exact(n, kl, full, applies):
     # one Karatsuba level on the Newton step's full product, forced on from 512
     # digits: the same digits as the oracle, and fewer digit products than the
@@ -146,7 +147,7 @@ def test_karatsuba_keeps_the_shifted_inverse_of_the_model():
     it = torch.zeros(4, dtype=torch.int32, device="cuda:0")
     st = torch.full((4,), -1, dtype=torch.int32, device="cuda:0")
     h_t = torch.full((4,), 3000, dtype=torch.int32, device="cuda:0")
-    mp.mpdiv_debug_shinv(ctx(kcut=512), dev(V), h_t, out, it, st)
+    mp.mpdiv_debug_shinv(ctx(flags=mp.MPDIV_FLAG_FULL_PRODUCTS, kcut=512), dev(V), h_t, out, it, st)
     torch.cuda.synchronize()
     O = host_u32(out)
     for i, v in enumerate(vs):

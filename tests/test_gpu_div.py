@@ -84,26 +84,32 @@ def test_shinv_equals_model_and_theorem2():
     it = torch.zeros(len(vs), dtype=torch.int32, device="cuda:0")
     st = torch.full((len(vs),), -1, dtype=torch.int32, device="cuda:0")
     h_t = torch.tensor(hs, dtype=torch.int32, device="cuda:0")
-    mp.mpdiv_debug_shinv(ctx(), dev(V), h_t, out, it, st)
-    torch.cuda.synchronize()
-    O = host_u32(out)
-    S = st.cpu().numpy()
-    I_ = it.cpu().numpy()
-    for i, (v, h) in enumerate(zip(vs, hs)):
-        assert S[i] == 0
-        tr = M.Trace()
-        s_model = M.shinv(v, h, B, tr)
-        s_gpu = oracle.to_int(O[i])
-        assert s_gpu == s_model, (i, v, h)
-        assert s_gpu - B**h // v in (0, 1)
-        assert I_[i] == tr.iterations
+    # default (clipped Newton steps, 3 columns per lane: 96-column strips) and
+    # the paper's full products
+    for flags, span in ((0, 96), (mp.MPDIV_FLAG_FULL_PRODUCTS, None)):
+        out.zero_()
+        st.fill_(-1)
+        mp.mpdiv_debug_shinv(ctx(flags=flags, cols=3), dev(V), h_t, out, it, st)
+        torch.cuda.synchronize()
+        O = host_u32(out)
+        S = st.cpu().numpy()
+        I_ = it.cpu().numpy()
+        for i, (v, h) in enumerate(zip(vs, hs)):
+            assert S[i] == 0
+            tr = M.Trace()
+            s_model = M.shinv(v, h, B, tr, span)
+            s_gpu = oracle.to_int(O[i])
+            assert s_gpu == s_model, (i, v, h, flags)
+            assert s_gpu - B**h // v in ((0, 1) if span is None else (-1, 0, 1, 2))
+            assert I_[i] == tr.iterations
 
 
 @pytest.mark.parametrize("full", [False, True])
 @pytest.mark.parametrize("n,kl", [(64, 32), (300, 37), (1024, 512), (97, 96), (500, 2)])
 def test_product_counter_equals_model(n, kl, full):
     # the kernel's count of algorithmic digit products equals the exact model's,
-    # for the paper's full products and for the clipped quotient/remainder
+    # for the paper's full products and for the clipped Newton step, quotient
+    # and remainder
     import torch
     import paper_2606_06386_gb300 as mp
 
@@ -113,7 +119,7 @@ def test_product_counter_equals_model(n, kl, full):
     r = torch.zeros((4, kl), dtype=torch.int32, device="cuda:0")
     st = torch.zeros(4, dtype=torch.int32, device="cuda:0")
     pr = torch.zeros(4, dtype=torch.int64, device="cuda:0")
-    mp.mpdiv_batch(ctx(flags=mp.MPDIV_FLAG_FULL_PRODUCTS if full else 0), dev(U), dev(V), q, r, st, None, pr)
+    mp.mpdiv_batch(ctx(flags=mp.MPDIV_FLAG_FULL_PRODUCTS if full else 0, cols=3), dev(U), dev(V), q, r, st, None, pr)
     torch.cuda.synchronize()
     P = pr.cpu().numpy()
     for i in range(4):
@@ -122,7 +128,7 @@ def test_product_counter_equals_model(n, kl, full):
         if full:
             M.div(u, v, B, tr)
         else:
-            assert M.div_clipped(u, v, B, tr) == divmod(u, v)
+            assert M.div_clipped(u, v, B, tr, span=96) == divmod(u, v)
         assert P[i] == tr.digit_products()
 
 
