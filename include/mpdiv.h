@@ -18,7 +18,10 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
  *    stream). Calls are asynchronous; results are valid after the stream is
  *    synchronised.
- *  - Sizes: 1 <= u_limbs, v_limbs <= MPDIV_MAX_LIMBS (8192 digits = 2^18 bits).
+ *  - Sizes: 1 <= u_limbs, v_limbs <= MPDIV_MAX_LIMBS (16384 digits = 2^19 bits;
+ *    dividends of more than 8192 digits need the default clipped products: with
+ *    MPDIV_FLAG_FULL_PRODUCTS their working set exceeds a block's shared memory
+ *    and the call returns MPDIV_EUNSUPPORTED).
  *    q_limbs >= 1 and r_limbs >= v_limbs. A quotient needs at most
  *    u_limbs - prec(v) + 1 digits; with q_limbs = u_limbs every quotient fits.
  *  - Return codes: MPDIV_OK (0) or a negative MPDIV_E* code; the text of the
@@ -34,7 +37,7 @@
 extern "C" {
 #endif
 
-#define MPDIV_MAX_LIMBS 8192
+#define MPDIV_MAX_LIMBS 16384
 
 /* return codes */
 #define MPDIV_OK 0
@@ -102,7 +105,8 @@ const char *mpdiv_last_error(const mpdiv_ctx *ctx);
  * Strides are in digits. All pointers are device pointers.
  * Errors: MPDIV_EINVAL (null pointer, non-positive size, r_limbs < v_limbs,
  * stride shorter than the digit count), MPDIV_EUNSUPPORTED (more than
- * MPDIV_MAX_LIMBS digits), MPDIV_ECUDA (launch failure). */
+ * MPDIV_MAX_LIMBS digits, or a working set beyond the device's shared memory
+ * per block), MPDIV_ECUDA (launch failure). */
 int mpdiv_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, int32_t u_limbs, int64_t u_stride,
                 const uint32_t *v, int32_t v_limbs, int64_t v_stride, uint32_t *q, int32_t q_limbs,
                 int64_t q_stride, uint32_t *r, int32_t r_limbs, int64_t r_stride, int32_t *status, int32_t *iters,

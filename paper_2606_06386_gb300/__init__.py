@@ -34,7 +34,7 @@ MPDIV_ST_OK, MPDIV_ST_DIV_BY_ZERO, MPDIV_ST_CORRECTION_OVERFLOW = 0, 1, 2
 MPDIV_ST_Q_OVERFLOW, MPDIV_ST_INTERNAL = 3, 4
 MPDIV_FLAG_INJECT_LAMBDA = 1
 MPDIV_FLAG_FULL_PRODUCTS = 2
-MPDIV_MAX_LIMBS = 8192
+MPDIV_MAX_LIMBS = 16384
 MPDIV_NOALLOC_MAX_ITEMS = 65536
 
 _lock = threading.Lock()

@@ -60,6 +60,7 @@ struct ShinvArgs {
   int smem_words;
   int tcols;
   int kcut;
+  int flags;  // MPDIV_FLAG_FULL_PRODUCTS is honoured; the others are ignored
 };
 
 }  // namespace mp

@@ -21,8 +21,9 @@
 // the rows of the shorter operand, keeping a sliding window of T digits of the
 // longer operand in registers and three-word column accumulators updated with
 // mad.lo.cc / madc.hi.cc / addc. Warps take 32-lane strips from a shared
-// counter, heaviest first. A final carry pass folds each strip's two overflow
-// digits into its neighbour.
+// counter, heaviest first; within a strip the lanes' overflow digits are folded
+// into their neighbours with a ballot-mask carry resolution, and a final carry
+// pass folds each strip's two overflow digits into the next strip.
 #pragma once
 #include <cstdint>
 
@@ -354,8 +355,12 @@ __device__ __forceinline__ void mac3(uint32_t& c0, uint32_t& c1, uint32_t& c2, u
 }
 
 // One warp strip: lane owns columns [p0, p0+T) of A*B restricted to rows
-// j in [jlo, jhi) of B. Writes the lane's low T digits to C (columns < npos)
-// and its two overflow digits to OV[2s], OV[2s+1] with s = p0 / T.
+// j in [jlo, jhi) of B. Each lane's column sums come to T digits plus two
+// overflow digits, which belong to the next lane's first two columns; they are
+// added there, the carries between lanes are resolved with the ballot-mask
+// addition of addsub, and the strip's own two overflow digits (those of lane
+// 31 plus the carry out of the strip) go to OV[2 ws], OV[2 ws + 1]. Writes the
+// strip's digits to C (columns < npos).
 template <int T>
 __device__ __forceinline__ void mul_strip(const Blk& b, uint32_t* C, int npos, const uint32_t* A, int na,
                                           const uint32_t* Bv, int nb, uint32_t* OV, int ws) {
@@ -398,12 +403,43 @@ __device__ __forceinline__ void mul_strip(const Blk& b, uint32_t* C, int npos, c
     o[c] = (uint32_t)s;
     carry = s >> 32;
   }
+  // lane L's overflow digits into lane L+1's first two columns
+  uint32_t i0 = __shfl_up_sync(FULL, o[T], 1);
+  uint32_t i1 = __shfl_up_sync(FULL, o[T + 1], 1);
+  if (b.lane == 0) i0 = i1 = 0u;
+  uint64_t t = (uint64_t)o[0] + i0;
+  o[0] = (uint32_t)t;
+  t = (uint64_t)o[1] + i1 + (t >> 32);
+  o[1] = (uint32_t)t;
+  uint32_t cy = (uint32_t)(t >> 32);
+  bool allf = (o[0] == FULL) && (o[1] == FULL);
+#pragma unroll
+  for (int c = 2; c < T; c++) {
+    t = (uint64_t)o[c] + cy;
+    o[c] = (uint32_t)t;
+    cy = (uint32_t)(t >> 32);
+    allf = allf && (o[c] == FULL);
+  }
+  // carries between lanes: lane L generates when its sum overflowed and
+  // propagates when its T digits are all ones
+  const uint32_t gm = __ballot_sync(FULL, cy != 0u), pm = __ballot_sync(FULL, allf);
+  const uint64_t xm = (uint64_t)(gm | pm);
+  const uint64_t sum = xm + gm;
+  uint32_t ci = ((uint32_t)(sum ^ xm ^ gm) >> b.lane) & 1u;
+#pragma unroll
+  for (int c = 0; c < T; c++) {
+    t = (uint64_t)o[c] + ci;
+    o[c] = (uint32_t)t;
+    ci = (uint32_t)(t >> 32);
+  }
 #pragma unroll
   for (int c = 0; c < T; c++)
     if (p0 + c < npos) C[p0 + c] = o[c];
-  const int s = ws * 32 + b.lane;
-  OV[2 * s] = o[T];
-  OV[2 * s + 1] = o[T + 1];
+  if (b.lane == 31) {
+    t = (uint64_t)o[T] + (uint32_t)(sum >> 32);  // the strip's value is below B^(32T+2)
+    OV[2 * ws] = (uint32_t)t;
+    OV[2 * ws + 1] = o[T + 1] + (uint32_t)(t >> 32);
+  }
 }
 
 // Digit pairs (i, j) with i < na, j < nb and i + j < npos: the digit products
@@ -441,41 +477,63 @@ __device__ __forceinline__ int strip_order(int idx, int ws0, int nws, int na, in
 // The strip multiply for T columns per lane (see mul).
 template <int T>
 __device__ __forceinline__ void mul_t(const Blk& b, uint32_t* C, int npos, uint32_t* A, int na, uint32_t* Bv, int nb,
-                                      uint32_t* OV, int plo) {
+                                      uint32_t* OV, int plo, bool compact) {
   constexpr int WSPAN = 32 * T;
   const int ws0 = plo / WSPAN;
   const int nws = (npos + WSPAN - 1) / WSPAN;
   const int cnt = nws - ws0;
+  const int p0 = ws0 * WSPAN;
+  // compact: column c lives at C[c - p0] and strip ws's overflow at OV[2 (ws - ws0)]
+  uint32_t* Cw = compact ? C - p0 : C;
+  uint32_t* OVw = compact ? OV - 2 * ws0 : OV;
   while (true) {
     int idx = 0;
     if (b.lane == 0) idx = atomicAdd(&b.red[RED_CNT], 1);
     idx = __shfl_sync(FULL, idx, 0);
     if (idx >= cnt) break;
-    mul_strip<T>(b, C, npos, A, na, Bv, nb, OV, strip_order(idx, ws0, nws, na, nb, WSPAN));
+    mul_strip<T>(b, Cw, npos, A, na, Bv, nb, OVw, strip_order(idx, ws0, nws, na, nb, WSPAN));
   }
   b.sync();
   // fold each strip's overflow digits into the next strip's first two columns
-  const int p0 = ws0 * WSPAN, s0 = ws0 * 32;
   addsub<false>(
-      b, C + p0, npos - p0, [&](int i) { return C[p0 + i]; },
+      b, Cw + p0, npos - p0, [&](int i) { return Cw[p0 + i]; },
       [&](int i) -> uint32_t {
-        const int s = (p0 + i) / T;
-        const int off = p0 + i - s * T;
-        return (s > s0 && off < 2) ? OV[2 * (s - 1) + off] : 0u;
+        const int s = (p0 + i) / WSPAN;
+        const int off = p0 + i - s * WSPAN;
+        return (s > ws0 && off < 2) ? OVw[2 * (s - 1) + off] : 0u;
       },
       0u);
 }
 
+// Zero digits a multiply operand needs on each side for T columns per lane.
+__host__ __device__ __forceinline__ int pad_for(int tcols) { return 33 * (tcols == 3 ? 3 : (tcols == 7 ? 7 : 5)); }
+
+// Lowest column that mul(b, C, npos, X, nx, Y, ny, OV, plo) writes: the start
+// of the warp strip holding plo (whose columns are complete digit-product sums),
+// or plo itself when the product is empty or lies wholly below plo (then the
+// columns from plo up are written as zeros).
+__device__ __forceinline__ int mul_first_column(const Blk& b, int npos, int nx, int ny, int plo) {
+  if (plo <= 0) return 0;
+  if (nx <= 0 || ny <= 0 || npos <= plo) return min(plo, npos);
+  const int span = 32 * (b.tcols == 3 ? 3 : (b.tcols == 7 ? 7 : 5));
+  return (plo / span) * span;
+}
+
+// Overflow words a multiply of at most npos columns needs (two per strip).
+__host__ __device__ __forceinline__ int ov_words(int npos) { return 2 * ((npos + 32 * T_MIN - 1) / (32 * T_MIN) + 4); }
+
 // C[plo..npos) of X * Y: the digits of (X * Y) mod B^npos at positions plo
 // and above, from the digit products at positions at or above the warp strip
 // holding plo; carries from products below that strip are dropped (plo = 0:
-// the exact product modulo B^npos). X (nx digits) and Y (ny digits) are
-// multiply operands: PAD zero digits must be addressable below index 0 and
-// above the digit count (the high pads are zeroed here); an operand passed
-// with x_rows needs only T_MAX zero digits above its count. OV needs
-// 2 * (ceil(npos / T_MIN) + 32) words. C must not alias X or Y.
-__device__ inline void mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int nx, uint32_t* Y, int ny, uint32_t* OV,
-                           int plo = 0, bool x_rows = false) {
+// the exact product modulo B^npos). With `compact`, column c is stored at
+// C[c - p0], p0 = mul_first_column(...), which is returned; otherwise at C[c].
+// X (nx digits) and Y (ny digits) are multiply operands: pad_for(b.tcols) zero
+// digits must be addressable below index 0 and above the digit count (the
+// high pads are zeroed here); an operand passed with x_rows needs only T_MAX
+// zero digits above its count. OV needs ov_words(npos - p0) words. C must not
+// alias X or Y.
+__device__ inline int mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int nx, uint32_t* Y, int ny, uint32_t* OV,
+                          int plo = 0, bool x_rows = false, bool compact = false) {
   // the longer operand is the window operand unless X must be the row operand
   // (x_rows: X has no zero digits below index 0, only T_MAX above nx)
   uint32_t* A = X;
@@ -490,34 +548,26 @@ __device__ inline void mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int
   if (plo < 0) plo = 0;
   if (b.work != nullptr && b.tid == 0)
     *b.work += pair_count(na, nb, npos) - pair_count(na, nb, min(plo, npos));
+  const int first = mul_first_column(b, npos, na, nb, plo);
   if (nb <= 0 || npos <= plo) {
-    for (int i = plo + b.tid; i < npos; i += b.nt) C[i] = 0u;
+    for (int i = plo + b.tid; i < npos; i += b.nt) C[compact ? i - first : i] = 0u;
     b.sync();
-    return;
+    return first;
   }
-  for (int i = b.tid; i < PAD; i += b.nt) {
+  const int pad = pad_for(b.tcols);
+  for (int i = b.tid; i < pad; i += b.nt) {
     A[na + i] = 0u;
     if (i < T_MAX) Bv[nb + i] = 0u;
   }
   if (b.tid == 0) b.red[RED_CNT] = 0;
   b.sync();
   if (b.tcols == 3)
-    mul_t<3>(b, C, npos, A, na, Bv, nb, OV, plo);
+    mul_t<3>(b, C, npos, A, na, Bv, nb, OV, plo, compact);
   else if (b.tcols == 7)
-    mul_t<7>(b, C, npos, A, na, Bv, nb, OV, plo);
+    mul_t<7>(b, C, npos, A, na, Bv, nb, OV, plo, compact);
   else
-    mul_t<5>(b, C, npos, A, na, Bv, nb, OV, plo);
-}
-
-// Lowest column that mul(b, C, npos, X, nx, Y, ny, OV, plo) writes: the start
-// of the warp strip holding plo (whose columns are complete digit-product sums),
-// or plo itself when the product is empty or lies wholly below plo (then the
-// columns from plo up are written as zeros).
-__device__ __forceinline__ int mul_first_column(const Blk& b, int npos, int nx, int ny, int plo) {
-  if (plo <= 0) return 0;
-  if (nx <= 0 || ny <= 0 || npos <= plo) return min(plo, npos);
-  const int span = 32 * (b.tcols == 3 ? 3 : (b.tcols == 7 ? 7 : 5));
-  return (plo / span) * span;
+    mul_t<5>(b, C, npos, A, na, Bv, nb, OV, plo, compact);
+  return first;
 }
 
 // ---------------------------------------------------------------- Karatsuba

@@ -18,14 +18,18 @@
 // more would set MPDIV_ST_CORRECTION_OVERFLOW.
 //
 // Shared-memory plan for an item with h dividend digits and kl divisor digits
-// (all digit counts; PAD zero digits between buffers, shared by neighbours):
+// (all digit counts; `pad` zero digits between buffers, shared by neighbours:
+// pad_for(T) with clipped products, PAD with full ones, whose Karatsuba views
+// borrow PAD digits around their splits):
 //   V  [kl]            divisor, whole run
 //   W  [h-kl+9]        shifted inverse; later the quotient q
 //   X  [kl+32]         divisor prefix v' and PowDiff result x      } u overlays
 //   R  [h-kl+16]       Step result before its shift                } X..R later
-//   P  [max(h+41, 2h-kl+9)]  products
-//   OV [2 (ceil(|P|/3) + 64)] multiply overflow digits
-// The total does not depend on kl and grows as ~4.6 h digits.
+//   P  products: clipped, max(h-kl+240, kl+32) (the clipped products keep
+//      only their top columns, stored from the first computed strip up);
+//      full, max(h+41, 2h-kl+9)
+//   OV [two words per 96-column strip of P] multiply overflow digits
+// The total is largest at kl = 1: about 3 h digits clipped, 4 h full.
 #pragma once
 #include "mp_block.cuh"
 
@@ -51,39 +55,55 @@ struct Layout {
   int capV, capW, capX, capR, capP, capOV, total;
 };
 
-__host__ __device__ __forceinline__ int cap_p(int h, int kl) {
+// Product buffer. Clipped: the Newton step keeps at most |R| - 1 digits above
+// its dropped ones plus QGUARD guard digits and the rest of the first strip
+// (< 32 T_MAX), i.e. at most h-kl+16+224 digits; the quotient at most
+// |W| + QGUARD + 32 T_MAX - 1; PowDiff's products and the remainder fit in
+// |X| = kl+32 digits. Full: the Newton step's and the quotient's full products.
+__host__ __device__ __forceinline__ int cap_p(int h, int kl, bool clip) {
+  if (clip) {
+    const int a = h - kl + 240, c = kl + 32;
+    return a > c ? a : c;
+  }
   const int a = h + 41, c = 2 * h - kl + 9;
   return a > c ? a : c;
 }
 
-__host__ __device__ __forceinline__ int cap_ov(int capP) { return 2 * ((capP + T_MIN - 1) / T_MIN + 64); }
+__host__ __device__ __forceinline__ int cap_ov(int capP) { return ov_words(capP); }
 
-__host__ __device__ __forceinline__ int layout_words(int h, int kl) {
-  const int capP = cap_p(h, kl);
+// Zero digits between the buffers: the strip multiply's reach for the launch's
+// strip width with clipped products, PAD with full ones.
+__host__ __device__ __forceinline__ int layout_pad(bool clip, int tcols) { return clip ? pad_for(tcols) : PAD; }
+
+__host__ __device__ __forceinline__ int layout_words(int h, int kl, bool clip, int pad) {
+  const int capP = cap_p(h, kl, clip);
   const int capOV = cap_ov(capP);
-  return 5 * PAD + kl + (h - kl + 9) + (kl + 32) + (h - kl + 16) + capP + capOV;
+  return 5 * pad + kl + (h - kl + 9) + (kl + 32) + (h - kl + 16) + capP + capOV;
 }
 
-// Words of dynamic shared memory that cover every item with at most h digits.
-__host__ __device__ __forceinline__ int smem_words_for(int h) { return layout_words(h, 1); }
+// Words of dynamic shared memory that cover every item with at most h digits
+// (the plan is largest for a one-digit divisor).
+__host__ __device__ __forceinline__ int smem_words_for(int h, bool clip, int pad) {
+  return layout_words(h, 1, clip, pad);
+}
 
-__device__ __forceinline__ Layout make_layout(uint32_t* sm, int h, int kl) {
+__device__ __forceinline__ Layout make_layout(uint32_t* sm, int h, int kl, bool clip, int pad) {
   Layout L;
   L.capV = kl;
   L.capW = h - kl + 9;
   L.capX = kl + 32;
   L.capR = h - kl + 16;
-  L.capP = cap_p(h, kl);
+  L.capP = cap_p(h, kl, clip);
   L.capOV = cap_ov(L.capP);
-  int off = PAD;
+  int off = pad;
   L.V = sm + off;
-  off += L.capV + PAD;
+  off += L.capV + pad;
   L.W = sm + off;
-  off += L.capW + PAD;
+  off += L.capW + pad;
   L.X = sm + off;
-  off += L.capX + PAD;
+  off += L.capX + pad;
   L.R = sm + off;
-  off += L.capR + PAD;
+  off += L.capR + pad;
   L.P = sm + off;
   off += L.capP;
   L.OV = sm + off;
@@ -118,7 +138,7 @@ __device__ __forceinline__ int refine_iters(int h, int k) {
 // Algorithm 1 for v (in L.V, kl digits, top digit nonzero) and h >= kl.
 // Leaves shinv_h(v) in L.W and returns its digit count bound in *lw.
 // Returns a status.
-__device__ inline int shinv(const Blk& b, const Layout& L, int h, int kl, int* lw_out, int* iters_out,
+__device__ __forceinline__ int shinv(const Blk& b, const Layout& L, int h, int kl, int* lw_out, int* iters_out,
                             bool clip_step) {
   const int k = kl - 1;
   uint32_t* V = L.V;
@@ -252,8 +272,8 @@ __device__ inline int shinv(const Blk& b, const Layout& L, int h, int kl, int* l
       copy(b, R, lr, [&](int i) { return i >= m ? W[i - m] : 0u; });
     } else {
       const int nt = pw + px;
-      if (nt > L.capP) return ST_INTERNAL;
-      int p0 = 0;  // lowest column of w x in P
+      if (!clip_step && nt > L.capP) return ST_INTERNAL;
+      int p0 = 0;  // lowest column of w x; column c of the product is at P[c - p0]
       if (clip_step) {
         // clipped: only the columns from e - QGUARD up (the strip holding it),
         // so shift_{-e} of the product may come out one short (and the floor's
@@ -261,8 +281,9 @@ __device__ inline int shinv(const Blk& b, const Layout& L, int h, int kl, int* l
         // then differ from Algorithm 1's by one unit, which Refine's later steps
         // and the quotient's corrections absorb
         const int plo = max(0, e - QGUARD);
-        mul(b, P, nt, W, pw, X, px, L.OV, plo);
         p0 = mul_first_column(b, nt, pw, px, plo);
+        if (nt - p0 > L.capP || ov_words(nt - p0) > L.capOV) return ST_INTERNAL;
+        mul(b, P, nt, W, pw, X, px, L.OV, plo, false, true);
       } else {
         // Karatsuba scratch: the product buffer's free tail, and R (free until
         // Step's sum below) for chunk products
@@ -272,11 +293,12 @@ __device__ inline int shinv(const Blk& b, const Layout& L, int h, int kl, int* l
       lr = max(pw + m, nt - e) + 1;
       if (lr > L.capR) return ST_INTERNAL;
       auto wm = [&](int i) -> uint32_t { return (i >= m && i - m < pw) ? W[i - m] : 0u; };
-      auto pe = [&](int i) -> uint32_t { return (i + e < nt) ? P[i + e] : 0u; };
+      const uint32_t* Pc = P - p0;
+      auto pe = [&](int i) -> uint32_t { return (i + e < nt) ? Pc[i + e] : 0u; };
       if (sign) {
         addsub<false>(b, R, lr, wm, pe, 0u);
       } else {
-        const uint32_t c = find_first(b, p0, min(e, nt), [&](int i) { return P[i] != 0u; }) >= 0 ? 1u : 0u;
+        const uint32_t c = find_first(b, p0, min(e, nt), [&](int i) { return Pc[i] != 0u; }) >= 0 ? 1u : 0u;
         const uint32_t bout = addsub<true>(b, R, lr, wm, pe, c);
         if (bout) return ST_INTERNAL;  // a negative iterate never happens (Theorem 2)
       }
@@ -306,7 +328,7 @@ __device__ __forceinline__ void store_digits(const Blk& b, uint32_t* g, int cap,
 
 // The whole of Algorithm 3 for one item. Returns a status; q and r are always
 // written (zeros on division by zero).
-__device__ inline int div_item(const Blk& b, uint32_t* sm, int smem_words, const ItemIO& io, int flags, int* iters_out,
+__device__ __forceinline__ int div_item(const Blk& b, uint32_t* sm, int smem_words, const ItemIO& io, int flags, int* iters_out,
                         uint32_t* dbg_w, int dbg_cap, int h_override) {
   const uint32_t* gu = io.u;
   const uint32_t* gv = io.v;
@@ -334,13 +356,14 @@ __device__ inline int div_item(const Blk& b, uint32_t* sm, int smem_words, const
   } else if (h < kl) {
     return ST_INTERNAL;
   }
-  const Layout L = make_layout(sm, h, kl);
+  const bool clip = (flags & FLAG_FULL_PRODUCTS) == 0;
+  const Layout L = make_layout(sm, h, kl, clip, layout_pad(clip, b.tcols));
   if (L.total > smem_words) return ST_INTERNAL;
   for (int i = b.tid; i < L.total; i += b.nt) sm[i] = 0u;
   b.sync();
   load_global(b, L.V, kl, [&](int i) { return gv[i]; });
   int lw = 0, iters = 0;
-  int st = shinv(b, L, h, kl, &lw, &iters, (flags & FLAG_FULL_PRODUCTS) == 0);
+  int st = shinv(b, L, h, kl, &lw, &iters, clip);
   *iters_out = iters;
   if (st != ST_OK) return st;
   uint32_t* W = L.W;
@@ -356,17 +379,21 @@ __device__ inline int div_item(const Blk& b, uint32_t* sm, int smem_words, const
   // ---- q0 = shift_{-h}(u * w)
   uint32_t* U = L.U;
   uint32_t* P = L.P;
-  const bool full = (flags & FLAG_FULL_PRODUCTS) != 0;
+  const bool full = !clip;
   load_global(b, U, h, [&](int i) { return gu[i]; });
   const int np = h + lw;
-  if (np > L.capP) return ST_INTERNAL;
   // full: the exact product; clipped (Section 5's clipped products): only the
-  // columns at or above h - QGUARD, so q0 may come out one short
-  mul(b, P, np, U, h, W, lw, L.OV, full ? 0 : max(0, h - QGUARD));
+  // columns at or above h - QGUARD (stored from the first computed strip up),
+  // so q0 may come out one short
+  const int qlo = full ? 0 : max(0, h - QGUARD);
+  const int q0c = mul_first_column(b, np, h, lw, qlo);
+  if (np - q0c > L.capP || ov_words(np - q0c) > L.capOV) return ST_INTERNAL;
+  mul(b, P, np, U, h, W, lw, L.OV, qlo, false, true);
+  const uint32_t* Pq = P - q0c;
   int lq = np - h;
   if (lq + 1 > L.capW) return ST_INTERNAL;
   // q lives in W from here (one zero digit above it for a later +1)
-  lq = copy_prec(b, W, lq + 1, [&](int i) { return i < np - h ? P[h + i] : 0u; });
+  lq = copy_prec(b, W, lq + 1, [&](int i) { return i < np - h ? Pq[h + i] : 0u; });
   uint32_t* V = L.V;
   int lr;
   if (full) {

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_persistent(RaggedArgs a) 
     const int half_words = (words / 2) & ~3;
     const int want = ul <= a.split_digits[0] ? 4 : (ul <= a.split_digits[1] ? 8 : 16);
     if (nw >= 2 * kMinGroupWarps && 2 * node + 2 < kMaxGroups && want <= nw / 2 &&
-        smem_words_for(ul) <= half_words) {
+        smem_words_for(ul, (a.flags & FLAG_FULL_PRODUCTS) == 0, PAD) <= half_words) {
       const bool left = b.warp < nw / 2;
       node = 2 * node + (left ? 1 : 2);
       nw /= 2;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_shinv(ShinvArgs a) {
     io.rn = 0;
     int it = 0;
     const int h = max(a.h[item], 1);
-    const int st = div_item(b, sm, a.smem_words, io, 0, &it, a.out + item * a.os, a.on, h);
+    const int st = div_item(b, sm, a.smem_words, io, a.flags & FLAG_FULL_PRODUCTS, &it, a.out + item * a.os, a.on, h);
     if (b.tid == 0) {
       a.status[item] = st;
       if (a.iters) a.iters[item] = it;

@@ -66,7 +66,10 @@ int mpdiv_cuda_check(mpdiv_ctx* ctx, cudaError_t e, const char* what) {
   return mpdiv_set_error(ctx, MPDIV_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-int mpdiv_smem_bytes(int max_digits) { return (smem_words_for(max_digits) * 4 + 15) & ~15; }
+int mpdiv_smem_bytes(int max_digits, int flags, int tcols) {
+  const bool clip = (flags & MPDIV_FLAG_FULL_PRODUCTS) == 0;
+  return (smem_words_for(max_digits, clip, layout_pad(clip, tcols)) * 4 + 15) & ~15;
+}
 
 int mpdiv_default_warps(mpdiv_ctx* ctx, int max_digits) {
   if (ctx->cfg.warps_per_block > 0) return ctx->cfg.warps_per_block;
@@ -161,7 +164,8 @@ extern "C" const char* mpdiv_last_error(const mpdiv_ctx* ctx) {
 // ------------------------------------------------------------------ plain batch
 int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t stream) {
   const int max_digits = L.un;
-  const int smem = mpdiv_smem_bytes(max_digits);
+  const int tcols = L.tcols > 0 ? L.tcols : mpdiv_default_tcols(ctx, max_digits);
+  const int smem = mpdiv_smem_bytes(max_digits, ctx->cfg.flags, tcols);
   if (smem > ctx->max_smem)
     return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory, device allows %d", smem,
                            ctx->max_smem);
@@ -188,7 +192,7 @@ int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t st
   a.rn = L.rn;
   a.smem_words = smem / 4;
   a.flags = ctx->cfg.flags;
-  a.tcols = L.tcols > 0 ? L.tcols : mpdiv_default_tcols(ctx, max_digits);
+  a.tcols = tcols;
   a.kcut = L.kcut >= 0 ? L.kcut : mpdiv_default_kcut(ctx, max_digits);
   const int64_t grid = std::min<int64_t>(L.n, 0x7fffffff);
   void* args[] = {&a};
@@ -249,7 +253,7 @@ static double item_cost(int n, int kl) {
 int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stream) {
   int max_u = 1;
   for (int64_t i = 0; i < L.n; i++) max_u = std::max(max_u, (int)L.u_len_host[i]);
-  const int smem = mpdiv_smem_bytes(max_u);
+  const int smem = mpdiv_smem_bytes(max_u, ctx->cfg.flags, T_MAX);  // any strip width per item
   if (smem > ctx->max_smem)
     return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory", smem);
   const int warps = L.split ? 16 : (L.warps > 0 ? L.warps : mpdiv_default_warps(ctx, max_u));
@@ -426,8 +430,12 @@ extern "C" int mpdiv_debug_shinv(mpdiv_ctx* ctx, int64_t n_items, const uint32_t
   if (v_limbs > MPDIV_MAX_LIMBS || out_limbs > MPDIV_MAX_LIMBS + 1)
     return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "too many digits");
   cudaSetDevice(ctx->device);
-  const int max_h = MPDIV_MAX_LIMBS;  // h_digits live on the device: size for the largest
-  const int smem = mpdiv_smem_bytes(max_h);
+  // h_digits live on the device: size for the largest h that fits (the kernel
+  // reports MPDIV_ST_INTERNAL for an item whose working set does not)
+  const int tcols = ctx->cfg.mul_columns > 0 ? ctx->cfg.mul_columns : 5;
+  int max_h = MPDIV_MAX_LIMBS;
+  while (max_h > 256 && mpdiv_smem_bytes(max_h, ctx->cfg.flags, tcols) > ctx->max_smem) max_h -= 256;
+  const int smem = mpdiv_smem_bytes(max_h, ctx->cfg.flags, tcols);
   const int warps = ctx->cfg.warps_per_block > 0 ? ctx->cfg.warps_per_block : 16;
   void* k = kernel_for(KK_SHINV, warps);
   int rc = prepare_kernel(ctx, k, smem);
@@ -444,8 +452,9 @@ extern "C" int mpdiv_debug_shinv(mpdiv_ctx* ctx, int64_t n_items, const uint32_t
   a.vn = v_limbs;
   a.on = out_limbs;
   a.smem_words = smem / 4;
-  a.tcols = ctx->cfg.mul_columns > 0 ? ctx->cfg.mul_columns : 5;
+  a.tcols = tcols;
   a.kcut = ctx->cfg.karatsuba_cutoff > 0 ? ctx->cfg.karatsuba_cutoff : 0;
+  a.flags = ctx->cfg.flags & MPDIV_FLAG_FULL_PRODUCTS;
   void* args[] = {&a};
   const int64_t grid = std::min<int64_t>(n_items, 0x7fffffff);
   return mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * warps), args, smem,
@@ -474,7 +483,7 @@ extern "C" int mpdiv_mul_batch(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* 
   cudaSetDevice(ctx->device);
   const int n = n_limbs;
   const int tc = mpdiv_default_tcols(ctx, n);
-  const int words = 4 * PAD + 3 * n + 8 + 2 * ((n + T_MIN - 1) / T_MIN + 64);
+  const int words = 4 * PAD + 3 * n + 8 + ov_words(n);
   const int smem = (words * 4 + 15) & ~15;
   if (smem > ctx->max_smem) return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory", smem);
   const int warps = mpdiv_default_warps(ctx, n);

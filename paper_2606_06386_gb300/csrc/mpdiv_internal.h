@@ -86,7 +86,7 @@ struct RaggedLaunch {
 
 int mpdiv_set_error(mpdiv_ctx* ctx, int code, const char* fmt, ...);
 int mpdiv_cuda_check(mpdiv_ctx* ctx, cudaError_t e, const char* what);
-int mpdiv_smem_bytes(int max_digits);
+int mpdiv_smem_bytes(int max_digits, int flags, int tcols);
 int mpdiv_size_class(int digits);
 int mpdiv_default_warps(mpdiv_ctx* ctx, int max_digits);
 int mpdiv_default_tcols(mpdiv_ctx* ctx, int max_digits);

@@ -118,7 +118,7 @@ extern "C" int mpdiv_batch_ragged_noalloc(int64_t n_items, const uint32_t* u, co
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const int smem = (mp::smem_words_for(max_u) * 4 + 15) & ~15;
+  const int smem = (mp::smem_words_for(max_u, true, mp::PAD) * 4 + 15) & ~15;
   if (smem > max_smem) return MPDIV_EUNSUPPORTED;
   void* k = (void*)mp::k_div_ragged<kWarps, kMinBlocks>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return MPDIV_ECUDA;

@@ -196,6 +196,8 @@ def stress(variant: str, n_items: int = 1024, n: int = 8192):
 # 2^13..2^18 bits with 2^32 / bits instances each; u has precision M - 2 and v
 # a random precision in [2, M/2], in the paper's 64-bit digits (M = bits / 64).
 PAPER_TABLE = [(1 << b, 1 << (32 - b)) for b in (13, 14, 15, 16, 17, 18)]
+# One size beyond the paper's table, built the same way: 2^19 bits, 2^13 instances.
+BEYOND_TABLE = [(1 << 19, 1 << 13)]
 
 
 def paper_workload(bits: int, n_items: int, seed: int = SEED_BASE + 6):

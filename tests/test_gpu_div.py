@@ -145,7 +145,7 @@ def test_full_products_mode_is_exact():
     assert_same(Q, R, S, Qo, Ro, So)
 
 
-@pytest.mark.parametrize("n", [1, 7, 100, 1024, 3000, 8192])
+@pytest.mark.parametrize("n", [1, 7, 100, 1024, 3000, 8192, 16384])
 def test_multiplication_cost_unit(n):
     # (u v) mod B^n, the product of Fig. 3 that the cost model counts in
     import torch
@@ -173,3 +173,31 @@ def test_paper_table1_datasets(bits):
     assert_same(Q, R, S, Qo, Ro, So)
     h = U.shape[1]
     assert all(it[i] == M.refine_iterations(h, int(v_len[i]) - 1) for i in range(n_items))
+
+
+@pytest.mark.parametrize("kind", ["half", "paper", "short"])
+def test_2e19_bits_beyond_the_paper(kind):
+    # 2^19-bit dividends (16384 digits), which the paper's A100 could not hold
+    # in shared memory: half-length divisors, the paper's random precisions,
+    # and a 64-digit divisor; every item exact
+    import paper_2606_06386_gb300 as mp
+
+    if kind == "half":
+        U, V = I.sweep(16384, 8192, 6)
+    elif kind == "paper":
+        U, V, _ = I.paper_workload(1 << 19, 6)
+    else:
+        U = I.uniform_batch(6, 16384, seed=19, stream=1)
+        V = I.uniform_batch(6, 64, seed=19, stream=2)
+    Q, R, S, it = run_uniform(U, V)
+    Qo, Ro, So = oracle_uniform(U, V)
+    assert_same(Q, R, S, Qo, Ro, So)
+    # the paper's full products do not fit a block's shared memory at this size
+    import torch
+
+    q = torch.zeros((1, U.shape[1]), dtype=torch.int32, device="cuda:0")
+    r = torch.zeros((1, V.shape[1]), dtype=torch.int32, device="cuda:0")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda:0")
+    with pytest.raises(mp.MpdivError) as e:
+        mp.mpdiv_batch(ctx(flags=mp.MPDIV_FLAG_FULL_PRODUCTS), dev(U[:1]), dev(V[:1]), q, r, st)
+    assert e.value.code == mp.MPDIV_EUNSUPPORTED
