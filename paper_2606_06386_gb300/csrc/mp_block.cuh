@@ -22,8 +22,8 @@
 // longer operand in registers and three-word column accumulators updated with
 // mad.lo.cc / madc.hi.cc / addc. Warps take 32-lane strips from a shared
 // counter, heaviest first; within a strip the lanes' overflow digits are folded
-// into their neighbours with a ballot-mask carry resolution, and a final carry
-// pass folds each strip's two overflow digits into the next strip.
+// into their neighbours with a ballot-mask carry resolution, and each strip's
+// two overflow digits are then added to the next strip's first two columns.
 #pragma once
 #include <cstdint>
 
@@ -39,8 +39,9 @@ constexpr int PAD = 32 * T_MAX + T_MAX;  // zero digits kept on each side of a m
 constexpr int RED_WORDS = 100;           // block scratch: 3 x 32 per-warp slots + counters
 
 // block scratch layout
-constexpr int RED_CNT = 96;   // multiply work counter
-constexpr int RED_AUX = 97;   // misc broadcast
+constexpr int RED_CNT = 96;     // multiply work counter
+constexpr int RED_AUX = 97;     // misc broadcast
+constexpr int RED_RIPPLE = 98;  // multiply: a strip fold carried past its two columns
 
 // A group of whole warps that cooperates on one division: the whole thread
 // block, or a slice of it synchronised by its own named barrier.
@@ -442,6 +443,26 @@ __device__ __forceinline__ void mul_strip(const Blk& b, uint32_t* C, int npos, c
   }
 }
 
+// One warp adds 1 at digit pos of C[0..npos) and propagates the carry (a carry
+// out of digit npos-1 is dropped).
+__device__ __forceinline__ void ripple_add_one(const Blk& b, uint32_t* C, int pos, int npos) {
+  for (int base = pos; base < npos; base += 32) {
+    const int i = base + b.lane;
+    const bool valid = i < npos;
+    const uint32_t d = valid ? C[i] : 0u;
+    const uint32_t stop = __ballot_sync(FULL, valid && d != FULL);
+    if (stop == 0u) {
+      if (valid) C[i] = 0u;
+      continue;
+    }
+    const int f = __ffs(stop) - 1;
+    if (b.lane < f) C[i] = 0u;
+    if (b.lane == f) C[i] = d + 1u;
+    break;
+  }
+  __syncwarp();
+}
+
 // Digit pairs (i, j) with i < na, j < nb and i + j < npos: the digit products
 // of a product kept modulo B^npos (all na nb of them for a full product).
 __host__ __device__ __forceinline__ unsigned long long pair_count(int na, int nb, int npos) {
@@ -494,15 +515,30 @@ __device__ __forceinline__ void mul_t(const Blk& b, uint32_t* C, int npos, uint3
     mul_strip<T>(b, Cw, npos, A, na, Bv, nb, OVw, strip_order(idx, ws0, nws, na, nb, WSPAN));
   }
   b.sync();
-  // fold each strip's overflow digits into the next strip's first two columns
-  addsub<false>(
-      b, Cw + p0, npos - p0, [&](int i) { return Cw[p0 + i]; },
-      [&](int i) -> uint32_t {
-        const int s = (p0 + i) / WSPAN;
-        const int off = p0 + i - s * WSPAN;
-        return (s > ws0 && off < 2) ? OVw[2 * (s - 1) + off] : 0u;
-      },
-      0u);
+  // fold each strip's two overflow digits into the next strip's first two
+  // columns, one thread per strip boundary; a carry out of those two columns
+  // (rare: it needs the high overflow digit plus the column to reach B) is
+  // recorded in the consumed overflow word and added afterwards, boundary by
+  // boundary, with a full carry ripple
+  for (int s = ws0 + 1 + b.tid; s < nws; s += b.nt) {
+    const int c = s * WSPAN;  // < npos
+    uint64_t t = (uint64_t)Cw[c] + OVw[2 * (s - 1)];
+    Cw[c] = (uint32_t)t;
+    uint32_t k = 0u;
+    if (c + 1 < npos) {
+      t = (uint64_t)Cw[c + 1] + OVw[2 * (s - 1) + 1] + (t >> 32);
+      Cw[c + 1] = (uint32_t)t;
+      k = (c + 2 < npos) ? (uint32_t)(t >> 32) : 0u;
+    }
+    OVw[2 * (s - 1)] = k;
+    if (k) b.red[RED_RIPPLE] = 1;
+  }
+  b.sync();
+  if (b.red[RED_RIPPLE] != 0 && b.warp == 0) {
+    for (int s = ws0 + 1; s < nws; s++)
+      if (OVw[2 * (s - 1)] != 0u) ripple_add_one(b, Cw, s * WSPAN + 2, npos);
+  }
+  b.sync();  // also orders every read of RED_RIPPLE before the next multiply resets it
 }
 
 // Zero digits a multiply operand needs on each side for T columns per lane.
@@ -559,7 +595,10 @@ __device__ inline int mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int 
     A[na + i] = 0u;
     if (i < T_MAX) Bv[nb + i] = 0u;
   }
-  if (b.tid == 0) b.red[RED_CNT] = 0;
+  if (b.tid == 0) {
+    b.red[RED_CNT] = 0;
+    b.red[RED_RIPPLE] = 0;
+  }
   b.sync();
   if (b.tcols == 3)
     mul_t<3>(b, C, npos, A, na, Bv, nb, OV, plo, compact);

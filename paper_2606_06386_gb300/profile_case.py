@@ -1,6 +1,7 @@
 """Run a few plain division launches of one size, for profilers.
 
-    python -m paper_2606_06386_gb300.profile_case --digits 8192 --vdigits 4096 --items 152 --launches 2
+    python -m paper_2606_06386_gb300.profile_case --digits 8192 --vdigits 4096 --items 152 --launches 2 \
+        [--warps W] [--cols T]
 
 The operands are the seeded uniform sweep inputs; the launches go through the
 C ABI (mpdiv_batch) on the current stream. Used to capture the division kernel
@@ -21,6 +22,7 @@ def main():
     ap.add_argument("--items", type=int, default=152)
     ap.add_argument("--launches", type=int, default=2)
     ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--cols", type=int, default=0, help="strip width (columns per lane): 3, 5 or 7")
     a = ap.parse_args()
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import torch
@@ -36,7 +38,7 @@ def main():
     q = torch.zeros((a.items, a.digits - kl + 1), dtype=torch.int32, device="cuda")
     r = torch.zeros((a.items, kl), dtype=torch.int32, device="cuda")
     st = torch.zeros(a.items, dtype=torch.int32, device="cuda")
-    ctx = mp.mpdiv_init(0, warps_per_block=a.warps)
+    ctx = mp.mpdiv_init(0, warps_per_block=a.warps, mul_columns=a.cols)
     for _ in range(a.launches):
         mp.mpdiv_batch(ctx, u, v, q, r, st)
     torch.cuda.synchronize()
