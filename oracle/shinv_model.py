@@ -114,32 +114,28 @@ def low_pairs(a: int, b: int, lo: int, B: int) -> int:
 
 
 def step(h: int, v: int, w: int, m: int, ell: int, g: int, B: int, tr: Trace,
-         span: int | None = None, guard: int = 2) -> int:
+         clip: bool = False, guard: int = 2) -> int:
     """Algorithm 1, Step: one Newton iteration on the shifted inverse.
 
-    With ``span`` set, w * x is clipped the way Section 5 proposes for the
+    With ``clip``, w * x is clipped the way Section 5 proposes for the
     quotient: Step keeps only the digits of w * x at and above position
-    e = h - 2m, so the digit products below e - guard are skipped. The
-    skipped columns are rounded down to a multiple of ``span`` (the
-    column-strip width of a GPU multiply that computes whole strips), and the
-    columns from there up are summed exactly. The shifted product is then at
-    most one short (the skipped sum is below B^(e-1) times the shorter
+    e = h - 2m, so the digit products below e - guard are skipped and the
+    columns from e - guard up are summed exactly. The shifted product is then
+    at most one short (the skipped sum is below B^(e-1) times the shorter
     operand's digit count), and the floor's sticky digit is read from the
     summed columns only.
     """
     sign, x = powdiff(v, w, h - m, ell - g, B, tr)
-    if span is None:
+    if not clip:
         tmp = tr.mult("step", w, x, B)
     else:
-        e = h - 2 * m
-        plo = max(0, e - guard)
+        plo = max(0, h - 2 * m - guard)
         tmp = tr.mult("step", w, x, B, lo=plo)
-        nt = prec(w, B) + prec(x, B)
         if plo > 0:
-            if nt <= plo:
+            if prec(w, B) + prec(x, B) <= plo:
                 tmp = 0  # every column lies below the clip: nothing is summed
             else:
-                tmp -= low_pairs(w, x, (plo // span) * span, B)
+                tmp -= low_pairs(w, x, plo, B)
     if sign:
         return shift(m, w, B) + shift(2 * m - h, tmp, B)
     res = shift(m, w, B) - (tmp // B ** (h - 2 * m))
@@ -159,8 +155,8 @@ def refine_iterations(h: int, k: int) -> int:
     return c + 2
 
 
-def refine(v: int, h: int, k: int, w: int, ell: int, B: int, tr: Trace, span: int | None = None) -> int:
-    """Algorithm 1, Refine: shorter iterates with divisor prefixes (``span``:
+def refine(v: int, h: int, k: int, w: int, ell: int, B: int, tr: Trace, clip: bool = False) -> int:
+    """Algorithm 1, Refine: shorter iterates with divisor prefixes (``clip``:
     Step's clipped product, see ``step``)."""
     g = 2
     w = shift(g, w, B)
@@ -168,7 +164,7 @@ def refine(v: int, h: int, k: int, w: int, ell: int, B: int, tr: Trace, span: in
     for i in range(n_it):
         m = min(h - k + 1 - ell, ell)
         s = max(0, k - 2 * ell + 1 - g)
-        w = step(k + ell + m - s + g, shift(-s, v, B), w, m, ell, g, B, tr, span)
+        w = step(k + ell + m - s + g, shift(-s, v, B), w, m, ell, g, B, tr, clip)
         if i < 2:
             w = shift(-m, w, B)
         else:
@@ -180,9 +176,9 @@ def refine(v: int, h: int, k: int, w: int, ell: int, B: int, tr: Trace, span: in
     return shift(q, w, B)
 
 
-def shinv(v: int, h: int, B: int, tr: Trace | None = None, span: int | None = None) -> int:
-    """Algorithm 1, Shinv(v, h, B) for B >= 16 and v > 0 (``span``: Step's
-    clipped product, see ``step``; None: the paper's algorithm)."""
+def shinv(v: int, h: int, B: int, tr: Trace | None = None, clip: bool = False) -> int:
+    """Algorithm 1, Shinv(v, h, B) for B >= 16 and v > 0 (``clip``: Step's
+    clipped product, see ``step``; False: the paper's algorithm)."""
     if tr is None:
         tr = Trace()
     if v <= 0:
@@ -200,7 +196,7 @@ def shinv(v: int, h: int, B: int, tr: Trace | None = None, span: int | None = No
         return B ** (h - k)
     V = (v // B ** (k - 1)) % B + ((v // B**k) % B) * B
     w = B**3 // V
-    return refine(v, h, k, w, 2, B, tr, span)
+    return refine(v, h, k, w, 2, B, tr, clip)
 
 
 def div(u: int, v: int, B: int, tr: Trace | None = None) -> tuple[int, int, int]:
@@ -232,11 +228,12 @@ def newton_shift_step(w: int, v: int, h: int, B: int) -> int:
 
 
 def div_clipped(u: int, v: int, B: int, tr: Trace | None = None, guard: int = 2,
-                span: int | None = None) -> tuple[int, int]:
+                clip_step: bool = False) -> tuple[int, int]:
     """Algorithm 3 with clipped products (the refinement Section 5 proposes):
 
-    * w = shinv_h(v) by Algorithm 1, with Step's product clipped when ``span``
-      is set (see ``step``): w may then differ from Algorithm 1's by one unit;
+    * w = shinv_h(v) by Algorithm 1, with Step's product clipped when
+      ``clip_step`` is set (see ``step``): w may then differ from Algorithm 1's
+      by one unit;
     * q0 is formed from the digit products of u * w at columns h - guard and
       above only (the carries of the lower columns are dropped), which leaves
       q0 at most one short of shift_{-h}(u * w);
@@ -249,7 +246,7 @@ def div_clipped(u: int, v: int, B: int, tr: Trace | None = None, guard: int = 2,
     if v <= 0:
         raise ZeroDivisionError("division by zero")
     h = prec(u, B)
-    w = shinv(v, h, B, tr, span)
+    w = shinv(v, h, B, tr, clip_step)
     lo = max(0, h - guard)
     full = tr.mult("quotient_clipped", u, w, B, lo=lo)
     q = (full - low_pairs(u, w, lo, B)) // B**h

@@ -355,8 +355,8 @@ __device__ __forceinline__ void mac3(uint32_t& c0, uint32_t& c1, uint32_t& c2, u
       : "r"(a), "r"(bb));
 }
 
-// One warp strip: lane owns columns [p0, p0+T) of A*B restricted to rows
-// j in [jlo, jhi) of B. Each lane's column sums come to T digits plus two
+// One warp strip, columns [P0, P0 + 32T): lane owns columns [p0, p0+T) of A*B
+// restricted to rows j in [jlo, jhi) of B. Each lane's column sums come to T digits plus two
 // overflow digits, which belong to the next lane's first two columns; they are
 // added there, the carries between lanes are resolved with the ballot-mask
 // addition of addsub, and the strip's own two overflow digits (those of lane
@@ -364,9 +364,8 @@ __device__ __forceinline__ void mac3(uint32_t& c0, uint32_t& c1, uint32_t& c2, u
 // strip's digits to C (columns < npos).
 template <int T>
 __device__ __forceinline__ void mul_strip(const Blk& b, uint32_t* C, int npos, const uint32_t* A, int na,
-                                          const uint32_t* Bv, int nb, uint32_t* OV, int ws) {
+                                          const uint32_t* Bv, int nb, uint32_t* OV, int P0, int ws) {
   constexpr int WSPAN = 32 * T;
-  const int P0 = ws * WSPAN;
   const int jlo = max(0, P0 - na + 1);
   const int jhi = min(nb, P0 + WSPAN);
   const int p0 = P0 + b.lane * T;
@@ -474,16 +473,17 @@ __host__ __device__ __forceinline__ unsigned long long pair_count(int na, int nb
   return s;
 }
 
-// Order of warp strips, heaviest first: strips on the plateau of the
-// trapezoid of row counts (every row of the shorter operand) come first, then
-// strips alternately left and right of it by distance. The band [ws0, nws) is
-// the part of the product that is computed.
-__device__ __forceinline__ int strip_order(int idx, int ws0, int nws, int na, int nb, int WSPAN) {
-  int lo = (min(na, nb) - 1) / WSPAN;  // first strip whose rows reach the shorter length
-  if (lo < 0) lo = 0;
-  int hi = (max(na, nb) - 1) / WSPAN;  // last strip before the ramp down
-  lo = min(max(lo, ws0), nws - 1);
-  hi = min(max(hi, ws0), nws - 1);
+// Order of the nws warp strips of a product whose strip ws starts at column
+// base + ws * WSPAN, heaviest first: strips on the plateau of the trapezoid of
+// row counts (every row of the shorter operand) come first, then strips
+// alternately left and right of it by distance.
+__device__ __forceinline__ int strip_order(int idx, int nws, int base, int na, int nb, int WSPAN) {
+  const int ws0 = 0;
+  const int c_lo = min(na, nb) - 1 - base, c_hi = max(na, nb) - 1 - base;
+  int lo = c_lo < 0 ? 0 : c_lo / WSPAN;  // first strip whose rows reach the shorter length
+  int hi = c_hi < 0 ? 0 : c_hi / WSPAN;  // last strip before the ramp down
+  lo = min(lo, nws - 1);
+  hi = min(hi, nws - 1);
   if (hi < lo) hi = lo;
   const int np = hi - lo + 1;
   if (idx < np) return lo + idx;
@@ -500,19 +500,17 @@ template <int T>
 __device__ __forceinline__ void mul_t(const Blk& b, uint32_t* C, int npos, uint32_t* A, int na, uint32_t* Bv, int nb,
                                       uint32_t* OV, int plo, bool compact) {
   constexpr int WSPAN = 32 * T;
-  const int ws0 = plo / WSPAN;
-  const int nws = (npos + WSPAN - 1) / WSPAN;
-  const int cnt = nws - ws0;
-  const int p0 = ws0 * WSPAN;
-  // compact: column c lives at C[c - p0] and strip ws's overflow at OV[2 (ws - ws0)]
-  uint32_t* Cw = compact ? C - p0 : C;
-  uint32_t* OVw = compact ? OV - 2 * ws0 : OV;
+  // strips start at column plo exactly: strip ws covers [plo + ws WSPAN, ...)
+  const int nws = (npos - plo + WSPAN - 1) / WSPAN;
+  // compact: column c lives at C[c - plo]
+  uint32_t* Cw = compact ? C - plo : C;
   while (true) {
     int idx = 0;
     if (b.lane == 0) idx = atomicAdd(&b.red[RED_CNT], 1);
     idx = __shfl_sync(FULL, idx, 0);
-    if (idx >= cnt) break;
-    mul_strip<T>(b, Cw, npos, A, na, Bv, nb, OVw, strip_order(idx, ws0, nws, na, nb, WSPAN));
+    if (idx >= nws) break;
+    const int ws = strip_order(idx, nws, plo, na, nb, WSPAN);
+    mul_strip<T>(b, Cw, npos, A, na, Bv, nb, OV, plo + ws * WSPAN, ws);
   }
   b.sync();
   // fold each strip's two overflow digits into the next strip's first two
@@ -520,23 +518,23 @@ __device__ __forceinline__ void mul_t(const Blk& b, uint32_t* C, int npos, uint3
   // (rare: it needs the high overflow digit plus the column to reach B) is
   // recorded in the consumed overflow word and added afterwards, boundary by
   // boundary, with a full carry ripple
-  for (int s = ws0 + 1 + b.tid; s < nws; s += b.nt) {
-    const int c = s * WSPAN;  // < npos
-    uint64_t t = (uint64_t)Cw[c] + OVw[2 * (s - 1)];
+  for (int s = 1 + b.tid; s < nws; s += b.nt) {
+    const int c = plo + s * WSPAN;  // < npos
+    uint64_t t = (uint64_t)Cw[c] + OV[2 * (s - 1)];
     Cw[c] = (uint32_t)t;
     uint32_t k = 0u;
     if (c + 1 < npos) {
-      t = (uint64_t)Cw[c + 1] + OVw[2 * (s - 1) + 1] + (t >> 32);
+      t = (uint64_t)Cw[c + 1] + OV[2 * (s - 1) + 1] + (t >> 32);
       Cw[c + 1] = (uint32_t)t;
       k = (c + 2 < npos) ? (uint32_t)(t >> 32) : 0u;
     }
-    OVw[2 * (s - 1)] = k;
+    OV[2 * (s - 1)] = k;
     if (k) b.red[RED_RIPPLE] = 1;
   }
   b.sync();
   if (b.red[RED_RIPPLE] != 0 && b.warp == 0) {
-    for (int s = ws0 + 1; s < nws; s++)
-      if (OVw[2 * (s - 1)] != 0u) ripple_add_one(b, Cw, s * WSPAN + 2, npos);
+    for (int s = 1; s < nws; s++)
+      if (OV[2 * (s - 1)] != 0u) ripple_add_one(b, Cw, plo + s * WSPAN + 2, npos);
   }
   b.sync();  // also orders every read of RED_RIPPLE before the next multiply resets it
 }
@@ -544,25 +542,21 @@ __device__ __forceinline__ void mul_t(const Blk& b, uint32_t* C, int npos, uint3
 // Zero digits a multiply operand needs on each side for T columns per lane.
 __host__ __device__ __forceinline__ int pad_for(int tcols) { return 33 * (tcols == 3 ? 3 : (tcols == 7 ? 7 : 5)); }
 
-// Lowest column that mul(b, C, npos, X, nx, Y, ny, OV, plo) writes: the start
-// of the warp strip holding plo (whose columns are complete digit-product sums),
-// or plo itself when the product is empty or lies wholly below plo (then the
-// columns from plo up are written as zeros).
-__device__ __forceinline__ int mul_first_column(const Blk& b, int npos, int nx, int ny, int plo) {
-  if (plo <= 0) return 0;
-  if (nx <= 0 || ny <= 0 || npos <= plo) return min(plo, npos);
-  const int span = 32 * (b.tcols == 3 ? 3 : (b.tcols == 7 ? 7 : 5));
-  return (plo / span) * span;
+// Lowest column that mul(b, C, npos, X, nx, Y, ny, OV, plo) writes: plo itself
+// (clamped to [0, npos]); the columns from there up are complete digit-product
+// sums (zeros when the product is empty or lies wholly below plo).
+__device__ __forceinline__ int mul_first_column(int npos, int plo) {
+  return plo <= 0 ? 0 : min(plo, npos);
 }
 
 // Overflow words a multiply of at most npos columns needs (two per strip).
 __host__ __device__ __forceinline__ int ov_words(int npos) { return 2 * ((npos + 32 * T_MIN - 1) / (32 * T_MIN) + 4); }
 
 // C[plo..npos) of X * Y: the digits of (X * Y) mod B^npos at positions plo
-// and above, from the digit products at positions at or above the warp strip
-// holding plo; carries from products below that strip are dropped (plo = 0:
-// the exact product modulo B^npos). With `compact`, column c is stored at
-// C[c - p0], p0 = mul_first_column(...), which is returned; otherwise at C[c].
+// and above, from the digit products at positions plo and above only; the
+// carries from the products below plo are dropped (plo = 0: the exact product
+// modulo B^npos). With `compact`, column c is stored at C[c - p0], p0 =
+// mul_first_column(npos, plo), which is returned; otherwise at C[c].
 // X (nx digits) and Y (ny digits) are multiply operands: pad_for(b.tcols) zero
 // digits must be addressable below index 0 and above the digit count (the
 // high pads are zeroed here); an operand passed with x_rows needs only T_MAX
@@ -584,7 +578,7 @@ __device__ inline int mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int 
   if (plo < 0) plo = 0;
   if (b.work != nullptr && b.tid == 0)
     *b.work += pair_count(na, nb, npos) - pair_count(na, nb, min(plo, npos));
-  const int first = mul_first_column(b, npos, na, nb, plo);
+  const int first = mul_first_column(npos, plo);
   if (nb <= 0 || npos <= plo) {
     for (int i = plo + b.tid; i < npos; i += b.nt) C[compact ? i - first : i] = 0u;
     b.sync();

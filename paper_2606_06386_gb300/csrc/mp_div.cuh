@@ -26,7 +26,7 @@
 //   X  [kl+32]         divisor prefix v' and PowDiff result x      } u overlays
 //   R  [h-kl+16]       Step result before its shift                } X..R later
 //   P  products: clipped, max(h-kl+240, kl+32) (the clipped products keep
-//      only their top columns, stored from the first computed strip up);
+//      only their top columns, stored from the lowest kept column up);
 //      full, max(h+41, 2h-kl+9)
 //   OV [two words per 96-column strip of P] multiply overflow digits
 // The total is largest at kl = 1: about 3 h digits clipped, 4 h full.
@@ -56,10 +56,9 @@ struct Layout {
 };
 
 // Product buffer. Clipped: the Newton step keeps at most |R| - 1 digits above
-// its dropped ones plus QGUARD guard digits and the rest of the first strip
-// (< 32 T_MAX), i.e. at most h-kl+16+224 digits; the quotient at most
-// |W| + QGUARD + 32 T_MAX - 1; PowDiff's products and the remainder fit in
-// |X| = kl+32 digits. Full: the Newton step's and the quotient's full products.
+// its dropped ones plus QGUARD guard digits, i.e. at most h-kl+17 digits; the
+// quotient at most |W| + QGUARD; PowDiff's products and the remainder fit in
+// |X| = kl+32 digits (the bound below keeps 224 digits of room). Full: the Newton step's and the quotient's full products.
 __host__ __device__ __forceinline__ int cap_p(int h, int kl, bool clip) {
   if (clip) {
     const int a = h - kl + 240, c = kl + 32;
@@ -275,13 +274,13 @@ __device__ __forceinline__ int shinv(const Blk& b, const Layout& L, int h, int k
       if (!clip_step && nt > L.capP) return ST_INTERNAL;
       int p0 = 0;  // lowest column of w x; column c of the product is at P[c - p0]
       if (clip_step) {
-        // clipped: only the columns from e - QGUARD up (the strip holding it),
-        // so shift_{-e} of the product may come out one short (and the floor's
+        // clipped: only the digit products at columns e - QGUARD and up, so
+        // shift_{-e} of the product may come out one short (and the floor's
         // sticky digit is read from the computed columns only); the iterate may
         // then differ from Algorithm 1's by one unit, which Refine's later steps
         // and the quotient's corrections absorb
         const int plo = max(0, e - QGUARD);
-        p0 = mul_first_column(b, nt, pw, px, plo);
+        p0 = mul_first_column(nt, plo);
         if (nt - p0 > L.capP || ov_words(nt - p0) > L.capOV) return ST_INTERNAL;
         mul(b, P, nt, W, pw, X, px, L.OV, plo, false, true);
       } else {
@@ -383,10 +382,10 @@ __device__ __forceinline__ int div_item(const Blk& b, uint32_t* sm, int smem_wor
   load_global(b, U, h, [&](int i) { return gu[i]; });
   const int np = h + lw;
   // full: the exact product; clipped (Section 5's clipped products): only the
-  // columns at or above h - QGUARD (stored from the first computed strip up),
+  // digit products at columns h - QGUARD and up (stored from that column up),
   // so q0 may come out one short
   const int qlo = full ? 0 : max(0, h - QGUARD);
-  const int q0c = mul_first_column(b, np, h, lw, qlo);
+  const int q0c = mul_first_column(np, qlo);
   if (np - q0c > L.capP || ov_words(np - q0c) > L.capOV) return ST_INTERNAL;
   mul(b, P, np, U, h, W, lw, L.OV, qlo, false, true);
   const uint32_t* Pq = P - q0c;

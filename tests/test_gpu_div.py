@@ -84,9 +84,8 @@ def test_shinv_equals_model_and_theorem2():
     it = torch.zeros(len(vs), dtype=torch.int32, device="cuda:0")
     st = torch.full((len(vs),), -1, dtype=torch.int32, device="cuda:0")
     h_t = torch.tensor(hs, dtype=torch.int32, device="cuda:0")
-    # default (clipped Newton steps, 3 columns per lane: 96-column strips) and
-    # the paper's full products
-    for flags, span in ((0, 96), (mp.MPDIV_FLAG_FULL_PRODUCTS, None)):
+    # default (clipped Newton steps) and the paper's full products
+    for flags, clip in ((0, True), (mp.MPDIV_FLAG_FULL_PRODUCTS, False)):
         out.zero_()
         st.fill_(-1)
         mp.mpdiv_debug_shinv(ctx(flags=flags, cols=3), dev(V), h_t, out, it, st)
@@ -97,10 +96,10 @@ def test_shinv_equals_model_and_theorem2():
         for i, (v, h) in enumerate(zip(vs, hs)):
             assert S[i] == 0
             tr = M.Trace()
-            s_model = M.shinv(v, h, B, tr, span)
+            s_model = M.shinv(v, h, B, tr, clip)
             s_gpu = oracle.to_int(O[i])
             assert s_gpu == s_model, (i, v, h, flags)
-            assert s_gpu - B**h // v in ((0, 1) if span is None else (-1, 0, 1, 2))
+            assert s_gpu - B**h // v in ((-1, 0, 1, 2) if clip else (0, 1))
             assert I_[i] == tr.iterations
 
 
@@ -128,7 +127,7 @@ def test_product_counter_equals_model(n, kl, full):
         if full:
             M.div(u, v, B, tr)
         else:
-            assert M.div_clipped(u, v, B, tr, span=96) == divmod(u, v)
+            assert M.div_clipped(u, v, B, tr, clip_step=True) == divmod(u, v)
         assert P[i] == tr.digit_products()
 
 
