@@ -389,6 +389,8 @@ def run_mixed(args, dev, dist, rank, ws):
 
     mp.build()
     ctx = mp.mpdiv_init(dev.index or 0)
+    for c in (1024, 2048, 4096, 8192):  # tuned shape per size class, for both launch forms
+        mp.mpdiv_autotune(ctx, c, c // 2, 1024)
     u_len, v_len = I.mixed_sizes(8192)
     R = _ragged_setup(u_len, v_len, seed=I.SEED_BASE + 2, dev=dev)
     stream = torch.cuda.current_stream(dev)
@@ -406,8 +408,6 @@ def run_mixed(args, dev, dist, rank, ws):
     with ClockSampler(dev.index or 0) as clk:
         ms_persist = _time(persistent, stream, args.steps)
     classes = _class_batches(R, None, dev, key=lambda n: 1 << max(10, (n - 1).bit_length()))
-    for c in (1024, 2048, 4096, 8192):  # tuned block size per class for the plain launches
-        mp.mpdiv_autotune(ctx, c, c // 2, 1024)
     per_n = _class_batches(R, None, dev, key=lambda n: n)
 
     def plain(batches):
@@ -451,6 +451,8 @@ def run_serve(args, dev, dist, rank, ws):
 
     mp.build()
     ctx = mp.mpdiv_init(dev.index or 0)
+    for c in (1024, 2048, 4096, 8192):  # tuned shape per size class, for both launch forms
+        mp.mpdiv_autotune(ctx, c, c // 2, 1024)
     u_len, v_len = I.mixed_sizes(8192)
     R = _ragged_setup(u_len, v_len, seed=I.SEED_BASE + 2, dev=dev)
     stream = torch.cuda.current_stream(dev)

@@ -41,13 +41,20 @@ struct RaggedArgs {
   int64_t n;
   int smem_words;
   int flags;
-  int split_digits[2];  // k_div_persistent: largest dividend for 4 and for 8 warps
   int tcols;            // columns per lane (0 in k_div_persistent: chosen per item)
-  int tcols_class[4];   // k_div_persistent: columns per lane for dividends of <= 1024,
-                        // 2048, 4096 and more digits
-  int kcut;             // Karatsuba cutoff for full products (0: schoolbook only)
-  int kcut_class[4];    // k_div_persistent: the cutoff per size class (when kcut < 0)
+  // k_div_persistent, per size class of the dividend (<= 1024, 2048, 4096,
+  // 8192 and more digits, see class_of): columns per lane, Karatsuba cutoff
+  // (when kcut < 0) and the warps a division of that class wants
+  int tcols_class[5];
+  int kcut;  // Karatsuba cutoff for full products (0: schoolbook only)
+  int kcut_class[5];
+  int want_class[5];
 };
+
+// Size class of a dividend of ul digits in the persistent kernel's tables.
+__host__ __device__ __forceinline__ int class_of(int ul) {
+  return ul <= 1024 ? 0 : ul <= 2048 ? 1 : ul <= 4096 ? 2 : ul <= 8192 ? 3 : 4;
+}
 
 struct ShinvArgs {
   const uint32_t* v;

@@ -79,25 +79,27 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_ragged(RaggedArgs a) {
 }
 
 // Persistent launch that splits itself for smaller items. The block starts as
-// one group of all its warps over all of its dynamic shared memory and takes
-// items largest-first from the queue. When a group draws an item that fits in
-// half of its shared memory and wants at most half of its warps (a.split_digits
-// gives the largest dividend per warp count), the group splits into two
-// independent halves, each with its own named barrier and scratch: the first
-// half divides the drawn item, the second draws the next one. Groups split down
-// to kMinGroupWarps warps. Results are those of the plain launch: the division
-// code is the same, only the number of cooperating warps differs.
-constexpr int kMinGroupWarps = 4;
-constexpr int kMaxGroups = 7;  // binary tree of groups: 16 -> 8 -> 4 warps
+// one group of all its NW warps over all of its dynamic shared memory and
+// takes items largest-first from the queue. When a group draws an item whose
+// size class wants at most half of its warps (a.want_class, the tuned block
+// size of the plain launch) and whose working set fits in half of its shared
+// memory, the group splits into two independent halves, each with its own
+// named barrier and scratch: the first half divides the drawn item, the second
+// draws the next one. Groups split down to NW/4 warps. Results are those of the
+// plain launch: the division code is the same, only the number of cooperating
+// warps differs.
+constexpr int kMaxGroups = 7;  // binary tree of groups: NW -> NW/2 -> NW/4 warps
 
 template <int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_div_persistent(RaggedArgs a) {
+  constexpr int kMinGroupWarps = NW / 4;
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int red[kMaxGroups][RED_WORDS];
   int node = 0, w0 = 0, nw = NW;
   uint32_t* base = sm;
   int words = a.smem_words;
   int pending = -1;
+  const bool clip = (a.flags & FLAG_FULL_PRODUCTS) == 0;
   while (true) {
     Blk b = make_group(red[node], w0, nw, node);
     int idx;
@@ -113,10 +115,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_persistent(RaggedArgs a) 
     if ((int64_t)idx >= a.n) break;
     const int item = a.order[idx];
     const int ul = a.u_len[item];
+    const int cls = class_of(ul);
+    const int tcols = a.tcols > 0 ? a.tcols : a.tcols_class[cls];
     const int half_words = (words / 2) & ~3;
-    const int want = ul <= a.split_digits[0] ? 4 : (ul <= a.split_digits[1] ? 8 : 16);
-    if (nw >= 2 * kMinGroupWarps && 2 * node + 2 < kMaxGroups && want <= nw / 2 &&
-        smem_words_for(ul, (a.flags & FLAG_FULL_PRODUCTS) == 0, PAD) <= half_words) {
+    if (nw >= 2 * kMinGroupWarps && 2 * node + 2 < kMaxGroups && a.want_class[cls] <= nw / 2 &&
+        smem_words_for(ul, clip, layout_pad(clip, tcols)) <= half_words) {
       const bool left = b.warp < nw / 2;
       node = 2 * node + (left ? 1 : 2);
       nw /= 2;
@@ -141,8 +144,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_persistent(RaggedArgs a) 
     unsigned long long work = 0ull;
     Blk bw = b;
     bw.work = a.products ? &work : nullptr;
-    const int cls = ul <= 1024 ? 0 : ul <= 2048 ? 1 : ul <= 4096 ? 2 : 3;
-    bw.tcols = a.tcols > 0 ? a.tcols : a.tcols_class[cls];
+    bw.tcols = tcols;
     bw.kcut = a.kcut >= 0 ? a.kcut : a.kcut_class[cls];
     const int st = div_item(bw, base, words, io, a.flags, &it, nullptr, 0, 0);
     if (b.tid == 0) {

@@ -36,7 +36,7 @@ enum KernKind {
 // registers at 64 per thread so that several blocks of the smaller size
 // classes share an SM. The persistent kernel always runs 16-warp blocks.
 void* kernel_for(KernKind kk, int warps) {
-  if (kk == KK_PERSIST) return mp_kernel_w16(MP_K_PERSIST);
+  if (kk == KK_PERSIST) return warps <= 8 ? mp_kernel_w8(MP_K_PERSIST) : mp_kernel_w16(MP_K_PERSIST);
   if (warps <= 1) return mp_kernel_w1(kk);
   if (warps <= 2) return mp_kernel_w2(kk);
   if (warps <= 4) return mp_kernel_w4(kk);
@@ -129,6 +129,7 @@ extern "C" int mpdiv_init(mpdiv_ctx** out, int device, const mpdiv_config* cfg) 
   }
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaDeviceGetAttribute(&ctx->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  cudaDeviceGetAttribute(&ctx->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
   if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&ctx->d_head, 64), "cudaMalloc(queue head)")) != MPDIV_OK) {
     delete ctx;
     return rc;
@@ -250,13 +251,59 @@ static double item_cost(int n, int kl) {
   return a * n + a * kl + newton + 64.0;
 }
 
+// The self-splitting persistent launch's shape: per size class the strip
+// width, Karatsuba cutoff and warps wanted (the plain launch's tuned shape),
+// the block size (8 warps, or 16 when a class wants more than 8) and the
+// shared memory per block: enough for the largest item, and where the budget
+// of two (one) resident blocks per SM allows, for a class that wants half
+// (a quarter) of the block's warps to run in half (a quarter) of it.
+static void persistent_shape(mpdiv_ctx* ctx, int max_u, RaggedArgs& a, int* warps, int* smem_words) {
+  static const int kClassMax[5] = {1024, 2048, 4096, 8192, 16384};
+  const bool clip = (ctx->cfg.flags & MPDIV_FLAG_FULL_PRODUCTS) == 0;
+  const int cmax = class_of(max_u);
+  int wmax = 1;
+  for (int c = 0; c < 5; c++) {
+    a.tcols_class[c] = mpdiv_default_tcols(ctx, kClassMax[c]);
+    a.kcut_class[c] = mpdiv_default_kcut(ctx, kClassMax[c]);
+    a.want_class[c] = std::max(1, std::min(32, mpdiv_default_warps(ctx, kClassMax[c])));
+    if (c <= cmax) wmax = std::max(wmax, a.want_class[c]);
+  }
+  const int nw = wmax > 8 ? 16 : 8;
+  const int minb = nw == 8 ? 2 : 1;
+  for (int c = 0; c < 5; c++) a.want_class[c] = std::max(nw / 4, std::min(nw, a.want_class[c]));
+  auto need = [&](int c) {
+    const int d = std::min(max_u, kClassMax[c]);
+    return smem_words_for(d, clip, layout_pad(clip, a.tcols_class[c]));
+  };
+  int words = 0;
+  for (int c = 0; c <= cmax; c++) words = std::max(words, need(c));
+  const int budget = std::min(ctx->max_smem, (ctx->smem_per_sm - minb * 1024) / minb) / 4;
+  for (int c = 0; c <= cmax; c++) {
+    int cand = 0;
+    if (a.want_class[c] <= nw / 2) cand = 2 * need(c) + 8;
+    if (a.want_class[c] <= nw / 4) cand = std::max(cand, 4 * need(c) + 16);
+    if (cand <= budget) words = std::max(words, cand);
+  }
+  *warps = nw;
+  *smem_words = (words + 3) & ~3;
+}
+
 int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stream) {
   int max_u = 1;
   for (int64_t i = 0; i < L.n; i++) max_u = std::max(max_u, (int)L.u_len_host[i]);
-  const int smem = mpdiv_smem_bytes(max_u, ctx->cfg.flags, T_MAX);  // any strip width per item
+  RaggedArgs a;
+  std::memset(&a, 0, sizeof a);  // the graph cache compares argument blocks bytewise
+  int warps = 0, smem = 0;
+  if (L.split) {
+    int words = 0;
+    persistent_shape(ctx, max_u, a, &warps, &words);
+    smem = words * 4;
+  } else {
+    smem = mpdiv_smem_bytes(max_u, ctx->cfg.flags, T_MAX);  // any strip width per item
+    warps = L.warps > 0 ? L.warps : mpdiv_default_warps(ctx, max_u);
+  }
   if (smem > ctx->max_smem)
     return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory", smem);
-  const int warps = L.split ? 16 : (L.warps > 0 ? L.warps : mpdiv_default_warps(ctx, max_u));
   void* k = kernel_for(L.split ? KK_PERSIST : KK_RAGGED, warps);
   int rc = prepare_kernel(ctx, k, smem);
   if (rc) return rc;
@@ -301,8 +348,6 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
   int64_t grid = (int64_t)ctx->num_sms * occ;
   if (L.grid_items) grid = L.n;  // one block per item: later launches backfill freed SMs
   grid = std::max<int64_t>(1, std::min<int64_t>(grid, std::min<int64_t>(L.n, 0x7fffffff)));
-  RaggedArgs a;
-  std::memset(&a, 0, sizeof a);  // the graph cache compares argument blocks bytewise
   a.u = L.u;
   a.u_off = L.u_off;
   a.u_len = L.u_len;
@@ -323,11 +368,7 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
   a.n = L.n;
   a.smem_words = smem / 4;
   a.flags = ctx->cfg.flags;
-  a.split_digits[0] = ctx->split_digits[0];
-  a.split_digits[1] = ctx->split_digits[1];
-  a.tcols = L.split ? ctx->cfg.mul_columns : mpdiv_default_tcols(ctx, max_u);
-  for (int c = 0; c < 4; c++) a.tcols_class[c] = mpdiv_default_tcols(ctx, 1024 << c);
-  for (int c = 0; c < 4; c++) a.kcut_class[c] = mpdiv_default_kcut(ctx, 1024 << c);
+  a.tcols = L.split ? 0 : mpdiv_default_tcols(ctx, max_u);  // persistent: per class (configured or tuned)
   a.kcut = L.split ? -1 : mpdiv_default_kcut(ctx, max_u);
   if (!L.use_graph) {
     if ((rc = mpdiv_cuda_check(ctx, cudaMemsetAsync(a.head, 0, sizeof(int32_t), stream), "queue reset"))) return rc;

@@ -18,6 +18,7 @@ struct mpdiv_ctx {
   int device = 0;
   int num_sms = 0;
   int max_smem = 0;
+  int smem_per_sm = 0;  // shared memory of one SM (all resident blocks)
   mpdiv_config cfg{0, 0, 0, 0, 0};
   mutable std::mutex err_mu;
   std::string err;
@@ -40,9 +41,6 @@ struct mpdiv_ctx {
   int64_t g_grid = 0;
   int g_warps = 0, g_smem = 0;
   int64_t graph_captures = 0, graph_replays = 0;
-  // self-splitting persistent kernel: largest dividend (digits) for a group of
-  // 4 warps and for 8 warps; larger items use 16
-  int split_digits[2] = {1536, 3072};
   // serving
   MpServer* server = nullptr;
 };
@@ -81,7 +79,7 @@ struct RaggedLaunch {
   int warps;       // 0: from the tuning table
   bool use_graph;  // capture/replay as a CUDA graph
   bool grid_items; // one block per item instead of one wave of resident blocks
-  bool split;      // the self-splitting persistent kernel (16-warp blocks)
+  bool split;      // the self-splitting persistent kernel
 };
 
 int mpdiv_set_error(mpdiv_ctx* ctx, int code, const char* fmt, ...);

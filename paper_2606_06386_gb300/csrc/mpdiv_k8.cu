@@ -9,6 +9,7 @@ void* mp_kernel_w8(int kind) {
     case MP_K_RAGGED: return (void*)mp::k_div_ragged<8, 4>;
     case MP_K_SHINV: return (void*)mp::k_shinv<8, 4>;
     case MP_K_MUL: return (void*)mp::k_mul_low<8, 4>;
+    case MP_K_PERSIST: return (void*)mp::k_div_persistent<8, 2>;
     default: return nullptr;
   }
 }

@@ -6,6 +6,6 @@ enum { MP_K_UNIFORM = 0, MP_K_RAGGED = 1, MP_K_SHINV = 2, MP_K_PERSIST = 3, MP_K
 void* mp_kernel_w1(int kind);
 void* mp_kernel_w2(int kind);
 void* mp_kernel_w4(int kind);
-void* mp_kernel_w8(int kind);
-void* mp_kernel_w16(int kind);  // also the self-splitting persistent kernel (16 warps)
+void* mp_kernel_w8(int kind);  // also the self-splitting persistent kernel (8 -> 4 -> 2 warps)
+void* mp_kernel_w16(int kind);  // also the self-splitting persistent kernel (16 -> 8 -> 4 warps)
 void* mp_kernel_w32(int kind);

@@ -57,16 +57,28 @@ def _ragged(u_len, v_len, seed, c=None, edge=False):
     return IT
 
 
-def test_mixed_precision_persistent_launch():
+@pytest.mark.parametrize("warps", [0, 2, 4, 16])
+def test_mixed_precision_persistent_launch(warps):
+    # block shapes of the self-splitting kernel: untuned defaults (16-warp
+    # blocks splitting to 8 and 4), and configured block sizes 2 and 4 (8-warp
+    # blocks splitting to 4 and 2 warps) and 16 (16-warp blocks, no split)
     u_len, v_len = I.mixed_sizes(192, seed=I.SEED_BASE + 20)
-    _ragged(u_len, v_len, seed=5)
+    _ragged(u_len, v_len, seed=5, c=ctx(warps=warps))
 
 
-def test_mixed_small_shapes_and_edges():
+@pytest.mark.parametrize("warps", [0, 2])
+def test_mixed_small_shapes_and_edges(warps):
     rnd = np.random.default_rng(3)
     u_len = rnd.integers(1, 300, size=200).astype(np.int32)
     v_len = np.maximum(1, (u_len * rnd.uniform(0.05, 1.3, size=200)).astype(np.int32))
-    _ragged(u_len, v_len, seed=6, edge=True)
+    _ragged(u_len, v_len, seed=6, edge=True, c=ctx(warps=warps))
+
+
+def test_mixed_with_2e19_bit_items():
+    # the persistent launch with dividends up to 2^19 bits in the queue
+    u_len = np.array([16384, 9000, 4096, 2048, 1000, 16384, 300, 8192], np.int32)
+    v_len = np.array([8192, 100, 4000, 1024, 999, 16000, 150, 8192], np.int32)
+    _ragged(u_len, v_len, seed=8)
 
 
 @pytest.mark.parametrize("variant", I.STRESS_VARIANTS)
