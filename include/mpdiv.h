@@ -129,10 +129,13 @@ int mpdiv_batch_ragged(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, const
                        const int32_t *u_len_host, const int32_t *v_len_host, void *stream);
 
 /* Test entry: the shifted inverse of Algorithm 1 for each item, as the
- * division path computes it: out + i*out_stride gets shinv_h(v_i) (out_limbs
- * digits, zero-padded) with h = h_digits[i] (device int32 array), iters[i]
- * the Refine iteration count. By Theorem 2 the value is floor(B^h/v) or one
- * more. Requires v_i != 0 and h_i >= prec(v_i); otherwise status[i] is set. */
+ * division path computes it (16-warp blocks; the context's strip width, 5 if
+ * unset, and its MPDIV_FLAG_FULL_PRODUCTS flag): out + i*out_stride gets
+ * shinv_h(v_i) (out_limbs digits, zero-padded) with h = h_digits[i] (device
+ * int32 array), iters[i] the Refine iteration count. With full products the
+ * value is floor(B^h/v) or one more (Theorem 2); with the default clipped
+ * Newton steps it can differ from that by one more unit either way. Requires
+ * v_i != 0 and h_i >= prec(v_i); otherwise status[i] is set. */
 int mpdiv_debug_shinv(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *v, int32_t v_limbs, int64_t v_stride,
                       const int32_t *h_digits, uint32_t *out, int32_t out_limbs, int64_t out_stride,
                       int32_t *iters, int32_t *status, void *stream);

@@ -37,6 +37,7 @@ enum KernKind {
 // classes share an SM. The persistent kernel always runs 16-warp blocks.
 void* kernel_for(KernKind kk, int warps) {
   if (kk == KK_PERSIST) return warps <= 8 ? mp_kernel_w8(MP_K_PERSIST) : mp_kernel_w16(MP_K_PERSIST);
+  if (kk == KK_RAGGED || kk == KK_SHINV) return mp_kernel_w16(kk);  // 16-warp blocks only
   if (warps <= 1) return mp_kernel_w1(kk);
   if (warps <= 2) return mp_kernel_w2(kk);
   if (warps <= 4) return mp_kernel_w4(kk);
@@ -110,9 +111,39 @@ int mpdiv_size_class(int digits) {
   return c;
 }
 
+// The dynamic shared memory each kernel has been opened to, per device. The
+// attribute belongs to the kernel, not to a context, so it is only ever raised:
+// a launch that needs less than an earlier one (of any context) keeps the
+// larger opening and skips the driver call.
+static std::mutex g_open_mu;
+static std::map<std::pair<int, void*>, int> g_smem_opened;
+
+cudaError_t mpdiv_open_kernel_smem(void* k, int smem) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(g_open_mu);
+  int& opened = g_smem_opened[std::make_pair(dev, k)];
+  if (opened >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) opened = smem;
+  return e;
+}
+
 static int prepare_kernel(mpdiv_ctx* ctx, void* k, int smem) {
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  return mpdiv_cuda_check(ctx, e, "cudaFuncSetAttribute(max dynamic shared memory)");
+  return mpdiv_cuda_check(ctx, mpdiv_open_kernel_smem(k, smem), "cudaFuncSetAttribute(max dynamic shared memory)");
+}
+
+// Resident blocks per SM of kernel k at that block size and shared memory (cached).
+static int kernel_occupancy(mpdiv_ctx* ctx, void* k, int threads, int smem) {
+  std::lock_guard<std::mutex> g(ctx->attr_mu);
+  const auto key = std::make_tuple(k, threads, smem);
+  auto it = ctx->occupancy.find(key);
+  if (it != ctx->occupancy.end()) return it->second;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem) != cudaSuccess) occ = 0;
+  ctx->occupancy[key] = occ;
+  return occ;
 }
 
 // ------------------------------------------------------------------ init / destroy
@@ -300,7 +331,7 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
     smem = words * 4;
   } else {
     smem = mpdiv_smem_bytes(max_u, ctx->cfg.flags, T_MAX);  // any strip width per item
-    warps = L.warps > 0 ? L.warps : mpdiv_default_warps(ctx, max_u);
+    warps = 16;  // the one-block-per-item queue kernel is built for 16-warp blocks
   }
   if (smem > ctx->max_smem)
     return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory", smem);
@@ -341,8 +372,7 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
     ctx->order_hash = hsh;
     ctx->order_n = L.n;
   }
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 32 * warps, smem);
+  int occ = kernel_occupancy(ctx, k, 32 * warps, smem);
   if (occ < 1) return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "kernel does not fit on an SM");
   if (ctx->cfg.blocks_per_sm > 0) occ = std::min(occ, ctx->cfg.blocks_per_sm);
   int64_t grid = (int64_t)ctx->num_sms * occ;
@@ -477,7 +507,7 @@ extern "C" int mpdiv_debug_shinv(mpdiv_ctx* ctx, int64_t n_items, const uint32_t
   int max_h = MPDIV_MAX_LIMBS;
   while (max_h > 256 && mpdiv_smem_bytes(max_h, ctx->cfg.flags, tcols) > ctx->max_smem) max_h -= 256;
   const int smem = mpdiv_smem_bytes(max_h, ctx->cfg.flags, tcols);
-  const int warps = ctx->cfg.warps_per_block > 0 ? ctx->cfg.warps_per_block : 16;
+  const int warps = 16;  // the test entry is built for 16-warp blocks
   void* k = kernel_for(KK_SHINV, warps);
   int rc = prepare_kernel(ctx, k, smem);
   if (rc) return rc;

@@ -6,6 +6,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 
 #include <cuda_runtime.h>
 
@@ -30,6 +31,9 @@ struct mpdiv_ctx {
   std::map<int, Shape> tuned;
   // persistent launch: queue head, cached order, cached graph
   std::mutex ragged_mu;
+  // occupancies by (kernel, threads, shared memory)
+  std::mutex attr_mu;
+  std::map<std::tuple<void*, int, int>, int> occupancy;
   int32_t* d_head = nullptr;
   int32_t* d_order = nullptr;
   size_t order_cap = 0;
@@ -85,6 +89,9 @@ struct RaggedLaunch {
 int mpdiv_set_error(mpdiv_ctx* ctx, int code, const char* fmt, ...);
 int mpdiv_cuda_check(mpdiv_ctx* ctx, cudaError_t e, const char* what);
 int mpdiv_smem_bytes(int max_digits, int flags, int tcols);
+// Raise kernel k's dynamic shared memory limit on the current device to at
+// least smem bytes (never lowers it; shared by every context and entry point).
+cudaError_t mpdiv_open_kernel_smem(void* k, int smem);
 int mpdiv_size_class(int digits);
 int mpdiv_default_warps(mpdiv_ctx* ctx, int max_digits);
 int mpdiv_default_tcols(mpdiv_ctx* ctx, int max_digits);

@@ -8,8 +8,6 @@
 void* mp_kernel_w1(int kind) {
   switch (kind) {
     case MP_K_UNIFORM: return (void*)mp::k_div_uniform<1, 32>;
-    case MP_K_RAGGED: return (void*)mp::k_div_ragged<1, 32>;
-    case MP_K_SHINV: return (void*)mp::k_shinv<1, 32>;
     case MP_K_MUL: return (void*)mp::k_mul_low<1, 32>;
     default: return nullptr;
   }

@@ -6,10 +6,10 @@
 void* mp_kernel_w16(int kind) {
   switch (kind) {
     case MP_K_UNIFORM: return (void*)mp::k_div_uniform<16, 2>;
-    case MP_K_RAGGED: return (void*)mp::k_div_ragged<16, 2>;
-    case MP_K_SHINV: return (void*)mp::k_shinv<16, 2>;
+    case MP_K_RAGGED: return mp_kernel_w16_queue(kind);
+    case MP_K_SHINV: return mp_kernel_w16_queue(kind);
     case MP_K_MUL: return (void*)mp::k_mul_low<16, 2>;
-    case MP_K_PERSIST: return (void*)mp::k_div_persistent<16, 1>;
+    case MP_K_PERSIST: return mp_kernel_persistent(16);
     default: return nullptr;
   }
 }

@@ -8,8 +8,6 @@
 void* mp_kernel_w2(int kind) {
   switch (kind) {
     case MP_K_UNIFORM: return (void*)mp::k_div_uniform<2, 16>;
-    case MP_K_RAGGED: return (void*)mp::k_div_ragged<2, 16>;
-    case MP_K_SHINV: return (void*)mp::k_shinv<2, 16>;
     case MP_K_MUL: return (void*)mp::k_mul_low<2, 16>;
     default: return nullptr;
   }

@@ -6,8 +6,6 @@
 void* mp_kernel_w32(int kind) {
   switch (kind) {
     case MP_K_UNIFORM: return (void*)mp::k_div_uniform<32, 1>;
-    case MP_K_RAGGED: return (void*)mp::k_div_ragged<32, 1>;
-    case MP_K_SHINV: return (void*)mp::k_shinv<32, 1>;
     case MP_K_MUL: return (void*)mp::k_mul_low<32, 1>;
     default: return nullptr;
   }

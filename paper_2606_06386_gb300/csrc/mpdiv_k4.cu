@@ -6,8 +6,6 @@
 void* mp_kernel_w4(int kind) {
   switch (kind) {
     case MP_K_UNIFORM: return (void*)mp::k_div_uniform<4, 8>;
-    case MP_K_RAGGED: return (void*)mp::k_div_ragged<4, 8>;
-    case MP_K_SHINV: return (void*)mp::k_shinv<4, 8>;
     case MP_K_MUL: return (void*)mp::k_mul_low<4, 8>;
     default: return nullptr;
   }

@@ -6,10 +6,8 @@
 void* mp_kernel_w8(int kind) {
   switch (kind) {
     case MP_K_UNIFORM: return (void*)mp::k_div_uniform<8, 4>;
-    case MP_K_RAGGED: return (void*)mp::k_div_ragged<8, 4>;
-    case MP_K_SHINV: return (void*)mp::k_shinv<8, 4>;
     case MP_K_MUL: return (void*)mp::k_mul_low<8, 4>;
-    case MP_K_PERSIST: return (void*)mp::k_div_persistent<8, 2>;
+    case MP_K_PERSIST: return mp_kernel_persistent(8);
     default: return nullptr;
   }
 }

@@ -1,4 +1,6 @@
-// Getters for the kernel instantiations of each block size (mpdiv_k*.cu).
+// Getters for the kernel instantiations of each block size (mpdiv_k*.cu): the
+// plain division and multiplication kernels at every size; the queue, test and
+// persistent kernels where noted.
 #pragma once
 
 enum { MP_K_UNIFORM = 0, MP_K_RAGGED = 1, MP_K_SHINV = 2, MP_K_PERSIST = 3, MP_K_MUL = 4 };
@@ -7,5 +9,8 @@ void* mp_kernel_w1(int kind);
 void* mp_kernel_w2(int kind);
 void* mp_kernel_w4(int kind);
 void* mp_kernel_w8(int kind);  // also the self-splitting persistent kernel (8 -> 4 -> 2 warps)
-void* mp_kernel_w16(int kind);  // also the self-splitting persistent kernel (16 -> 8 -> 4 warps)
+void* mp_kernel_w16(int kind);  // also the self-splitting persistent kernel (16 -> 8 -> 4 warps),
+                                // the one-block-per-item queue kernel and the shifted-inverse test entry
 void* mp_kernel_w32(int kind);
+void* mp_kernel_persistent(int warps);  // mpdiv_p.cu: 8 (warps <= 8) or 16 warps per block
+void* mp_kernel_w16_queue(int kind);    // mpdiv_q.cu: MP_K_RAGGED and MP_K_SHINV

@@ -22,6 +22,8 @@
 #include "mp_kernels.cuh"
 #include "mpdiv.h"
 
+cudaError_t mpdiv_open_kernel_smem(void* k, int smem);  // mpdiv.cu: raise-only, shared with the context path
+
 namespace {
 
 constexpr int kBuckets = 64;
@@ -121,7 +123,7 @@ extern "C" int mpdiv_batch_ragged_noalloc(int64_t n_items, const uint32_t* u, co
   const int smem = (mp::smem_words_for(max_u, true, mp::PAD) * 4 + 15) & ~15;
   if (smem > max_smem) return MPDIV_EUNSUPPORTED;
   void* k = (void*)mp::k_div_ragged<kWarps, kMinBlocks>;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return MPDIV_ECUDA;
+  if (mpdiv_open_kernel_smem(k, smem) != cudaSuccess) return MPDIV_ECUDA;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 32 * kWarps, smem) != cudaSuccess || occ < 1)
     return MPDIV_ECUDA;

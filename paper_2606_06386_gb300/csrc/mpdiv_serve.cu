@@ -7,8 +7,7 @@
 // itself, outside the server lock. A scheduler thread turns the oldest ready
 // requests into a batch: a contiguous run of the input ring (one host-to-device
 // copy), per-item offsets and a largest-first order (one more copy), one launch
-// per dividend size class (each sized for its class, one block per item, so
-// blocks of the next batch fill SMs as blocks of this one retire), and one
+// of the self-splitting persistent kernel over the batch's queue, and one
 // device-to-host copy of the batch's results, all on the batch's own stream.
 // Up to max_inflight batches run at once. While fewer than low_water requests
 // are on the GPU, queued requests launch at once; under load they gather into
@@ -102,8 +101,6 @@ struct Ring {
   }
 };
 
-int size_class(int32_t ul) { return ul <= 1024 ? 0 : ul <= 2048 ? 1 : ul <= 4096 ? 2 : 3; }
-
 }  // namespace
 
 struct MpServer {
@@ -171,8 +168,7 @@ bool MpServer::launch(Slot& s) {
   }
   std::iota(order, order + n, 0);
   std::stable_sort(order, order + n, [&](int32_t a, int32_t b) {
-    const int ca = size_class(s.reqs[a]->u_len), cb = size_class(s.reqs[b]->u_len);
-    if (ca != cb) return ca > cb;
+    if (s.reqs[a]->u_len != s.reqs[b]->u_len) return s.reqs[a]->u_len > s.reqs[b]->u_len;
     return cost[a] > cost[b];
   });
   std::memset(heads, 0, 8 * sizeof(int32_t));
@@ -186,11 +182,10 @@ bool MpServer::launch(Slot& s) {
   const int32_t* d_len = reinterpret_cast<const int32_t*>(s.d_meta + 8 * n);
   int32_t* d_status = reinterpret_cast<int32_t*>(s.d_meta + status_w);
   int rc = (e == cudaSuccess) ? MPDIV_OK : MPDIV_ECUDA;
-  for (int64_t beg = 0; beg < n && rc == MPDIV_OK;) {
-    const int c = size_class(s.reqs[order[beg]]->u_len);
-    int64_t end = beg;
-    std::vector<int32_t> ulh;
-    while (end < n && size_class(s.reqs[order[end]]->u_len) == c) ulh.push_back(s.reqs[order[end++]]->u_len);
+  if (rc == MPDIV_OK) {
+    // one self-splitting persistent launch over the batch, largest first
+    std::vector<int32_t> ulh(n);
+    for (int64_t i = 0; i < n; i++) ulh[i] = s.reqs[i]->u_len;
     RaggedLaunch L{};
     L.u = d_in;
     L.u_off = d_off;
@@ -207,13 +202,12 @@ bool MpServer::launch(Slot& s) {
     L.status = d_status;
     L.u_len_host = ulh.data();
     L.v_len_host = ulh.data();
-    L.order = d_len + 4 * n + beg;
-    L.head = const_cast<int32_t*>(d_len + 5 * n) + c;
-    L.n = end - beg;
+    L.order = d_len + 4 * n;
+    L.head = const_cast<int32_t*>(d_len + 5 * n);
+    L.n = n;
     L.use_graph = false;
-    L.grid_items = true;
+    L.split = true;
     rc = mpdiv_launch_ragged(ctx, L, s.stream);
-    beg = end;
   }
   if (rc == MPDIV_OK)
     e = cudaMemcpyAsync(h_out + s.out_off, d_out + s.out_off, 4 * (size_t)(pq - s.out_off), cudaMemcpyDeviceToHost,
