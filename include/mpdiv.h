@@ -188,8 +188,10 @@ int mpdiv_serve_start(mpdiv_ctx *ctx, const mpdiv_serve_config *cfg);
 
 /* Submit one division from host memory; the operands are copied before the
  * call returns. *ticket identifies the request. MPDIV_EBUSY when the request
- * would exceed max_pending or can never fit the pool; MPDIV_EUNSUPPORTED for
- * sizes beyond MPDIV_MAX_LIMBS. */
+ * would exceed max_pending, finds the pool full (retry later) or can never fit
+ * it, or when the ticket 2*max_pending (rounded up to a power of two) before
+ * it has not been polled yet; MPDIV_EUNSUPPORTED for sizes beyond
+ * MPDIV_MAX_LIMBS. Thread-safe. */
 int mpdiv_serve_submit(mpdiv_ctx *ctx, const uint32_t *u_host, int32_t u_len, const uint32_t *v_host,
                        int32_t v_len, uint64_t *ticket);
 
@@ -197,7 +199,8 @@ int mpdiv_serve_submit(mpdiv_ctx *ctx, const uint32_t *u_host, int32_t u_len, co
  * done, after copying q (q_cap digits, zero-padded; q_cap >= u_len - prec(v) + 1
  * always suffices) and r (r_cap >= v_len digits) to host memory and the item
  * status to *status. A finished ticket can be polled once; afterwards it is
- * MPDIV_EINVAL. timeout_us > 0 waits up to that long for completion
+ * MPDIV_EINVAL. Thread-safe; a finished ticket is collected without the
+ * server's lock. timeout_us > 0 waits up to that long for completion
  * (MPDIV_ETIMEDOUT after); 0 returns at once. */
 int mpdiv_serve_poll(mpdiv_ctx *ctx, uint64_t ticket, uint32_t *q_host, int32_t q_cap, uint32_t *r_host,
                      int32_t r_cap, int32_t *status, int64_t timeout_us);

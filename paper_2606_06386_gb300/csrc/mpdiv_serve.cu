@@ -23,7 +23,6 @@
 #include <memory>
 #include <numeric>
 #include <thread>
-#include <unordered_map>
 #include <vector>
 
 #include "mpdiv_internal.h"
@@ -42,7 +41,7 @@ enum ReqState { RQ_QUEUED = 0, RQ_RUNNING = 1, RQ_DONE = 2 };
 // the batch has been polled.
 struct OutBatch {
   int64_t seq = -1;
-  int remaining = 0;
+  std::atomic<int> remaining{0};
 };
 
 struct Request {
@@ -54,7 +53,7 @@ struct Request {
   std::shared_ptr<OutBatch> out;  // the batch's output allocation
   std::atomic<int> ready{0};      // operands copied into the ring
   int32_t status = 0;
-  int state = RQ_QUEUED;
+  std::atomic<int> state{RQ_QUEUED};  // RQ_DONE is published with release order
   int64_t t_submit = 0, t_done = 0;
 };
 
@@ -111,7 +110,10 @@ struct MpServer {
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
   std::deque<Request*> queue;
-  std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
+  // request of ticket t at by_ticket[t & ticket_mask], owned there until it is
+  // polled (a poller claims it by swapping the slot to null, without the lock)
+  std::unique_ptr<std::atomic<Request*>[]> by_ticket;
+  uint64_t ticket_mask = 0;
   uint64_t next_ticket = 1;
   int64_t pending = 0, inflight_items = 0;
   bool stopping = false, quit = false;
@@ -234,8 +236,8 @@ void MpServer::run() {
       for (int64_t i = 0; i < n; i++) {
         Request* r = s->reqs[i];
         r->status = st[i];
-        r->state = RQ_DONE;
         r->t_done = t;
+        r->state.store(RQ_DONE, std::memory_order_release);
         in_ring.release(r->in_seq);
       }
       completed += n;
@@ -284,7 +286,7 @@ void MpServer::run() {
         free_slot->out_off = off;
         free_slot->out_seq = oseq;
         free_slot->busy = true;
-        for (Request* r : b) r->state = RQ_RUNNING;
+        for (Request* r : b) r->state.store(RQ_RUNNING, std::memory_order_relaxed);
         const int64_t nb = (int64_t)b.size();
         inflight_items += nb;
         launches++;
@@ -299,8 +301,8 @@ void MpServer::run() {
             r->out.reset();  // no results: the output allocation is released below
             r->out_off = -1;
             r->status = MPDIV_ST_INTERNAL;
-            r->state = RQ_DONE;
             r->t_done = tf;
+            r->state.store(RQ_DONE, std::memory_order_release);
             in_ring.release(r->in_seq);
           }
           out_ring.release(oseq);
@@ -345,6 +347,13 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
   S->in_ring.cap = half;
   S->out_ring.cap = half;
   S->meta_words = meta_words_for(S->cfg.max_batch);
+  {
+    uint64_t cap = 1024;
+    while (cap < 2 * (uint64_t)S->cfg.max_pending) cap *= 2;
+    S->by_ticket.reset(new std::atomic<Request*>[cap]);
+    for (uint64_t i = 0; i < cap; i++) S->by_ticket[i].store(nullptr, std::memory_order_relaxed);
+    S->ticket_mask = cap - 1;
+  }
   int rc = mpdiv_cuda_check(ctx, cudaMalloc(&S->d_in, 4 * (size_t)half), "server input ring");
   if (!rc) rc = mpdiv_cuda_check(ctx, cudaMalloc(&S->d_out, 4 * (size_t)half), "server output ring");
   if (!rc) rc = mpdiv_cuda_check(ctx, cudaMallocHost(&S->h_in, 4 * (size_t)half), "server pinned input ring");
@@ -382,10 +391,13 @@ extern "C" int mpdiv_serve_submit(mpdiv_ctx* ctx, const uint32_t* u_host, int32_
   r->q_len = u_len;  // enough for any quotient
   r->r_len = v_len;
   Request* rp = r.get();
+  bool wake = false;
   {
     std::lock_guard<std::mutex> g(S->mu);
     if (S->stopping) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server stopping");
     if (S->pending >= S->cfg.max_pending) return MPDIV_EBUSY;
+    // the ticket's slot still holds an unpolled result from ticket - capacity
+    if (S->by_ticket[S->next_ticket & S->ticket_mask].load(std::memory_order_acquire) != nullptr) return MPDIV_EBUSY;
     int64_t seq = -1;
     const int64_t off = S->in_ring.alloc(u_len + v_len, &seq);
     if (off < 0) return MPDIV_EBUSY;  // input ring full: retry later
@@ -394,15 +406,18 @@ extern "C" int mpdiv_serve_submit(mpdiv_ctx* ctx, const uint32_t* u_host, int32_
     r->ticket = S->next_ticket++;
     r->t_submit = now_ns();
     *ticket = r->ticket;
+    // the scheduler re-checks a non-empty queue every few microseconds by
+    // itself; only a request into an empty queue needs to wake it
+    wake = S->queue.empty();
     S->queue.push_back(rp);
-    S->reqs.emplace(rp->ticket, std::move(r));
+    S->by_ticket[rp->ticket & S->ticket_mask].store(r.release(), std::memory_order_release);
     S->pending++;
   }
   // the operands go straight into the pinned ring; the scheduler waits for `ready`
   std::memcpy(S->h_in + rp->in_off, u_host, 4 * (size_t)u_len);
   std::memcpy(S->h_in + rp->in_off + u_len, v_host, 4 * (size_t)v_len);
   rp->ready.store(1, std::memory_order_release);
-  S->cv_sched.notify_one();
+  if (wake) S->cv_sched.notify_one();
   return MPDIV_OK;
 }
 
@@ -410,37 +425,36 @@ static int poll_impl(mpdiv_ctx* ctx, uint64_t ticket, uint32_t* q_host, int32_t 
                      int32_t r_cap, int32_t* status, int64_t timeout_us, int64_t* t_done) {
   MpServer* S = ctx->server;
   if (!S) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server not running");
-  std::unique_ptr<Request> done;
-  {
+  std::atomic<Request*>& slot = S->by_ticket[ticket & S->ticket_mask];
+  Request* r = slot.load(std::memory_order_acquire);
+  if (r == nullptr || r->ticket != ticket) return mpdiv_set_error(ctx, MPDIV_EINVAL, "unknown ticket");
+  if (r->state.load(std::memory_order_acquire) != RQ_DONE) {
+    if (timeout_us <= 0) return MPDIV_PENDING;
     std::unique_lock<std::mutex> lk(S->mu);
-    auto it = S->reqs.find(ticket);
-    if (it == S->reqs.end()) return mpdiv_set_error(ctx, MPDIV_EINVAL, "unknown ticket");
-    Request* r = it->second.get();
-    if (r->state != RQ_DONE) {
-      if (timeout_us <= 0) return MPDIV_PENDING;
-      const auto until = Clock::now() + std::chrono::microseconds(timeout_us);
-      while (r->state != RQ_DONE) {
-        if (S->sched_error && r->state == RQ_QUEUED)
-          return mpdiv_set_error(ctx, S->sched_error, "the server stopped after a failed launch");
-        if (S->cv_done.wait_until(lk, until) == std::cv_status::timeout && r->state != RQ_DONE)
-          return MPDIV_ETIMEDOUT;
-      }
+    const auto until = Clock::now() + std::chrono::microseconds(timeout_us);
+    while (r->state.load(std::memory_order_acquire) != RQ_DONE) {
+      if (S->sched_error && r->state.load(std::memory_order_relaxed) == RQ_QUEUED)
+        return mpdiv_set_error(ctx, S->sched_error, "the server stopped after a failed launch");
+      if (S->cv_done.wait_until(lk, until) == std::cv_status::timeout &&
+          r->state.load(std::memory_order_acquire) != RQ_DONE)
+        return MPDIV_ETIMEDOUT;
     }
-    const uint32_t* qd = r->out_off >= 0 ? S->h_out + r->out_off : nullptr;
-    if (qd && ((q_host && q_cap < r->q_len) || (r_host && r_cap < r->r_len))) {
-      // a short buffer is fine when the digits it drops are zero
-      int qs = r->q_len, rs = r->r_len;
-      while (qs > 0 && qd[qs - 1] == 0u) qs--;
-      while (rs > 0 && qd[r->q_len + rs - 1] == 0u) rs--;
-      if (q_host && qs > q_cap) return mpdiv_set_error(ctx, MPDIV_EINVAL, "q_cap too small (%d digits needed)", qs);
-      if (r_host && rs > r_cap) return mpdiv_set_error(ctx, MPDIV_EINVAL, "r_cap too small");
-    }
-    done = std::move(it->second);
-    S->reqs.erase(it);
   }
-  // the digits stay valid until this request's share of its batch is released below
-  const Request* r = done.get();
   const uint32_t* qd = r->out_off >= 0 ? S->h_out + r->out_off : nullptr;
+  if (qd && ((q_host && q_cap < r->q_len) || (r_host && r_cap < r->r_len))) {
+    // a short buffer is fine when the digits it drops are zero
+    int qs = r->q_len, rs = r->r_len;
+    while (qs > 0 && qd[qs - 1] == 0u) qs--;
+    while (rs > 0 && qd[r->q_len + rs - 1] == 0u) rs--;
+    if (q_host && qs > q_cap) return mpdiv_set_error(ctx, MPDIV_EINVAL, "q_cap too small (%d digits needed)", qs);
+    if (r_host && rs > r_cap) return mpdiv_set_error(ctx, MPDIV_EINVAL, "r_cap too small");
+  }
+  // claim the request: a concurrent poll of the same ticket finds it gone
+  Request* expect = r;
+  if (!slot.compare_exchange_strong(expect, nullptr, std::memory_order_acq_rel))
+    return mpdiv_set_error(ctx, MPDIV_EINVAL, "unknown ticket");
+  std::unique_ptr<Request> done(r);
+  // the digits stay valid until this request's share of its batch is released below
   if (q_host) {
     const int n = qd ? std::min(q_cap, r->q_len) : 0;
     if (n) std::memcpy(q_host, qd, 4 * (size_t)n);
@@ -453,9 +467,9 @@ static int poll_impl(mpdiv_ctx* ctx, uint64_t ticket, uint32_t* q_host, int32_t 
   }
   if (status) *status = r->status;
   if (t_done) *t_done = r->t_done;
-  if (r->out) {
+  if (r->out && r->out->remaining.fetch_sub(1, std::memory_order_acq_rel) == 1) {
     std::lock_guard<std::mutex> g(S->mu);
-    if (--r->out->remaining == 0) S->out_ring.release(r->out->seq);
+    S->out_ring.release(r->out->seq);
   }
   return MPDIV_OK;
 }
@@ -506,6 +520,8 @@ void mpdiv_serve_shutdown(mpdiv_ctx* ctx) {
     if (s.h_meta) cudaFreeHost(s.h_meta);
     if (s.d_meta) cudaFree(s.d_meta);
   }
+  if (S->by_ticket)
+    for (uint64_t i = 0; i <= S->ticket_mask; i++) delete S->by_ticket[i].exchange(nullptr);
   cudaFree(S->d_in);
   cudaFree(S->d_out);
   if (S->h_in) cudaFreeHost(S->h_in);
