@@ -200,3 +200,31 @@ def test_2e19_bits_beyond_the_paper(kind):
     with pytest.raises(mp.MpdivError) as e:
         mp.mpdiv_batch(ctx(flags=mp.MPDIV_FLAG_FULL_PRODUCTS), dev(U[:1]), dev(V[:1]), q, r, st)
     assert e.value.code == mp.MPDIV_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("cols", [3, 5, 7])
+def test_strip_fold_carry_ripple(cols):
+    # operands built so that every strip's two overflow digits, added to the
+    # next strip's first two columns, carry out of them: u is all ones except
+    # digits 1, 1 at each strip start (strips of 32 * cols columns), v = B - 1.
+    # Each strip's low two digits are then B^2 - 1 and the previous strip's
+    # overflow is B - 2, so the rare ripple path runs at every boundary.
+    import torch
+    import paper_2606_06386_gb300 as mp
+
+    n = 1000
+    w = 32 * cols
+    u = np.full(n, 0xFFFFFFFF, np.uint32)
+    for s in range(1, n // w + 1):
+        if s * w + 1 < n:
+            u[s * w] = u[s * w + 1] = 1
+    v = np.zeros(n, np.uint32)
+    v[0] = 0xFFFFFFFF
+    out = torch.zeros((2, n), dtype=torch.int32, device="cuda:0")
+    U = np.stack([u, v])
+    V = np.stack([v, u])  # both operand roles
+    mp.mpdiv_mul_batch(ctx(cols=cols), dev(U), dev(V), out)
+    torch.cuda.synchronize()
+    O = host_u32(out)
+    want = (oracle.to_int(u) * oracle.to_int(v)) % (B**n)
+    assert oracle.to_int(O[0]) == want and oracle.to_int(O[1]) == want
