@@ -495,10 +495,43 @@ __device__ __forceinline__ int strip_order(int idx, int nws, int base, int na, i
   return (nl > nr) ? lo - d : hi + d;
 }
 
+// Whether the kernels of a translation unit divide with groups that are
+// slices of a block under named barriers (the self-splitting persistent
+// kernel defines it to 1); otherwise every group is a whole block.
+#ifndef MP_NAMED_GROUPS
+#define MP_NAMED_GROUPS 0
+#endif
+
+// Group barrier: the block's own barrier when the group is the whole block
+// (WHOLE), so that a kernel whose groups are all whole blocks reserves one
+// barrier only; a named barrier otherwise.
+template <bool WHOLE>
+__device__ __forceinline__ void group_sync(const Blk& b) {
+  if (WHOLE)
+    __syncthreads();
+  else
+    b.sync();
+}
+
+// Whether the strip multiply is a called function rather than inlined at each
+// call site. A translation unit of small-block kernels defines it to 1: one
+// copy per strip width and group kind then serves every call site, which keeps
+// the instruction footprint of kernels that run many small divisions per SM
+// small (measured faster for one- and two-warp blocks); inlined is faster for
+// larger blocks.
+#ifndef MP_MUL_NOINLINE
+#define MP_MUL_NOINLINE 0
+#endif
+#if MP_MUL_NOINLINE
+#define MP_MUL_ATTR __noinline__
+#else
+#define MP_MUL_ATTR __forceinline__
+#endif
+
 // The strip multiply for T columns per lane (see mul).
-template <int T>
-__device__ __forceinline__ void mul_t(const Blk& b, uint32_t* C, int npos, uint32_t* A, int na, uint32_t* Bv, int nb,
-                                      uint32_t* OV, int plo, bool compact) {
+template <int T, bool WHOLE>
+__device__ MP_MUL_ATTR void mul_t(const Blk& b, uint32_t* C, int npos, uint32_t* A, int na, uint32_t* Bv, int nb,
+                                   uint32_t* OV, int plo, bool compact) {
   constexpr int WSPAN = 32 * T;
   // strips start at column plo exactly: strip ws covers [plo + ws WSPAN, ...)
   const int nws = (npos - plo + WSPAN - 1) / WSPAN;
@@ -512,7 +545,7 @@ __device__ __forceinline__ void mul_t(const Blk& b, uint32_t* C, int npos, uint3
     const int ws = strip_order(idx, nws, plo, na, nb, WSPAN);
     mul_strip<T>(b, Cw, npos, A, na, Bv, nb, OV, plo + ws * WSPAN, ws);
   }
-  b.sync();
+  group_sync<WHOLE>(b);
   // fold each strip's two overflow digits into the next strip's first two
   // columns, one thread per strip boundary; a carry out of those two columns
   // (rare: it needs the high overflow digit plus the column to reach B) is
@@ -531,12 +564,12 @@ __device__ __forceinline__ void mul_t(const Blk& b, uint32_t* C, int npos, uint3
     OV[2 * (s - 1)] = k;
     if (k) b.red[RED_RIPPLE] = 1;
   }
-  b.sync();
+  group_sync<WHOLE>(b);
   if (b.red[RED_RIPPLE] != 0 && b.warp == 0) {
     for (int s = 1; s < nws; s++)
       if (OV[2 * (s - 1)] != 0u) ripple_add_one(b, Cw, plo + s * WSPAN + 2, npos);
   }
-  b.sync();  // also orders every read of RED_RIPPLE before the next multiply resets it
+  group_sync<WHOLE>(b);  // also orders every read of RED_RIPPLE before the next multiply resets it
 }
 
 // Zero digits a multiply operand needs on each side for T columns per lane.
@@ -594,12 +627,13 @@ __device__ inline int mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int 
     b.red[RED_RIPPLE] = 0;
   }
   b.sync();
+  constexpr bool kWhole = !MP_NAMED_GROUPS;
   if (b.tcols == 3)
-    mul_t<3>(b, C, npos, A, na, Bv, nb, OV, plo, compact);
+    mul_t<3, kWhole>(b, C, npos, A, na, Bv, nb, OV, plo, compact);
   else if (b.tcols == 7)
-    mul_t<7>(b, C, npos, A, na, Bv, nb, OV, plo, compact);
+    mul_t<7, kWhole>(b, C, npos, A, na, Bv, nb, OV, plo, compact);
   else
-    mul_t<5>(b, C, npos, A, na, Bv, nb, OV, plo, compact);
+    mul_t<5, kWhole>(b, C, npos, A, na, Bv, nb, OV, plo, compact);
   return first;
 }
 

@@ -2,6 +2,7 @@
 // pair for the small precisions, so that many divisions share an SM and a
 // group barrier spans two warps (a separate translation unit, so that the
 // block sizes build in parallel).
+#define MP_MUL_NOINLINE 1  // the strip multiply as one called copy (see mp_block.cuh)
 #include "mp_kernels.cuh"
 #include "mpdiv_kernels.h"
 
