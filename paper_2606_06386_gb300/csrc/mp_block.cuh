@@ -54,7 +54,10 @@ struct Blk {
   int kcut;                  // Karatsuba for full products whose shorter operand has >= kcut digits (0: never)
 
   __device__ __forceinline__ void sync() const {
-    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
+    if (nt == 32)
+      __syncwarp();  // a one-warp group
+    else
+      asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
   }
 };
 
@@ -75,6 +78,28 @@ __device__ __forceinline__ Blk make_group(int* red, int w0, int nw, int bar) {
 }
 
 __device__ __forceinline__ Blk make_blk(int* red) { return make_group(red, 0, blockDim.x >> 5, 0); }
+
+// The whole block of a kernel built for NW warps: with the group size a
+// compile-time constant, one-warp groups skip their cross-warp summaries.
+template <int NW>
+__device__ __forceinline__ Blk make_block(int* red) { return make_group(red, 0, NW, 0); }
+
+// Group-wide maximum (minimum) of a warp-uniform value, one per warp; ends
+// with a group barrier.
+__device__ __forceinline__ int group_max(const Blk& b, int v) {
+  if (b.nw == 1) {
+    __syncwarp();
+    return v;
+  }
+  if (b.lane == 0) b.red[b.warp] = v;
+  b.sync();
+  int r = (b.lane < b.nw) ? b.red[b.lane] : -0x7fffffff - 1;
+  for (int o = 1; o < b.nw; o <<= 1) r = max(r, __shfl_xor_sync(FULL, r, o));
+  r = __shfl_sync(FULL, r, 0);
+  b.sync();
+  return r;
+}
+__device__ __forceinline__ int group_min(const Blk& b, int v) { return -group_max(b, -v); }
 
 // Range of a warp's digits for a linear operation over [0, len): a multiple of 32.
 __device__ __forceinline__ void warp_range(const Blk& b, int len, int& lo, int& hi) {
@@ -120,6 +145,10 @@ __device__ uint32_t addsub(const Blk& b, uint32_t* C, int len, FX X, FY Y, uint3
     if (valid) C[i] = SUB ? d - ci : d + ci;
     c = (uint32_t)(sum >> 32);
     allp = allp && (pm == FULL);
+  }
+  if (b.nw == 1) {  // one warp: its carry out is the result
+    __syncwarp();
+    return c;
   }
   if (b.lane == 0) b.red[b.warp] = (int)(c | ((allp && b.warp != 0) ? 2u : 0u));
   b.sync();
@@ -174,13 +203,7 @@ __device__ inline int find_last(const Blk& b, int lo, int hi, F pred) {
       if (base == wl) break;
     }
   }
-  if (b.lane == 0) b.red[b.warp] = best;
-  b.sync();
-  int r = (b.lane < b.nw) ? b.red[b.lane] : -1;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) r = max(r, __shfl_xor_sync(FULL, r, o));
-  b.sync();
-  return r;
+  return group_max(b, best);
 }
 
 // Smallest i in [lo, hi) with pred(i), or -1.
@@ -201,12 +224,7 @@ __device__ inline int find_first(const Blk& b, int lo, int hi, F pred) {
       }
     }
   }
-  if (b.lane == 0) b.red[b.warp] = best;
-  b.sync();
-  int r = (b.lane < b.nw) ? b.red[b.lane] : 0x7fffffff;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) r = min(r, __shfl_xor_sync(FULL, r, o));
-  b.sync();
+  const int r = group_min(b, best);
   return r == 0x7fffffff ? -1 : r;
 }
 
@@ -251,13 +269,7 @@ __device__ inline int copy_prec(const Blk& b, uint32_t* C, int len, FX X) {
     const uint32_t m = __ballot_sync(FULL, d != 0u);
     if (m) best = base + 31 - __clz(m);
   }
-  if (b.lane == 0) b.red[b.warp] = best;
-  b.sync();
-  int r = (b.lane < b.nw) ? b.red[b.lane] : -1;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) r = max(r, __shfl_xor_sync(FULL, r, o));
-  b.sync();
-  return r + 1;
+  return group_max(b, best) + 1;
 }
 
 // One pass over P[0..len): the lowest nonzero digit (*z), the highest
@@ -278,22 +290,29 @@ __device__ inline void scan3(const Blk& b, const uint32_t* P, int len, int* z, i
     }
     if (mf) b2 = base + 31 - __clz(mf);
   }
-  if (b.lane == 0) {
-    b.red[b.warp] = bz;
-    b.red[32 + b.warp] = b1;
-    b.red[64 + b.warp] = b2;
+  int rz = bz, r1 = b1, r2 = b2;
+  if (b.nw == 1) {
+    __syncwarp();
+  } else {
+    if (b.lane == 0) {
+      b.red[b.warp] = bz;
+      b.red[32 + b.warp] = b1;
+      b.red[64 + b.warp] = b2;
+    }
+    b.sync();
+    rz = (b.lane < b.nw) ? b.red[b.lane] : 0x7fffffff;
+    r1 = (b.lane < b.nw) ? b.red[32 + b.lane] : -1;
+    r2 = (b.lane < b.nw) ? b.red[64 + b.lane] : -1;
+    for (int o = 1; o < b.nw; o <<= 1) {
+      rz = min(rz, __shfl_xor_sync(FULL, rz, o));
+      r1 = max(r1, __shfl_xor_sync(FULL, r1, o));
+      r2 = max(r2, __shfl_xor_sync(FULL, r2, o));
+    }
+    rz = __shfl_sync(FULL, rz, 0);
+    r1 = __shfl_sync(FULL, r1, 0);
+    r2 = __shfl_sync(FULL, r2, 0);
+    b.sync();
   }
-  b.sync();
-  int rz = (b.lane < b.nw) ? b.red[b.lane] : 0x7fffffff;
-  int r1 = (b.lane < b.nw) ? b.red[32 + b.lane] : -1;
-  int r2 = (b.lane < b.nw) ? b.red[64 + b.lane] : -1;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    rz = min(rz, __shfl_xor_sync(FULL, rz, o));
-    r1 = max(r1, __shfl_xor_sync(FULL, r1, o));
-    r2 = max(r2, __shfl_xor_sync(FULL, r2, o));
-  }
-  b.sync();
   *z = rz == 0x7fffffff ? -1 : rz;
   *t1 = r1;
   *t2 = r2;
@@ -507,10 +526,12 @@ __device__ __forceinline__ int strip_order(int idx, int nws, int base, int na, i
 // barrier only; a named barrier otherwise.
 template <bool WHOLE>
 __device__ __forceinline__ void group_sync(const Blk& b) {
-  if (WHOLE)
+  if (!WHOLE)
+    b.sync();
+  else if (b.nt > 32)
     __syncthreads();
   else
-    b.sync();
+    __syncwarp();  // a one-warp block
 }
 
 // Whether the strip multiply is a called function rather than inlined at each

@@ -12,7 +12,7 @@ template <int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_div_uniform(UniformArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int red[RED_WORDS];
-  Blk b = make_blk(red);
+  Blk b = make_block<NW>(red);
   b.tcols = a.tcols;
   b.kcut = a.kcut;
   for (int64_t item = blockIdx.x; item < a.n; item += gridDim.x) {
@@ -45,7 +45,7 @@ template <int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_div_ragged(RaggedArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int red[RED_WORDS];
-  Blk b = make_blk(red);
+  Blk b = make_block<NW>(red);
   b.tcols = a.tcols > 0 ? a.tcols : 5;
   b.kcut = a.kcut > 0 ? a.kcut : 0;
   while (true) {
@@ -162,7 +162,7 @@ template <int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_mul_low(UniformArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int red[RED_WORDS];
-  Blk b = make_blk(red);
+  Blk b = make_block<NW>(red);
   b.tcols = a.tcols;
   const int n = a.un;
   uint32_t* X = sm + PAD;
@@ -184,7 +184,7 @@ template <int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_shinv(ShinvArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int red[RED_WORDS];
-  Blk b = make_blk(red);
+  Blk b = make_block<NW>(red);
   b.tcols = a.tcols > 0 ? a.tcols : 5;
   b.kcut = a.kcut > 0 ? a.kcut : 0;
   for (int64_t item = blockIdx.x; item < a.n; item += gridDim.x) {

@@ -72,13 +72,22 @@ int mpdiv_smem_bytes(int max_digits, int flags, int tcols) {
   return (smem_words_for(max_digits, clip, layout_pad(clip, tcols)) * 4 + 15) & ~15;
 }
 
+// The block size of the kernel instantiation that serves a request for w
+// warps: 1, 2, 4, 8, 16 or 32 (the kernels are built for exactly that many
+// warps, so a launch always uses this value).
+static int kernel_warps(int w) {
+  int k = 1;
+  while (k < w && k < 32) k *= 2;
+  return k;
+}
+
 int mpdiv_default_warps(mpdiv_ctx* ctx, int max_digits) {
-  if (ctx->cfg.warps_per_block > 0) return ctx->cfg.warps_per_block;
+  if (ctx->cfg.warps_per_block > 0) return kernel_warps(ctx->cfg.warps_per_block);
   {
     std::lock_guard<std::mutex> g(ctx->tune_mu);
     const int cls = mpdiv_size_class(max_digits);
     auto it = ctx->tuned.find(cls);
-    if (it != ctx->tuned.end()) return it->second.warps;
+    if (it != ctx->tuned.end()) return kernel_warps(it->second.warps);
   }
   if (max_digits <= 2048) return 4;
   if (max_digits <= 4096) return 8;
@@ -201,7 +210,7 @@ int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t st
   if (smem > ctx->max_smem)
     return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory, device allows %d", smem,
                            ctx->max_smem);
-  const int warps = L.warps > 0 ? L.warps : mpdiv_default_warps(ctx, max_digits);
+  const int warps = L.warps > 0 ? kernel_warps(L.warps) : mpdiv_default_warps(ctx, max_digits);
   void* k = kernel_for(KK_UNIFORM, warps);
   int rc = prepare_kernel(ctx, k, smem);
   if (rc) return rc;

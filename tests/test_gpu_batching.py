@@ -178,3 +178,17 @@ def test_autotune_picks_a_launch_shape():
         assert tw == w and tc in (3, 5, 7) and kc in (0, 512, 1024, 2048)
     finally:
         mp.mpdiv_destroy(c)
+
+
+@pytest.mark.parametrize("warps", [3, 6, 12, 40])
+def test_configured_block_size_rounds_to_a_built_kernel(warps):
+    # the kernels are built for 1, 2, 4, 8, 16 and 32 warps; another configured
+    # block size runs the next one up (32 at most), with the same digits
+    import paper_2606_06386_gb300 as mp
+
+    U = I.uniform_batch(8, 700, seed=60, stream=warps)
+    V = I.uniform_batch(8, 300, seed=61, stream=warps)
+    Q, R, S, _ = run_uniform(U, V, warps=warps)
+    Qo, Ro, So = oracle_uniform(U, V)
+    assert_same(Q, R, S, Qo, Ro, So)
+    assert mp.mpdiv_tuning(ctx(warps=warps), 700)[0] == min(32, 1 << (warps - 1).bit_length())
