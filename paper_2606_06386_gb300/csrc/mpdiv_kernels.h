@@ -12,5 +12,7 @@ void* mp_kernel_w8(int kind);  // also the self-splitting persistent kernel (8 -
 void* mp_kernel_w16(int kind);  // also the self-splitting persistent kernel (16 -> 8 -> 4 warps),
                                 // the one-block-per-item queue kernel and the shifted-inverse test entry
 void* mp_kernel_w32(int kind);
-void* mp_kernel_persistent(int warps);  // mpdiv_p.cu: 8 (warps <= 8) or 16 warps per block
+void* mp_kernel_persistent(int warps);  // 8 (warps <= 8) or 16 warps per block
+void* mp_kernel_persistent8();          // mpdiv_p.cu
+void* mp_kernel_persistent16();         // mpdiv_p16.cu
 void* mp_kernel_w16_queue(int kind);    // mpdiv_q.cu: MP_K_RAGGED and MP_K_SHINV
