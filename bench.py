@@ -44,6 +44,12 @@ UNIT = "div/s"
 SM_COUNT_GB300 = 152
 PRODUCTS_PER_CLK_SM = 32  # 64 32-bit IMAD results/clk/SM, two (lo, hi) per 32x32->64 digit product
 SM_MAX_MHZ = 2070.0
+# DRAM bytes per 2^18-bit division of k_div_uniform, from one ncu capture of
+# that kernel (dram__bytes_read.sum + dram__bytes_write.sum = 15,100,928 + 0
+# bytes over a 304-division launch, 8 warps, 5 columns per lane): the operands
+# read once, the results held in L2; the roofline's traffic is this times the
+# launch's divisions
+DRAM_BYTES_PER_DIV_2E18 = 15100928 / 304
 
 
 def _peaks():
@@ -324,7 +330,8 @@ def run_sweep(args, dev, dist, rank, ws):
                      "kernel": f"k_div_uniform, 2^{(32 * sizes[big]['n']).bit_length() - 1}-bit launch "
                                f"({sizes[big]['b']} divisions)",
                      "achieved": achieved, "peak": peak, "unit": "Tprod/s", "frac": achieved / peak,
-                     "traffic": None,
+                     "traffic": (DRAM_BYTES_PER_DIV_2E18 * sizes[big]["b"] if sizes[big]["n"] == 8192 else None),
+                     "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled from a 304-division launch)",
                      "peak_basis": "derived: 152 SMs x 32 digit products/clk/SM (64 IMAD/clk/SM, lo+hi per "
                                    "32x32->64 product) x 2070 MHz max SM clock",
                      "work_basis": "algorithmic 32x32-bit digit products of Algorithms 1-3 at operand precision, "
