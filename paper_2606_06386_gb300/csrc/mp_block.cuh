@@ -649,9 +649,17 @@ __device__ inline int mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int 
   }
   b.sync();
   constexpr bool kWhole = !MP_NAMED_GROUPS;
-  if (b.tcols == 3)
+  // in groups of several warps, a product with fewer strips than the group
+  // has warps at the launch's strip width runs with the narrowest strips
+  // (more strips to share out; its pads, sized for the launch's width, cover
+  // the narrower reach). The one- and two-warp kernels keep the launch's width.
+  int tc = b.tcols;
+#if !MP_MUL_NOINLINE
+  if (tc != 3 && npos - plo < 32 * (tc == 7 ? 7 : 5) * b.nw) tc = 3;
+#endif
+  if (tc == 3)
     mul_t<3, kWhole>(b, C, npos, A, na, Bv, nb, OV, plo, compact);
-  else if (b.tcols == 7)
+  else if (tc == 7)
     mul_t<7, kWhole>(b, C, npos, A, na, Bv, nb, OV, plo, compact);
   else
     mul_t<5, kWhole>(b, C, npos, A, na, Bv, nb, OV, plo, compact);
