@@ -77,8 +77,6 @@ __device__ __forceinline__ Blk make_group(int* red, int w0, int nw, int bar) {
   return b;
 }
 
-__device__ __forceinline__ Blk make_blk(int* red) { return make_group(red, 0, blockDim.x >> 5, 0); }
-
 // The whole block of a kernel built for NW warps: with the group size a
 // compile-time constant, one-warp groups skip their cross-warp summaries.
 template <int NW>

@@ -34,7 +34,8 @@ enum KernKind {
 
 // Instantiations by block size (mpdiv_k*.cu); the minimum-blocks bound caps
 // registers at 64 per thread so that several blocks of the smaller size
-// classes share an SM. The persistent kernel always runs 16-warp blocks.
+// classes share an SM. The persistent kernel runs 8- or 16-warp blocks, the
+// queue and test kernels 16-warp blocks.
 void* kernel_for(KernKind kk, int warps) {
   if (kk == KK_PERSIST) return warps <= 8 ? mp_kernel_w8(MP_K_PERSIST) : mp_kernel_w16(MP_K_PERSIST);
   if (kk == KK_RAGGED || kk == KK_SHINV) return mp_kernel_w16(kk);  // 16-warp blocks only
