@@ -246,6 +246,7 @@ extern "C" int mpdiv_batch(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* u, i
                            const uint32_t* v, int32_t v_limbs, int64_t v_stride, uint32_t* q, int32_t q_limbs,
                            int64_t q_stride, uint32_t* r, int32_t r_limbs, int64_t r_stride, int32_t* status,
                            int32_t* iters, int64_t* products, void* stream) {
+  MpdivRange nvtx_range("mpdiv.batch");
   if (!ctx) return MPDIV_EINVAL;
   if (n_items < 0) return mpdiv_set_error(ctx, MPDIV_EINVAL, "n_items < 0");
   if (n_items == 0) return MPDIV_OK;
@@ -461,6 +462,7 @@ extern "C" int mpdiv_batch_ragged(mpdiv_ctx* ctx, int64_t n_items, const uint32_
                                   uint32_t* r, const int64_t* r_off, const int32_t* r_len, int32_t* status,
                                   int32_t* iters, int64_t* products, const int32_t* u_len_host,
                                   const int32_t* v_len_host, void* stream) {
+  MpdivRange nvtx_range("mpdiv.batch_ragged");
   if (!ctx) return MPDIV_EINVAL;
   if (n_items < 0) return mpdiv_set_error(ctx, MPDIV_EINVAL, "n_items < 0");
   if (n_items == 0) return MPDIV_OK;
@@ -555,6 +557,7 @@ extern "C" int mpdiv_tuning(mpdiv_ctx* ctx, int32_t u_limbs, int32_t* warps, int
 // ------------------------------------------------------------------ multiplication (cost unit)
 extern "C" int mpdiv_mul_batch(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* u, const uint32_t* v, int32_t n_limbs,
                                int64_t stride, uint32_t* out, int64_t out_stride, void* stream) {
+  MpdivRange nvtx_range("mpdiv.mul_batch");
   if (!ctx) return MPDIV_EINVAL;
   if (n_items < 0) return mpdiv_set_error(ctx, MPDIV_EINVAL, "n_items < 0");
   if (n_items == 0) return MPDIV_OK;

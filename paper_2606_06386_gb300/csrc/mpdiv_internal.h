@@ -9,6 +9,7 @@
 #include <tuple>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "mp_args.h"
 #include "mpdiv.h"
@@ -100,3 +101,12 @@ int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t st
 int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stream);
 void mpdiv_tune_load(mpdiv_ctx* ctx, const char* path);
 void mpdiv_serve_shutdown(mpdiv_ctx* ctx);
+
+// A named NVTX range over a scope (batch, queue, tuning and serving phases);
+// free unless a profiler is attached.
+struct MpdivRange {
+  explicit MpdivRange(const char* name) { nvtxRangePushA(name); }
+  ~MpdivRange() { nvtxRangePop(); }
+  MpdivRange(const MpdivRange&) = delete;
+  MpdivRange& operator=(const MpdivRange&) = delete;
+};

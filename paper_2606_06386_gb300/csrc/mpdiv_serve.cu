@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "mpdiv_internal.h"
+#include "serve_ring.h"
 
 namespace {
 
@@ -57,56 +58,13 @@ struct Request {
   int64_t t_submit = 0, t_done = 0;
 };
 
-// Ring allocator in digits with first-in first-out release; an allocation
-// that would cross the end starts again at 0 and the skipped tail counts as
-// used until it is released with its allocation.
-struct Ring {
-  int64_t cap = 0, tail = 0, used = 0;
-  struct Entry {
-    int64_t len;  // includes any skipped gap before the allocation
-    bool done;
-  };
-  std::deque<Entry> live;
-  int64_t front_seq = 0;  // sequence number of live.front()
-  // returns the offset (or -1) and the allocation's sequence number in *seq
-  int64_t alloc(int64_t n, int64_t* seq) {
-    n = (n + 3) & ~int64_t(3);
-    if (n > cap) return -1;
-    int64_t off = tail, gap = 0;
-    if (off + n > cap) {
-      gap = cap - off;
-      off = 0;
-    }
-    if (used + gap + n > cap) return -1;
-    tail = off + n;
-    if (tail == cap) tail = 0;
-    used += gap + n;
-    *seq = front_seq + (int64_t)live.size();
-    live.push_back({gap + n, false});
-    return off;
-  }
-  // mark allocation `seq` finished, then free finished ones from the front
-  void release(int64_t seq) {
-    live[(size_t)(seq - front_seq)].done = true;
-    while (!live.empty() && live.front().done) {
-      used -= live.front().len;
-      live.pop_front();
-      front_seq++;
-    }
-    if (live.empty()) {
-      tail = 0;
-      used = 0;
-    }
-  }
-};
-
 }  // namespace
 
 struct MpServer {
   mpdiv_ctx* ctx = nullptr;
   mpdiv_serve_config cfg{};
   uint32_t *d_in = nullptr, *h_in = nullptr, *d_out = nullptr, *h_out = nullptr;
-  Ring in_ring, out_ring;
+  mp_serve::Ring in_ring, out_ring;
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
   std::deque<Request*> queue;
@@ -140,6 +98,7 @@ struct MpServer {
 static int64_t meta_words_for(int64_t n) { return 8 * n + 5 * n + 8 + n + 8; }
 
 bool MpServer::launch(Slot& s) {
+  MpdivRange nvtx_range("mpdiv.serve.batch");
   const int64_t n = (int64_t)s.reqs.size();
   uint32_t* H = s.h_meta;
   int64_t* h_off = reinterpret_cast<int64_t*>(H);

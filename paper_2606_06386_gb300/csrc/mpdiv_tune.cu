@@ -53,6 +53,7 @@ static void tune_save(mpdiv_ctx* ctx, const char* path) {
 }
 
 extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, int32_t n_items) {
+  MpdivRange nvtx_range("mpdiv.autotune");
   if (!ctx) return MPDIV_EINVAL;
   if (u_limbs < 1 || v_limbs < 1 || v_limbs > u_limbs || n_items < 1)
     return mpdiv_set_error(ctx, MPDIV_EINVAL, "autotune: bad shape");
