@@ -140,6 +140,27 @@ int mpdiv_debug_shinv(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *v, int32_
                       const int32_t *h_digits, uint32_t *out, int32_t out_limbs, int64_t out_stride,
                       int32_t *iters, int32_t *status, void *stream);
 
+/* Test entry: one block-group primitive of the division path per item, on
+ * item i's x (x + i*nx, nx digits) and y (y + i*ny, ny digits), with the
+ * result digits at out + i*cap (cap >= 1; 3 for op 7) and an int32 at result[i]:
+ *   op 0: out = (x + y) mod B^cap, result = carry out of digit cap-1
+ *   op 1: out = (x - y) mod B^cap, result = borrow out
+ *   op 2: result = -1, 0, 1 as x <, ==, > y
+ *   op 3: result = prec(x), the significant digits of x
+ *   op 4: out = x - B^arg (cap digits), result = 0 if x < B^arg (then out is x)
+ *   op 5: out = x + B^arg mod B^cap, result = 0 on a carry out of cap
+ *   op 6: out[arg..cap) = digits arg.. of the sum of the digit products
+ *         x_i y_j B^(i+j) with i + j >= arg, mod B^cap (the clipped product;
+ *         arg = 0: x y mod B^cap); out below arg is zero; result = arg
+ *   op 7: out[0..3) = lowest nonzero digit, highest nonzero digit, highest
+ *         digit that is not all ones of x (-1 where there is none)
+ *   op 8: out = B^cap - x (x nonzero below cap)
+ * with `warps` warps per block (rounded up to 1, 2, 4, 8, 16 or 32) and the
+ * context's strip width (3 if unset). Device pointers; asynchronous. */
+int mpdiv_debug_primitive(mpdiv_ctx *ctx, int32_t op, int64_t n_items, const uint32_t *x, int32_t nx,
+                          const uint32_t *y, int32_t ny, int32_t arg, uint32_t *out, int32_t cap, int32_t *result,
+                          int32_t warps, void *stream);
+
 /* Tuning: time the plain kernel for the given (u_limbs, v_limbs) shape at each
  * candidate block size (1 and 2 warps for u_limbs <= 1024, then 4, 8, 16 and
  * 32 warps) and strip width (3, 5, 7 columns

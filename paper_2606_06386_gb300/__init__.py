@@ -22,7 +22,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 SO_PATH = os.path.join(_BUILD, "libmpdiv.so")
 HEADER = os.path.join(_ROOT, "include", "mpdiv.h")
-SOURCES = ["mpdiv_p.cu", "mpdiv_p16.cu", "mpdiv_q.cu", "mpdiv_k1.cu", "mpdiv_k2.cu", "mpdiv_k4.cu", "mpdiv_k8.cu", "mpdiv_k16.cu",
+SOURCES = ["mpdiv_p.cu", "mpdiv_p16.cu", "mpdiv_q.cu", "mpdiv_t.cu", "mpdiv_k1.cu", "mpdiv_k2.cu", "mpdiv_k4.cu", "mpdiv_k8.cu", "mpdiv_k16.cu",
            "mpdiv_k32.cu", "mpdiv_noalloc.cu", "mpdiv.cu", "mpdiv_tune.cu", "mpdiv_serve.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -103,6 +103,7 @@ _SIGS = {
     "mpdiv_batch_ragged": (ctypes.c_int, [_P, _I64] + [_P] * 18),
     "mpdiv_debug_shinv": (ctypes.c_int, [_P, _I64, _P, _I32, _I64, _P, _P, _I32, _I64, _P, _P, _P]),
     "mpdiv_autotune": (ctypes.c_int, [_P, _I32, _I32, _I32]),
+    "mpdiv_debug_primitive": (ctypes.c_int, [_P, _I32, _I64, _P, _I32, _P, _I32, _I32, _P, _I32, _P, _I32, _P]),
     "mpdiv_mul_batch": (ctypes.c_int, [_P, _I64, _P, _P, _I32, _I64, _P, _I64, _P]),
     "mpdiv_tuning": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "mpdiv_serve_start": (ctypes.c_int, [_P, ctypes.POINTER(mpdiv_serve_config)]),
@@ -251,6 +252,17 @@ def mpdiv_debug_shinv(ctx, v, h_digits, out, iters, status, stream=None) -> None
             _ptr(iters), _ptr(status), _stream(stream),
         ),
     )
+
+
+def mpdiv_debug_primitive(ctx, op: int, x, y, arg: int, out, result, warps: int, stream=None) -> None:
+    """Test entry: one group primitive per row of the contiguous (items, nx) and
+    (items, ny) CUDA tensors x, y into out (items, cap) and result (items,)."""
+    _check_dev(x, y, out, result)
+    for t in (x, y, out):
+        if not t.is_contiguous():
+            raise ValueError("contiguous tensors expected")
+    _check(ctx, lib().mpdiv_debug_primitive(ctx, op, x.shape[0], _ptr(x), x.shape[1], _ptr(y), y.shape[1], arg,
+                                            _ptr(out), out.shape[1], _ptr(result), warps, _stream(stream)))
 
 
 def mpdiv_mul_batch(ctx, u, v, out, stream=None) -> None:

@@ -70,4 +70,17 @@ struct ShinvArgs {
   int flags;  // MPDIV_FLAG_FULL_PRODUCTS is honoured; the others are ignored
 };
 
+// Test entry: one group primitive per item (mpdiv_debug_primitive).
+struct PrimArgs {
+  const uint32_t* x;
+  const uint32_t* y;
+  uint32_t* out;
+  int32_t* result;
+  int64_t n;
+  int nx, ny, cap;
+  int op, arg;
+  int tcols;
+  int smem_words;
+};
+
 }  // namespace mp

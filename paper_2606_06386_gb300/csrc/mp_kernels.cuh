@@ -179,6 +179,61 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_mul_low(UniformArgs a) {
   }
 }
 
+// Test entry: one group primitive per item on operands in shared memory
+// (x of nx digits, y of ny digits, result digits C of cap digits), the ops of
+// mpdiv_debug_primitive.
+template <int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_prim(PrimArgs a) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ int red[RED_WORDS];
+  Blk b = make_block<NW>(red);
+  b.tcols = a.tcols;
+  uint32_t* X = sm + PAD;
+  uint32_t* Y = X + a.nx + PAD;
+  uint32_t* C = Y + a.ny + PAD;
+  uint32_t* OV = C + a.cap + 4;
+  for (int64_t item = blockIdx.x; item < a.n; item += gridDim.x) {
+    for (int i = b.tid; i < a.smem_words; i += b.nt) sm[i] = 0u;
+    b.sync();
+    load_global(b, X, a.nx, [&](int i) { return a.x[item * a.nx + i]; });
+    load_global(b, Y, a.ny, [&](int i) { return a.y[item * a.ny + i]; });
+    auto xd = [&](int i) -> uint32_t { return i < a.nx ? X[i] : 0u; };
+    auto yd = [&](int i) -> uint32_t { return i < a.ny ? Y[i] : 0u; };
+    int res = 0;
+    switch (a.op) {
+      case 0: res = (int)addsub<false>(b, C, a.cap, xd, yd, 0u); break;
+      case 1: res = (int)addsub<true>(b, C, a.cap, xd, yd, 0u); break;
+      case 2: res = cmp(b, X, a.nx, Y, a.ny); break;
+      case 3: res = prec(b, X, a.nx); break;
+      case 4:
+        copy(b, C, a.cap, xd);
+        res = sub_pow(b, C, a.arg, a.cap) ? 1 : 0;
+        break;
+      case 5:
+        copy(b, C, a.cap, xd);
+        res = add_pow(b, C, a.arg, a.cap) ? 1 : 0;
+        break;
+      case 6: res = mul(b, C, a.cap, X, a.nx, Y, a.ny, OV, a.arg); break;
+      case 7: {
+        int z, t1, t2;
+        scan3(b, X, a.nx, &z, &t1, &t2);
+        if (b.tid == 0) {
+          C[0] = (uint32_t)z;
+          C[1] = (uint32_t)t1;
+          C[2] = (uint32_t)t2;
+        }
+        b.sync();
+        break;
+      }
+      case 8: negate(b, C, a.cap, X, a.nx); break;
+      default: res = -1;
+    }
+    for (int i = b.tid; i < a.cap; i += b.nt) a.out[item * a.cap + i] = C[i];
+    if (b.tid == 0) a.result[item] = res;
+    b.sync();
+  }
+}
+
 // Test entry: shinv_h(v) as the division path computes it.
 template <int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_shinv(ShinvArgs a) {

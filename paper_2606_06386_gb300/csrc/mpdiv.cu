@@ -545,6 +545,46 @@ extern "C" int mpdiv_debug_shinv(mpdiv_ctx* ctx, int64_t n_items, const uint32_t
                           "launch of the shifted-inverse kernel");
 }
 
+extern "C" int mpdiv_debug_primitive(mpdiv_ctx* ctx, int32_t op, int64_t n_items, const uint32_t* x, int32_t nx,
+                                     const uint32_t* y, int32_t ny, int32_t arg, uint32_t* out, int32_t cap,
+                                     int32_t* result, int32_t warps, void* stream) {
+  if (!ctx) return MPDIV_EINVAL;
+  if (n_items <= 0) return n_items == 0 ? MPDIV_OK : mpdiv_set_error(ctx, MPDIV_EINVAL, "n_items < 0");
+  if (!x || !y || !out || !result) return mpdiv_set_error(ctx, MPDIV_EINVAL, "null pointer argument");
+  if (op < 0 || op > 8) return mpdiv_set_error(ctx, MPDIV_EINVAL, "unknown primitive %d", op);
+  if (nx < 1 || ny < 1 || cap < 1 || arg < 0 || (op == 7 && cap < 3))
+    return mpdiv_set_error(ctx, MPDIV_EINVAL, "bad sizes");
+  if ((op == 0 || op == 1 || op == 8) && cap < std::max(nx, ny))
+    return mpdiv_set_error(ctx, MPDIV_EINVAL, "cap shorter than the operands");
+  if ((op == 4 || op == 5) && (cap < nx || arg >= cap)) return mpdiv_set_error(ctx, MPDIV_EINVAL, "bad power");
+  cudaSetDevice(ctx->device);
+  const int w = kernel_warps(warps < 1 ? 1 : warps);
+  const int words = 3 * PAD + nx + ny + cap + 4 + ov_words(cap);
+  const int smem = (words * 4 + 15) & ~15;
+  if (smem > ctx->max_smem) return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory", smem);
+  void* k = mp_kernel_prim(w);
+  int rc = prepare_kernel(ctx, k, smem);
+  if (rc) return rc;
+  PrimArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.x = x;
+  a.y = y;
+  a.out = out;
+  a.result = result;
+  a.n = n_items;
+  a.nx = nx;
+  a.ny = ny;
+  a.cap = cap;
+  a.op = op;
+  a.arg = arg;
+  a.tcols = ctx->cfg.mul_columns > 0 ? ctx->cfg.mul_columns : 3;
+  a.smem_words = smem / 4;
+  void* args[] = {&a};
+  const int64_t grid = std::min<int64_t>(n_items, 0x7fffffff);
+  return mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * w), args, smem, (cudaStream_t)stream),
+                          "launch of the primitive test kernel");
+}
+
 extern "C" int mpdiv_tuning(mpdiv_ctx* ctx, int32_t u_limbs, int32_t* warps, int32_t* mul_columns,
                             int32_t* karatsuba_cutoff) {
   if (!ctx || u_limbs < 1) return MPDIV_EINVAL;

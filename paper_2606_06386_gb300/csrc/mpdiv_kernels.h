@@ -16,3 +16,4 @@ void* mp_kernel_persistent(int warps);  // 8 (warps <= 8) or 16 warps per block
 void* mp_kernel_persistent8();          // mpdiv_p.cu
 void* mp_kernel_persistent16();         // mpdiv_p16.cu
 void* mp_kernel_w16_queue(int kind);    // mpdiv_q.cu: MP_K_RAGGED and MP_K_SHINV
+void* mp_kernel_prim(int warps);        // mpdiv_t.cu: the primitive test kernel (1, 2, 4, 8, 16, 32 warps)
