@@ -78,3 +78,106 @@ def test_replay_of_a_poisson_stream():
     assert (st == 0).all() and (lat > 0).all()
     qo, ro, so, _ = oracle.divmod_ragged_u32(u_flat, u_off, u_len, v_flat, v_off, v_len, q_off, q_len, r_off, r_len)
     assert (q == qo).all() and (r == ro).all()
+
+
+def _submit_retry(mp, c, u, v, tries=20000):
+    import time
+
+    for _ in range(tries):
+        try:
+            return mp.mpdiv_serve_submit(c, u, v)
+        except mp.MpdivError as e:
+            if e.code != mp.MPDIV_EBUSY:
+                raise
+            time.sleep(0.0005)
+    raise AssertionError("the server never admitted the request")
+
+
+def _wait_completed(mp, c, n, seconds=30.0):
+    import time
+
+    t0 = time.time()
+    while mp.mpdiv_serve_stats(c)[0] < n:
+        assert time.time() - t0 < seconds, "requests did not complete"
+        time.sleep(0.001)
+
+
+def test_ticket_table_and_admission_limits():
+    # a finished ticket is collected once; at most 1024 finished tickets (here,
+    # with max_pending 4) wait unpolled, after which submit is refused until
+    # the oldest of them is collected; stop keeps results pollable, refuses
+    # new work, and a stopped server can be started again
+    import paper_2606_06386_gb300 as mp
+
+    u = np.array([7, 1], np.uint32)  # 2^32 + 7
+    v = np.array([3], np.uint32)
+    q_want, r_want = divmod((1 << 32) + 7, 3)
+    c = mp.mpdiv_init(0)
+    try:
+        mp.mpdiv_serve_start(c, pool_digits=1 << 20, max_batch=64, max_inflight=4, max_pending=4)
+        t = _submit_retry(mp, c, u, v)
+        rc, q, r, st = mp.mpdiv_serve_poll(c, t, 2, 1, timeout_us=30_000_000)
+        assert rc == mp.MPDIV_OK and st == 0 and oracle.to_int(q) == q_want and r[0] == r_want
+        with pytest.raises(mp.MpdivError) as e:
+            mp.mpdiv_serve_poll(c, t, 2, 1)
+        assert e.value.code == mp.MPDIV_EINVAL
+        tickets = [_submit_retry(mp, c, u, v) for _ in range(1024)]
+        _wait_completed(mp, c, 1 + 1024)
+        with pytest.raises(mp.MpdivError) as e:
+            mp.mpdiv_serve_submit(c, u, v)  # its slot still holds an unpolled result
+        assert e.value.code == mp.MPDIV_EBUSY
+        rc, q, r, st = mp.mpdiv_serve_poll(c, tickets[0], 2, 1)
+        assert rc == mp.MPDIV_OK and oracle.to_int(q) == q_want
+        tickets.append(mp.mpdiv_serve_submit(c, u, v))
+        mp.mpdiv_serve_stop(c)
+        with pytest.raises(mp.MpdivError) as e:
+            mp.mpdiv_serve_submit(c, u, v)
+        assert e.value.code == mp.MPDIV_ESTATE
+        for tk in tickets[1:]:
+            rc, q, r, st = mp.mpdiv_serve_poll(c, tk, 2, 1, timeout_us=30_000_000)
+            assert rc == mp.MPDIV_OK and st == 0 and oracle.to_int(q) == q_want and r[0] == r_want
+        mp.mpdiv_serve_start(c, pool_digits=1 << 20)
+        t = _submit_retry(mp, c, u, v)
+        rc, q, r, st = mp.mpdiv_serve_poll(c, t, 2, 1, timeout_us=30_000_000)
+        assert rc == mp.MPDIV_OK and oracle.to_int(q) == q_want
+        mp.mpdiv_serve_stop(c)
+    finally:
+        mp.mpdiv_destroy(c)
+
+
+def test_concurrent_polls_of_one_ticket():
+    # pollers race for a finished ticket without the server lock: exactly one
+    # collects it, the others find it gone
+    import threading
+
+    import paper_2606_06386_gb300 as mp
+
+    items = _mix(16, seed=I.SEED_BASE + 32)
+    c = mp.mpdiv_init(0)
+    try:
+        mp.mpdiv_serve_start(c, pool_digits=1 << 22)
+        for u, v in items:
+            n0 = mp.mpdiv_serve_stats(c)[0]
+            t = _submit_retry(mp, c, u, v)
+            _wait_completed(mp, c, n0 + 1)
+            got, gone = [], []
+
+            def poll():
+                try:
+                    rc, q, r, st = mp.mpdiv_serve_poll(c, t, len(u), len(v))
+                    if rc == mp.MPDIV_OK:
+                        got.append((q, r, st))
+                except mp.MpdivError as e:
+                    gone.append(e.code)
+
+            ths = [threading.Thread(target=poll) for _ in range(8)]
+            for th in ths:
+                th.start()
+            for th in ths:
+                th.join()
+            assert len(got) == 1 and len(gone) == 7 and set(gone) == {mp.MPDIV_EINVAL}
+            qo, ro, _ = oracle.divmod_u32(u, v, len(u), len(v))
+            assert (got[0][0] == qo).all() and (got[0][1] == ro).all() and got[0][2] == 0
+        mp.mpdiv_serve_stop(c)
+    finally:
+        mp.mpdiv_destroy(c)
