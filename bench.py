@@ -29,6 +29,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -104,7 +105,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples go to $MPDIV_CLOCKS_DIR (default: the temporary directory)
+        out_dir = os.environ.get("MPDIV_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"mpdiv_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
