@@ -42,6 +42,10 @@ from paper_2606_06386_gb300 import inputs as I  # noqa: E402
 SWEEP = I.SWEEP  # (u digits, v digits, batch)
 METRIC = "divisions/sec at 2^15-2^18 bits, batched vs plain launch; p99 latency; % IMAD peak"
 UNIT = "div/s"
+# mpdiv_config.flags per product mode: clipped (Section 5's clipped products,
+# the default), the paper's full products, full products by the
+# number-theoretic transform where it fits (MPDIV_FLAG_NTT_PRODUCTS)
+PRODUCT_FLAGS = {"clipped": 0, "full": 2, "ntt": 6}
 SM_COUNT_GB300 = 152
 PRODUCTS_PER_CLK_SM = 32  # 64 32-bit IMAD results/clk/SM, two (lo, hi) per 32x32->64 digit product
 SM_MAX_MHZ = 2070.0
@@ -183,7 +187,7 @@ def run_sweep(args, dev, dist, rank, ws):
     import paper_2606_06386_gb300 as mp
 
     mp.build()
-    ctx = mp.mpdiv_init(dev.index or 0)
+    ctx = mp.mpdiv_init(dev.index or 0, flags=PRODUCT_FLAGS[args.products])
     host = [I.sweep(n, kl, b) for n, kl, b in SWEEP]
     sizes = []
     for (n, kl, b), (U, V) in zip(SWEEP, host):
@@ -327,13 +331,15 @@ def run_sweep(args, dev, dist, rank, ws):
         "config": {"workload": "plain per-size sweep: 2^15/2^16/2^17/2^18-bit dividends by half-length divisors, "
                                "batches 8192/4096/2048/1024, one plain launch per size (15360 divisions per step)",
                    "l2": "no flush: each step reads ~200 MB of operands (> 129 MB L2) before any reuse",
+                   "products": args.products,
                    "parallelism": f"replicas x{ws}"},
         "per_size": per_size,
         "roofline": {"bound": "alu",
                      "kernel": f"k_div_uniform, 2^{(32 * sizes[big]['n']).bit_length() - 1}-bit launch "
                                f"({sizes[big]['b']} divisions)",
                      "achieved": achieved, "peak": peak, "unit": "Tprod/s", "frac": achieved / peak,
-                     "traffic": (DRAM_BYTES_PER_DIV_2E18 * sizes[big]["b"] if sizes[big]["n"] == 8192 else None),
+                     "traffic": (DRAM_BYTES_PER_DIV_2E18 * sizes[big]["b"]
+                                 if sizes[big]["n"] == 8192 and args.products == "clipped" else None),
                      "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled from a 304-division launch)",
                      "peak_basis": "derived: 152 SMs x 32 digit products/clk/SM (64 IMAD/clk/SM, lo+hi per "
                                    "32x32->64 product) x 2070 MHz max SM clock",
@@ -701,6 +707,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep", choices=["sweep", "mixed", "serve", "stress", "paper"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--products", default="clipped", choices=sorted(PRODUCT_FLAGS),
+                    help="sweep workload: clipped products (default), the paper's full products, or full "
+                    "products by the number-theoretic transform where it fits")
     ap.add_argument("--requests", type=int, default=200000, help="serve workload: number of requests")
     ap.add_argument("--max-batch", type=int, default=1024, help="serve workload: most requests per batch")
     ap.add_argument("--max-inflight", type=int, default=32, help="serve workload: batches in flight")

@@ -67,6 +67,13 @@ extern "C" {
                                       the remainder from v*q mod B^(prec(v)+1); same q and r,
                                       fewer products; the shifted inverse itself can then differ
                                       from Algorithm 1's by one unit) */
+#define MPDIV_FLAG_NTT_PRODUCTS 4  /* full products (implies MPDIV_FLAG_FULL_PRODUCTS) by a
+                                      number-theoretic transform over three primes where the
+                                      block's spare shared memory holds it (transforms of up to
+                                      8192 points, four words per point), the strip product
+                                      elsewhere: the FFT multiplication the paper names for larger
+                                      sizes (Section 6); same digits, fewer instructions for
+                                      long operands */
 
 typedef struct mpdiv_ctx mpdiv_ctx; /* opaque; owned by the library */
 
@@ -80,6 +87,8 @@ typedef struct mpdiv_config {
                            MPDIV_FLAG_FULL_PRODUCTS) whose shorter operand has at least this
                            many digits (> 0); -1: never; 0: per size class from the tuning
                            table (never if untuned) */
+  int transform_cutoff; /* with MPDIV_FLAG_NTT_PRODUCTS: products whose operands have at least
+                           this many digits together use the transform (0: 1024) */
 } mpdiv_config;
 
 /* Create a context on CUDA device `device` (cfg may be NULL for defaults).
@@ -155,6 +164,10 @@ int mpdiv_debug_shinv(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *v, int32_
  *   op 7: out[0..3) = lowest nonzero digit, highest nonzero digit, highest
  *         digit that is not all ones of x (-1 where there is none)
  *   op 8: out = B^cap - x (x nonzero below cap)
+ *   op 9: out[arg..cap) = digits arg.. of x y mod B^cap by the number-theoretic
+ *         transform (MPDIV_FLAG_NTT_PRODUCTS), exact (the carries of the
+ *         digits below arg included); out below arg is zero; result = arg;
+ *         nx + ny <= 8192 (else MPDIV_EUNSUPPORTED)
  * with `warps` warps per block (rounded up to 1, 2, 4, 8, 16 or 32) and the
  * context's strip width (3 if unset). Device pointers; asynchronous. */
 int mpdiv_debug_primitive(mpdiv_ctx *ctx, int32_t op, int64_t n_items, const uint32_t *x, int32_t nx,
@@ -180,9 +193,11 @@ int mpdiv_tuning(mpdiv_ctx *ctx, int32_t u_limbs, int32_t *warps, int32_t *mul_c
 /* The cost unit of the paper's multiplication count (Section 2.3, Fig. 3 and
  * Table 1's "Our Mul"): out + i*out_stride gets (u_i * v_i) mod B^n, the
  * product of two n-digit numbers kept to n digits (the digit pairs below n),
- * one thread block per item, with the division path's strip multiply. u_i,
- * v_i at u + i*stride, v + i*stride; all device pointers. Asynchronous on
- * stream. n_limbs <= 2 * MPDIV_MAX_LIMBS. */
+ * one thread block per item, with the division path's strip multiply (with
+ * MPDIV_FLAG_NTT_PRODUCTS, by the number-theoretic transform when 2 n_limbs is
+ * at most 8192 and at least the transform cutoff). u_i, v_i at u + i*stride,
+ * v + i*stride; all device pointers. Asynchronous on stream.
+ * n_limbs <= 2 * MPDIV_MAX_LIMBS. */
 int mpdiv_mul_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, const uint32_t *v, int32_t n_limbs,
                     int64_t stride, uint32_t *out, int64_t out_stride, void *stream);
 

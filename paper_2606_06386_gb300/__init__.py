@@ -23,7 +23,8 @@ _BUILD = os.path.join(_HERE, "_build")
 SO_PATH = os.path.join(_BUILD, "libmpdiv.so")
 HEADER = os.path.join(_ROOT, "include", "mpdiv.h")
 SOURCES = ["mpdiv_p.cu", "mpdiv_p16.cu", "mpdiv_q.cu", "mpdiv_t.cu", "mpdiv_k1.cu", "mpdiv_k2.cu", "mpdiv_k4.cu", "mpdiv_k8.cu", "mpdiv_k16.cu",
-           "mpdiv_k32.cu", "mpdiv_noalloc.cu", "mpdiv.cu", "mpdiv_tune.cu", "mpdiv_serve.cu"]
+           "mpdiv_k32.cu", "mpdiv_n.cu", "mpdiv_n8.cu", "mpdiv_n16.cu",
+           "mpdiv_n2.cu", "mpdiv_n3.cu", "mpdiv_noalloc.cu", "mpdiv.cu", "mpdiv_tune.cu", "mpdiv_serve.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 # return codes and statuses (include/mpdiv.h)
@@ -34,6 +35,7 @@ MPDIV_ST_OK, MPDIV_ST_DIV_BY_ZERO, MPDIV_ST_CORRECTION_OVERFLOW = 0, 1, 2
 MPDIV_ST_Q_OVERFLOW, MPDIV_ST_INTERNAL = 3, 4
 MPDIV_FLAG_INJECT_LAMBDA = 1
 MPDIV_FLAG_FULL_PRODUCTS = 2
+MPDIV_FLAG_NTT_PRODUCTS = 4
 MPDIV_MAX_LIMBS = 16384
 MPDIV_NOALLOC_MAX_ITEMS = 65536
 
@@ -79,7 +81,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 class mpdiv_config(ctypes.Structure):
     _fields_ = [("warps_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("flags", ctypes.c_int),
-                ("mul_columns", ctypes.c_int), ("karatsuba_cutoff", ctypes.c_int)]
+                ("mul_columns", ctypes.c_int), ("karatsuba_cutoff", ctypes.c_int),
+                ("transform_cutoff", ctypes.c_int)]
 
 
 class mpdiv_serve_config(ctypes.Structure):
@@ -175,8 +178,8 @@ def _check_dev(*ts):
 
 # ---------------------------------------------------------------- context
 def mpdiv_init(device: int = 0, warps_per_block: int = 0, blocks_per_sm: int = 0, flags: int = 0,
-               mul_columns: int = 0, karatsuba_cutoff: int = 0):
-    cfg = mpdiv_config(warps_per_block, blocks_per_sm, flags, mul_columns, karatsuba_cutoff)
+               mul_columns: int = 0, karatsuba_cutoff: int = 0, transform_cutoff: int = 0):
+    cfg = mpdiv_config(warps_per_block, blocks_per_sm, flags, mul_columns, karatsuba_cutoff, transform_cutoff)
     h = _P()
     _check(None, lib().mpdiv_init(ctypes.byref(h), device, ctypes.byref(cfg)))
     return h

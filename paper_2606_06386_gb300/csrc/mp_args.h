@@ -18,6 +18,8 @@ struct UniformArgs {
   int flags;
   int tcols;  // columns per lane of the strip multiply
   int kcut;   // Karatsuba cutoff for full products (0: schoolbook only)
+  const uint32_t* ntt;  // transform tables for full products (null: strip products only)
+  int ntt_cut;          // the transform for products of at least this many digits
 };
 
 struct RaggedArgs {
@@ -49,6 +51,8 @@ struct RaggedArgs {
   int kcut;  // Karatsuba cutoff for full products (0: schoolbook only)
   int kcut_class[5];
   int want_class[5];
+  const uint32_t* ntt;  // transform tables for full products (null: strip products only)
+  int ntt_cut;
 };
 
 // Size class of a dividend of ul digits in the persistent kernel's tables.
@@ -68,6 +72,8 @@ struct ShinvArgs {
   int tcols;
   int kcut;
   int flags;  // MPDIV_FLAG_FULL_PRODUCTS is honoured; the others are ignored
+  const uint32_t* ntt;  // transform tables for full products (null: strip products only)
+  int ntt_cut;
 };
 
 // Test entry: one group primitive per item (mpdiv_debug_primitive).
@@ -81,6 +87,7 @@ struct PrimArgs {
   int op, arg;
   int tcols;
   int smem_words;
+  const uint32_t* ntt;  // transform tables (op 9)
 };
 
 }  // namespace mp

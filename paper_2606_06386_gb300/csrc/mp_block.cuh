@@ -82,6 +82,26 @@ __device__ __forceinline__ Blk make_group(int* red, int w0, int nw, int bar) {
 template <int NW>
 __device__ __forceinline__ Blk make_block(int* red) { return make_group(red, 0, NW, 0); }
 
+// Whether the kernels of a translation unit divide with groups that are
+// slices of a block under named barriers (the self-splitting persistent
+// kernel defines it to 1); otherwise every group is a whole block.
+#ifndef MP_NAMED_GROUPS
+#define MP_NAMED_GROUPS 0
+#endif
+
+// Group barrier: the block's own barrier when the group is the whole block
+// (WHOLE), so that a kernel whose groups are all whole blocks reserves one
+// barrier only; a named barrier otherwise.
+template <bool WHOLE>
+__device__ __forceinline__ void group_sync(const Blk& b) {
+  if (!WHOLE)
+    b.sync();
+  else if (b.nt > 32)
+    __syncthreads();
+  else
+    __syncwarp();  // a one-warp block
+}
+
 // Group-wide maximum (minimum) of a warp-uniform value, one per warp; ends
 // with a group barrier.
 __device__ __forceinline__ int group_max(const Blk& b, int v) {
@@ -111,7 +131,7 @@ __device__ __forceinline__ void warp_range(const Blk& b, int len, int& lo, int& 
 // C[i] = X(i) + Y(i) (+ cin at digit 0) or X(i) - Y(i) (- cin) for i < len.
 // Returns the carry (borrow) out of digit len-1. C may alias X or Y only where
 // that functor reads index i itself.
-template <bool SUB, class FX, class FY>
+template <bool SUB, bool WHOLE = false, class FX, class FY>
 __device__ uint32_t addsub(const Blk& b, uint32_t* C, int len, FX X, FY Y, uint32_t cin) {
   int lo, hi;
   warp_range(b, len, lo, hi);
@@ -149,7 +169,7 @@ __device__ uint32_t addsub(const Blk& b, uint32_t* C, int len, FX X, FY Y, uint3
     return c;
   }
   if (b.lane == 0) b.red[b.warp] = (int)(c | ((allp && b.warp != 0) ? 2u : 0u));
-  b.sync();
+  group_sync<WHOLE>(b);
   const uint32_t sw = (b.lane < b.nw) ? (uint32_t)b.red[b.lane] : 2u;
   const uint32_t Gm = __ballot_sync(FULL, (sw & 1u) != 0);
   const uint32_t Pm = __ballot_sync(FULL, (sw & 3u) == 2u);
@@ -176,7 +196,7 @@ __device__ uint32_t addsub(const Blk& b, uint32_t* C, int len, FX X, FY Y, uint3
       }
     }
   }
-  b.sync();
+  group_sync<WHOLE>(b);
   return cout;
 }
 
@@ -510,26 +530,6 @@ __device__ __forceinline__ int strip_order(int idx, int nws, int base, int na, i
   if (k < 2 * m) return (k & 1) ? hi + (k >> 1) + 1 : lo - (k >> 1) - 1;
   const int d = m + 1 + (k - 2 * m);
   return (nl > nr) ? lo - d : hi + d;
-}
-
-// Whether the kernels of a translation unit divide with groups that are
-// slices of a block under named barriers (the self-splitting persistent
-// kernel defines it to 1); otherwise every group is a whole block.
-#ifndef MP_NAMED_GROUPS
-#define MP_NAMED_GROUPS 0
-#endif
-
-// Group barrier: the block's own barrier when the group is the whole block
-// (WHOLE), so that a kernel whose groups are all whole blocks reserves one
-// barrier only; a named barrier otherwise.
-template <bool WHOLE>
-__device__ __forceinline__ void group_sync(const Blk& b) {
-  if (!WHOLE)
-    b.sync();
-  else if (b.nt > 32)
-    __syncthreads();
-  else
-    __syncwarp();  // a one-warp block
 }
 
 // Whether the strip multiply is a called function rather than inlined at each

@@ -30,8 +30,12 @@
 //      full, max(h+41, 2h-kl+9)
 //   OV [two words per 96-column strip of P] multiply overflow digits
 // The total is largest at kl = 1: about 3 h digits clipped, 4 h full.
+// With full products and the number-theoretic transform enabled, the shared
+// memory left after OV is the transform's scratch: products of up to 2^s_log
+// digits with 4 * 2^s_log <= the words left use the transform.
 #pragma once
 #include "mp_block.cuh"
+#include "mp_ntt.cuh"
 
 namespace mp {
 
@@ -53,6 +57,10 @@ constexpr int CLIP_CORR = 4;
 struct Layout {
   uint32_t *V, *W, *X, *R, *U, *P, *OV;
   int capV, capW, capX, capR, capP, capOV, total;
+  uint32_t* S;  // transform scratch (4 * 2^s_log words) or null
+  int s_log;
+  const uint32_t* ntt;  // transform tables (ntt_tables.h), with S
+  int ntt_cut;          // the transform for products of at least this many digits
 };
 
 // Product buffer. Clipped: the Newton step keeps at most |R| - 1 digits above
@@ -109,7 +117,44 @@ __device__ __forceinline__ Layout make_layout(uint32_t* sm, int h, int kl, bool 
   off += L.capOV;
   L.total = off;
   L.U = L.X;  // u (h digits) overlays X, the pad and R once the shifted inverse is known
+  L.S = nullptr;
+  L.s_log = 0;
+  L.ntt = nullptr;
+  L.ntt_cut = 0;
   return L;
+}
+
+// The transform's scratch in the shared memory after the layout (words in
+// all): the longest transform whose four arrays fit; tab and cut as in Layout.
+__device__ __forceinline__ void layout_ntt_scratch(Layout& L, uint32_t* sm, int words, const uint32_t* tab, int cut) {
+  const int off = (L.total + 3) & ~3;
+  int t = NTT_LOG_MAX;
+  while (t > 0 && off + (4 << t) > words) t--;
+  if (t > 0) {
+    L.S = sm + off;
+    L.s_log = t;
+    L.ntt = tab;
+    L.ntt_cut = cut;
+  }
+}
+
+// An exact product C[0..npos) = (X Y) mod B^npos of full-product mode: in
+// kernels built with the transform (NTT) by the transform when nx + ny
+// reaches the cutoff and the transform fits the scratch, else by the strip
+// multiply (X and Y are then multiply operands). Both give the same digits.
+template <bool NTT>
+__device__ __forceinline__ bool ntt_fits(const Blk& b, const Layout& L, int nx, int ny) {
+  return NTT && L.s_log > 0 && nx > 0 && ny > 0 && nx + ny >= L.ntt_cut && nx + ny <= (1 << L.s_log);
+}
+template <bool NTT>
+__device__ __forceinline__ void mul_exact(const Blk& b, const Layout& L, uint32_t* C, int npos, uint32_t* X, int nx,
+                                          uint32_t* Y, int ny) {
+  if (ntt_fits<NTT>(b, L, nx, ny)) {
+    if (b.work != nullptr && b.tid == 0) *b.work += pair_count(nx, ny, npos);
+    ntt_mul<!MP_NAMED_GROUPS>(b, C, npos, X, nx, Y, ny, L.S, L.ntt, 0, false);
+  } else {
+    mul(b, C, npos, X, nx, Y, ny, L.OV);
+  }
 }
 
 __device__ __forceinline__ int ceil_log2(int x) {  // x >= 1
@@ -137,6 +182,7 @@ __device__ __forceinline__ int refine_iters(int h, int k) {
 // Algorithm 1 for v (in L.V, kl digits, top digit nonzero) and h >= kl.
 // Leaves shinv_h(v) in L.W and returns its digit count bound in *lw.
 // Returns a status.
+template <bool NTT>
 __device__ __forceinline__ int shinv(const Blk& b, const Layout& L, int h, int kl, int* lw_out, int* iters_out,
                             bool clip_step) {
   const int k = kl - 1;
@@ -225,7 +271,7 @@ __device__ __forceinline__ int shinv(const Blk& b, const Layout& L, int h, int k
     if (pw == 0 || Lc >= hp) {
       const int np = pv + pw;
       if (np > L.capP || np > L.capX || hp + 1 > L.capX) return ST_INTERNAL;
-      mul(b, P, np, X, pv, W, pw, L.OV);
+      mul_exact<NTT>(b, L, P, np, X, pv, W, pw);
       const bool ge = find_first(b, hp, np, [&](int i) { return P[i] != 0u; }) >= 0;
       if (!ge) {
         sign = 1;
@@ -246,7 +292,7 @@ __device__ __forceinline__ int shinv(const Blk& b, const Layout& L, int h, int k
       px = (px > 0) ? prec(b, X, px) : 0;
     } else {
       if (Lc > L.capP || Lc > L.capX) return ST_INTERNAL;
-      mul(b, P, Lc, X, pv, W, pw, L.OV);  // MultMod: v' w mod B^L
+      mul_exact<NTT>(b, L, P, Lc, X, pv, W, pw);  // MultMod: v' w mod B^L
       // one pass gives the sign test, the negation's pivot and |x|'s length
       int z, t1, t2;
       scan3(b, P, Lc, &z, &t1, &t2);
@@ -283,6 +329,8 @@ __device__ __forceinline__ int shinv(const Blk& b, const Layout& L, int h, int k
         p0 = mul_first_column(nt, plo);
         if (nt - p0 > L.capP || ov_words(nt - p0) > L.capOV) return ST_INTERNAL;
         mul(b, P, nt, W, pw, X, px, L.OV, plo, false, true);
+      } else if (ntt_fits<NTT>(b, L, pw, px)) {
+        mul_exact<NTT>(b, L, P, nt, W, pw, X, px);
       } else {
         // Karatsuba scratch: the product buffer's free tail, and R (free until
         // Step's sum below) for chunk products
@@ -327,8 +375,10 @@ __device__ __forceinline__ void store_digits(const Blk& b, uint32_t* g, int cap,
 
 // The whole of Algorithm 3 for one item. Returns a status; q and r are always
 // written (zeros on division by zero).
+template <bool NTT = false>
 __device__ __forceinline__ int div_item(const Blk& b, uint32_t* sm, int smem_words, const ItemIO& io, int flags, int* iters_out,
-                        uint32_t* dbg_w, int dbg_cap, int h_override) {
+                        uint32_t* dbg_w, int dbg_cap, int h_override, const uint32_t* ntt_tab = nullptr,
+                        int ntt_cut = 0) {
   const uint32_t* gu = io.u;
   const uint32_t* gv = io.v;
   *iters_out = 0;
@@ -356,13 +406,14 @@ __device__ __forceinline__ int div_item(const Blk& b, uint32_t* sm, int smem_wor
     return ST_INTERNAL;
   }
   const bool clip = (flags & FLAG_FULL_PRODUCTS) == 0;
-  const Layout L = make_layout(sm, h, kl, clip, layout_pad(clip, b.tcols));
+  Layout L = make_layout(sm, h, kl, clip, layout_pad(clip, b.tcols));
   if (L.total > smem_words) return ST_INTERNAL;
+  if (NTT && ntt_tab != nullptr && !clip) layout_ntt_scratch(L, sm, smem_words, ntt_tab, ntt_cut);
   for (int i = b.tid; i < L.total; i += b.nt) sm[i] = 0u;
   b.sync();
   load_global(b, L.V, kl, [&](int i) { return gv[i]; });
   int lw = 0, iters = 0;
-  int st = shinv(b, L, h, kl, &lw, &iters, clip);
+  int st = shinv<NTT>(b, L, h, kl, &lw, &iters, clip);
   *iters_out = iters;
   if (st != ST_OK) return st;
   uint32_t* W = L.W;
@@ -387,7 +438,10 @@ __device__ __forceinline__ int div_item(const Blk& b, uint32_t* sm, int smem_wor
   const int qlo = full ? 0 : max(0, h - QGUARD);
   const int q0c = mul_first_column(np, qlo);
   if (np - q0c > L.capP || ov_words(np - q0c) > L.capOV) return ST_INTERNAL;
-  mul(b, P, np, U, h, W, lw, L.OV, qlo, false, true);
+  if (NTT && full)
+    mul_exact<NTT>(b, L, P, np, U, h, W, lw);
+  else
+    mul(b, P, np, U, h, W, lw, L.OV, qlo, false, true);
   const uint32_t* Pq = P - q0c;
   int lq = np - h;
   if (lq + 1 > L.capW) return ST_INTERNAL;
@@ -399,7 +453,7 @@ __device__ __forceinline__ int div_item(const Blk& b, uint32_t* sm, int smem_wor
     // ---- m = v * q
     int nm = kl + lq;
     if (nm > L.capP) return ST_INTERNAL;
-    mul(b, P, nm, V, kl, W, lq, L.OV);
+    mul_exact<NTT>(b, L, P, nm, V, kl, W, lq);
     nm = prec(b, P, nm);
     // ---- if u < m: q -= 1, m -= v   (Theorem 2: delta = -1)
     for (int t = 0;; t++) {

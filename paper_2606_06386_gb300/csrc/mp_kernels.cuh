@@ -7,8 +7,9 @@
 
 namespace mp {
 
-// Plain launch: block b handles items b, b + gridDim.x, ...
-template <int NW, int MINB>
+// Plain launch: block b handles items b, b + gridDim.x, ... (NTT: full
+// products may use the transform, with its scratch after the item's layout)
+template <int NW, int MINB, bool NTT = false>
 __global__ void __launch_bounds__(NW * 32, MINB) k_div_uniform(UniformArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int red[RED_WORDS];
@@ -29,7 +30,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_uniform(UniformArgs a) {
     unsigned long long work = 0ull;
     Blk bw = b;
     bw.work = a.products ? &work : nullptr;
-    const int st = div_item(bw, sm, a.smem_words, io, a.flags, &it, nullptr, 0, 0);
+    const int st = div_item<NTT>(bw, sm, a.smem_words, io, a.flags, &it, nullptr, 0, 0, a.ntt, a.ntt_cut);
     if (b.tid == 0) {
       a.status[item] = st;
       if (a.iters) a.iters[item] = it;
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_uniform(UniformArgs a) {
 
 // Persistent launch over a size-sorted queue: each block repeatedly takes the
 // next item (largest first) until the queue is empty.
-template <int NW, int MINB>
+template <int NW, int MINB, bool NTT = false>
 __global__ void __launch_bounds__(NW * 32, MINB) k_div_ragged(RaggedArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int red[RED_WORDS];
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_ragged(RaggedArgs a) {
     unsigned long long work = 0ull;
     Blk bw = b;
     bw.work = a.products ? &work : nullptr;
-    const int st = div_item(bw, sm, a.smem_words, io, a.flags, &it, nullptr, 0, 0);
+    const int st = div_item<NTT>(bw, sm, a.smem_words, io, a.flags, &it, nullptr, 0, 0, a.ntt, a.ntt_cut);
     if (b.tid == 0) {
       a.status[item] = st;
       if (a.iters) a.iters[item] = it;
@@ -157,8 +158,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_persistent(RaggedArgs a) 
 }
 
 // The cost unit of the paper's multiplication count (Section 2.3, Fig. 3): the
-// product of two n-digit numbers kept to n digits, one per block.
-template <int NW, int MINB>
+// product of two n-digit numbers kept to n digits, one per block (NTT: by the
+// transform, with its scratch after OV, 16-byte aligned).
+template <int NW, int MINB, bool NTT = false>
 __global__ void __launch_bounds__(NW * 32, MINB) k_mul_low(UniformArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int red[RED_WORDS];
@@ -169,11 +171,15 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_mul_low(UniformArgs a) {
   uint32_t* Y = X + n + PAD;
   uint32_t* P = Y + n + PAD;
   uint32_t* OV = P + n + 4;
+  uint32_t* S = sm + ((PAD + n + PAD + n + PAD + n + 4 + ov_words(n) + 3) & ~3);
   for (int64_t item = blockIdx.x; item < a.n; item += gridDim.x) {
     for (int i = b.tid; i < PAD; i += b.nt) sm[i] = 0u;
     load_global(b, X, n, [&](int i) { return a.u[item * a.us + i]; });
     load_global(b, Y, n, [&](int i) { return a.v[item * a.vs + i]; });
-    mul(b, P, n, X, n, Y, n, OV);
+    if (NTT)
+      ntt_mul<true>(b, P, n, X, n, Y, n, S, a.ntt, 0, false);
+    else
+      mul(b, P, n, X, n, Y, n, OV);
     store_digits(b, a.q + item * a.qs, n, P, n);
     b.sync();
   }
@@ -192,6 +198,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_prim(PrimArgs a) {
   uint32_t* Y = X + a.nx + PAD;
   uint32_t* C = Y + a.ny + PAD;
   uint32_t* OV = C + a.cap + 4;
+  uint32_t* S = sm + ((PAD + a.nx + PAD + a.ny + PAD + a.cap + 4 + ov_words(a.cap) + 3) & ~3);
   for (int64_t item = blockIdx.x; item < a.n; item += gridDim.x) {
     for (int i = b.tid; i < a.smem_words; i += b.nt) sm[i] = 0u;
     b.sync();
@@ -226,6 +233,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_prim(PrimArgs a) {
         break;
       }
       case 8: negate(b, C, a.cap, X, a.nx); break;
+      case 9: res = ntt_mul<true>(b, C, a.cap, X, a.nx, Y, a.ny, S, a.ntt, a.arg, false); break;
       default: res = -1;
     }
     for (int i = b.tid; i < a.cap; i += b.nt) a.out[item * a.cap + i] = C[i];
@@ -235,7 +243,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_prim(PrimArgs a) {
 }
 
 // Test entry: shinv_h(v) as the division path computes it.
-template <int NW, int MINB>
+template <int NW, int MINB, bool NTT = false>
 __global__ void __launch_bounds__(NW * 32, MINB) k_shinv(ShinvArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int red[RED_WORDS];
@@ -254,7 +262,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_shinv(ShinvArgs a) {
     io.rn = 0;
     int it = 0;
     const int h = max(a.h[item], 1);
-    const int st = div_item(b, sm, a.smem_words, io, a.flags & FLAG_FULL_PRODUCTS, &it, a.out + item * a.os, a.on, h);
+    const int st =
+        div_item<NTT>(b, sm, a.smem_words, io, a.flags & FLAG_FULL_PRODUCTS, &it, a.out + item * a.os, a.on, h,
+                      a.ntt, a.ntt_cut);
     if (b.tid == 0) {
       a.status[item] = st;
       if (a.iters) a.iters[item] = it;

@@ -47,6 +47,15 @@ void* kernel_for(KernKind kk, int warps) {
   return mp_kernel_w32(kk);
 }
 
+// Block size of the transform-enabled plain kernel that serves a request for
+// w warps (4, 8 or 16), and the kernel of a kind with the transform enabled
+// (the plain launch at that block size; the queue and test kernels at 16).
+int ntt_kernel_warps(int w) { return w <= 4 ? 4 : w <= 8 ? 8 : 16; }
+void* ntt_kernel_for(KernKind kk, int warps) {
+  if (kk == KK_UNIFORM) return mp_kernel_ntt_uniform(ntt_kernel_warps(warps));
+  return mp_kernel_ntt_queue(kk);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ context helpers
@@ -71,6 +80,29 @@ int mpdiv_cuda_check(mpdiv_ctx* ctx, cudaError_t e, const char* what) {
 int mpdiv_smem_bytes(int max_digits, int flags, int tcols) {
   const bool clip = (flags & MPDIV_FLAG_FULL_PRODUCTS) == 0;
   return (smem_words_for(max_digits, clip, layout_pad(clip, tcols)) * 4 + 15) & ~15;
+}
+
+// Transform tables for the division kernels (null unless the context's full
+// products may use the transform) and the digit count from which they do.
+static const uint32_t* ntt_tables(const mpdiv_ctx* ctx) {
+  return (ctx->cfg.flags & MPDIV_FLAG_NTT_PRODUCTS) ? ctx->d_ntt : nullptr;
+}
+static int ntt_cutoff(const mpdiv_ctx* ctx) {
+  return ctx->cfg.transform_cutoff > 0 ? ctx->cfg.transform_cutoff : 1024;
+}
+
+// Shared memory of a division launch whose dividends have at most max_digits
+// digits: the layout, and with the transform enabled its scratch after it,
+// four words per point of the longest transform that a product of two such
+// operands can use within the device's limit (longer products take the strip
+// multiply).
+static int launch_smem_bytes(mpdiv_ctx* ctx, int max_digits, int tcols) {
+  const int smem = mpdiv_smem_bytes(max_digits, ctx->cfg.flags, tcols);
+  if (ntt_tables(ctx) == nullptr || smem > ctx->max_smem) return smem;
+  int t = std::min(NTT_LOG_MAX, ntt_log(2 * max_digits));
+  while (t > 0 && smem + (16 << t) > ctx->max_smem) t--;
+  if (t == 0 || (1 << t) < ntt_cutoff(ctx)) return smem;
+  return smem + (16 << t);
 }
 
 // The block size of the kernel instantiation that serves a request for w
@@ -171,12 +203,29 @@ extern "C" int mpdiv_init(mpdiv_ctx** out, int device, const mpdiv_config* cfg) 
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaDeviceGetAttribute(&ctx->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   cudaDeviceGetAttribute(&ctx->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+  if (ctx->cfg.flags & MPDIV_FLAG_NTT_PRODUCTS) ctx->cfg.flags |= MPDIV_FLAG_FULL_PRODUCTS;
   if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&ctx->d_head, 64), "cudaMalloc(queue head)")) != MPDIV_OK) {
     delete ctx;
     return rc;
   }
+  {
+    std::vector<uint32_t> tab(mp_ntt::kWords);
+    mp_ntt::build_tables(tab.data());
+    rc = mpdiv_cuda_check(ctx, cudaMalloc(&ctx->d_ntt, sizeof(uint32_t) * tab.size()), "cudaMalloc(transform tables)");
+    if (rc == MPDIV_OK)
+      rc = mpdiv_cuda_check(
+          ctx, cudaMemcpy(ctx->d_ntt, tab.data(), sizeof(uint32_t) * tab.size(), cudaMemcpyHostToDevice),
+          "upload of the transform tables");
+    if (rc != MPDIV_OK) {
+      if (ctx->d_ntt) cudaFree(ctx->d_ntt);
+      cudaFree(ctx->d_head);
+      delete ctx;
+      return rc;
+    }
+  }
   if ((rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking),
                              "cudaStreamCreate")) != MPDIV_OK) {
+    cudaFree(ctx->d_ntt);
     cudaFree(ctx->d_head);
     delete ctx;
     return rc;
@@ -194,6 +243,7 @@ extern "C" void mpdiv_destroy(mpdiv_ctx* ctx) {
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->d_order) cudaFree(ctx->d_order);
   if (ctx->d_head) cudaFree(ctx->d_head);
+  if (ctx->d_ntt) cudaFree(ctx->d_ntt);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
@@ -207,15 +257,16 @@ extern "C" const char* mpdiv_last_error(const mpdiv_ctx* ctx) {
 int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t stream) {
   const int max_digits = L.un;
   const int tcols = L.tcols > 0 ? L.tcols : mpdiv_default_tcols(ctx, max_digits);
-  const int smem = mpdiv_smem_bytes(max_digits, ctx->cfg.flags, tcols);
+  const int smem = launch_smem_bytes(ctx, max_digits, tcols);
   if (smem > ctx->max_smem)
     return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory, device allows %d", smem,
                            ctx->max_smem);
-  const int warps = L.warps > 0 ? kernel_warps(L.warps) : mpdiv_default_warps(ctx, max_digits);
-  void* k = kernel_for(KK_UNIFORM, warps);
+  int warps = L.warps > 0 ? kernel_warps(L.warps) : mpdiv_default_warps(ctx, max_digits);
+  if (ntt_tables(ctx)) warps = ntt_kernel_warps(warps);
+  void* k = ntt_tables(ctx) ? ntt_kernel_for(KK_UNIFORM, warps) : kernel_for(KK_UNIFORM, warps);
   int rc = prepare_kernel(ctx, k, smem);
   if (rc) return rc;
-  UniformArgs a;
+  UniformArgs a{};
   a.u = L.u;
   a.v = L.v;
   a.q = L.q;
@@ -236,6 +287,8 @@ int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t st
   a.flags = ctx->cfg.flags;
   a.tcols = tcols;
   a.kcut = L.kcut >= 0 ? L.kcut : mpdiv_default_kcut(ctx, max_digits);
+  a.ntt = ntt_tables(ctx);
+  a.ntt_cut = ntt_cutoff(ctx);
   const int64_t grid = std::min<int64_t>(L.n, 0x7fffffff);
   void* args[] = {&a};
   cudaError_t e = cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * warps), args, smem, stream);
@@ -336,17 +389,20 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
   RaggedArgs a;
   std::memset(&a, 0, sizeof a);  // the graph cache compares argument blocks bytewise
   int warps = 0, smem = 0;
-  if (L.split) {
+  // the self-splitting kernel is built without the transform
+  const bool split = L.split && ntt_tables(ctx) == nullptr;
+  if (split) {
     int words = 0;
     persistent_shape(ctx, max_u, a, &warps, &words);
     smem = words * 4;
   } else {
-    smem = mpdiv_smem_bytes(max_u, ctx->cfg.flags, T_MAX);  // any strip width per item
+    smem = launch_smem_bytes(ctx, max_u, T_MAX);  // any strip width per item
     warps = 16;  // the one-block-per-item queue kernel is built for 16-warp blocks
   }
   if (smem > ctx->max_smem)
     return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory", smem);
-  void* k = kernel_for(L.split ? KK_PERSIST : KK_RAGGED, warps);
+  void* k = split ? kernel_for(KK_PERSIST, warps)
+                  : (ntt_tables(ctx) ? ntt_kernel_for(KK_RAGGED, warps) : kernel_for(KK_RAGGED, warps));
   int rc = prepare_kernel(ctx, k, smem);
   if (rc) return rc;
   // size-sorted order (cached by content of the shape list)
@@ -409,8 +465,10 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
   a.n = L.n;
   a.smem_words = smem / 4;
   a.flags = ctx->cfg.flags;
-  a.tcols = L.split ? 0 : mpdiv_default_tcols(ctx, max_u);  // persistent: per class (configured or tuned)
-  a.kcut = L.split ? -1 : mpdiv_default_kcut(ctx, max_u);
+  a.tcols = split ? 0 : mpdiv_default_tcols(ctx, max_u);  // persistent: per class (configured or tuned)
+  a.kcut = split ? -1 : mpdiv_default_kcut(ctx, max_u);
+  a.ntt = ntt_tables(ctx);
+  a.ntt_cut = ntt_cutoff(ctx);
   if (!L.use_graph) {
     if ((rc = mpdiv_cuda_check(ctx, cudaMemsetAsync(a.head, 0, sizeof(int32_t), stream), "queue reset"))) return rc;
     void* args[] = {&a};
@@ -520,10 +578,12 @@ extern "C" int mpdiv_debug_shinv(mpdiv_ctx* ctx, int64_t n_items, const uint32_t
   while (max_h > 256 && mpdiv_smem_bytes(max_h, ctx->cfg.flags, tcols) > ctx->max_smem) max_h -= 256;
   const int smem = mpdiv_smem_bytes(max_h, ctx->cfg.flags, tcols);
   const int warps = 16;  // the test entry is built for 16-warp blocks
-  void* k = kernel_for(KK_SHINV, warps);
+  void* k = ntt_tables(ctx) ? ntt_kernel_for(KK_SHINV, warps) : kernel_for(KK_SHINV, warps);
   int rc = prepare_kernel(ctx, k, smem);
   if (rc) return rc;
-  ShinvArgs a;
+  ShinvArgs a{};
+  a.ntt = ntt_tables(ctx);  // per item, the shared memory its layout leaves
+  a.ntt_cut = ntt_cutoff(ctx);
   a.v = v;
   a.h = h_digits;
   a.out = out;
@@ -551,7 +611,8 @@ extern "C" int mpdiv_debug_primitive(mpdiv_ctx* ctx, int32_t op, int64_t n_items
   if (!ctx) return MPDIV_EINVAL;
   if (n_items <= 0) return n_items == 0 ? MPDIV_OK : mpdiv_set_error(ctx, MPDIV_EINVAL, "n_items < 0");
   if (!x || !y || !out || !result) return mpdiv_set_error(ctx, MPDIV_EINVAL, "null pointer argument");
-  if (op < 0 || op > 8) return mpdiv_set_error(ctx, MPDIV_EINVAL, "unknown primitive %d", op);
+  if (op < 0 || op > 9) return mpdiv_set_error(ctx, MPDIV_EINVAL, "unknown primitive %d", op);
+  if (op == 9 && nx + ny > NTT_MAX) return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "transform longer than %d", NTT_MAX);
   if (nx < 1 || ny < 1 || cap < 1 || arg < 0 || (op == 7 && cap < 3))
     return mpdiv_set_error(ctx, MPDIV_EINVAL, "bad sizes");
   if ((op == 0 || op == 1 || op == 8) && cap < std::max(nx, ny))
@@ -559,7 +620,8 @@ extern "C" int mpdiv_debug_primitive(mpdiv_ctx* ctx, int32_t op, int64_t n_items
   if ((op == 4 || op == 5) && (cap < nx || arg >= cap)) return mpdiv_set_error(ctx, MPDIV_EINVAL, "bad power");
   cudaSetDevice(ctx->device);
   const int w = kernel_warps(warps < 1 ? 1 : warps);
-  const int words = 3 * PAD + nx + ny + cap + 4 + ov_words(cap);
+  int words = 3 * PAD + nx + ny + cap + 4 + ov_words(cap);
+  if (op == 9) words = ((words + 3) & ~3) + (4 << ntt_log(nx + ny));  // the transform's scratch
   const int smem = (words * 4 + 15) & ~15;
   if (smem > ctx->max_smem) return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory", smem);
   void* k = mp_kernel_prim(w);
@@ -579,6 +641,7 @@ extern "C" int mpdiv_debug_primitive(mpdiv_ctx* ctx, int32_t op, int64_t n_items
   a.arg = arg;
   a.tcols = ctx->cfg.mul_columns > 0 ? ctx->cfg.mul_columns : 3;
   a.smem_words = smem / 4;
+  a.ntt = ctx->d_ntt;
   void* args[] = {&a};
   const int64_t grid = std::min<int64_t>(n_items, 0x7fffffff);
   return mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * w), args, smem, (cudaStream_t)stream),
@@ -607,11 +670,14 @@ extern "C" int mpdiv_mul_batch(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* 
   cudaSetDevice(ctx->device);
   const int n = n_limbs;
   const int tc = mpdiv_default_tcols(ctx, n);
-  const int words = 4 * PAD + 3 * n + 8 + ov_words(n);
+  int words = 4 * PAD + 3 * n + 8 + ov_words(n);
+  // with the transform enabled, n-digit products up to its length use it
+  const bool use_ntt = ntt_tables(ctx) != nullptr && 2 * n <= NTT_MAX && 2 * n >= ntt_cutoff(ctx);
+  if (use_ntt) words = std::max(words, ((3 * PAD + 3 * n + 4 + ov_words(n) + 3) & ~3) + (4 << ntt_log(2 * n)));
   const int smem = (words * 4 + 15) & ~15;
   if (smem > ctx->max_smem) return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory", smem);
-  const int warps = mpdiv_default_warps(ctx, n);
-  void* k = kernel_for(KK_MUL, warps);
+  const int warps = use_ntt ? ntt_kernel_warps(mpdiv_default_warps(ctx, n)) : mpdiv_default_warps(ctx, n);
+  void* k = use_ntt ? mp_kernel_ntt_mul(warps) : kernel_for(KK_MUL, warps);
   int rc = prepare_kernel(ctx, k, smem);
   if (rc) return rc;
   UniformArgs a;
@@ -625,6 +691,7 @@ extern "C" int mpdiv_mul_batch(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* 
   a.qs = out_stride;
   a.un = n;
   a.tcols = tc;
+  a.ntt = use_ntt ? ctx->d_ntt : nullptr;
   void* args[] = {&a};
   const int64_t grid = std::min<int64_t>(n_items, 0x7fffffff);
   return mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * warps), args, smem,

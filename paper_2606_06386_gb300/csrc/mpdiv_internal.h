@@ -21,7 +21,8 @@ struct mpdiv_ctx {
   int num_sms = 0;
   int max_smem = 0;
   int smem_per_sm = 0;  // shared memory of one SM (all resident blocks)
-  mpdiv_config cfg{0, 0, 0, 0, 0};
+  mpdiv_config cfg{0, 0, 0, 0, 0, 0};
+  uint32_t* d_ntt = nullptr;  // transform tables (ntt_tables.h), built at init
   mutable std::mutex err_mu;
   std::string err;
   // tuning table: size class (digits, power of two >= 128) -> launch shape

@@ -1,0 +1,6 @@
+// The 8-warp plain-launch division kernel whose full products may use the
+// number-theoretic transform.
+#include "mp_kernels.cuh"
+#include "mpdiv_kernels.h"
+
+void* mp_kernel_ntt_uniform8() { return (void*)mp::k_div_uniform<8, 4, true>; }

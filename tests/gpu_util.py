@@ -19,14 +19,15 @@ def host_u32(t):
 _ctx = {}
 
 
-def ctx(flags=0, warps=0, cols=0, kcut=0):
-    key = (flags, warps, cols, kcut)
+def ctx(flags=0, warps=0, cols=0, kcut=0, tcut=0):
+    key = (flags, warps, cols, kcut, tcut)
     if key not in _ctx:
-        _ctx[key] = mp.mpdiv_init(0, warps_per_block=warps, flags=flags, mul_columns=cols, karatsuba_cutoff=kcut)
+        _ctx[key] = mp.mpdiv_init(0, warps_per_block=warps, flags=flags, mul_columns=cols, karatsuba_cutoff=kcut,
+                                  transform_cutoff=tcut)
     return _ctx[key]
 
 
-def run_uniform(U, V, qn=None, rn=None, flags=0, warps=0, cols=0, kcut=0, products=False):
+def run_uniform(U, V, qn=None, rn=None, flags=0, warps=0, cols=0, kcut=0, products=False, tcut=0):
     """Divide row i of U by row i of V on the GPU. Returns (Q, R, status, iters)."""
     import torch
 
@@ -40,7 +41,7 @@ def run_uniform(U, V, qn=None, rn=None, flags=0, warps=0, cols=0, kcut=0, produc
     st = torch.full((n,), -7, dtype=torch.int32, device="cuda:0")
     it = torch.full((n,), -1, dtype=torch.int32, device="cuda:0")
     pr = torch.zeros((n,), dtype=torch.int64, device="cuda:0") if products else None
-    mp.mpdiv_batch(ctx(flags, warps, cols, kcut), dev(U), dev(V), q, r, st, it, pr)
+    mp.mpdiv_batch(ctx(flags, warps, cols, kcut, tcut), dev(U), dev(V), q, r, st, it, pr)
     torch.cuda.synchronize()
     if products:
         return host_u32(q), host_u32(r), st.cpu().numpy(), it.cpu().numpy(), pr.cpu().numpy()
