@@ -88,7 +88,7 @@ typedef struct mpdiv_config {
                            many digits (> 0); -1: never; 0: per size class from the tuning
                            table (never if untuned) */
   int transform_cutoff; /* with MPDIV_FLAG_NTT_PRODUCTS: products whose operands have at least
-                           this many digits together use the transform (0: 1024) */
+                           this many digits together use the transform (0: 4096) */
 } mpdiv_config;
 
 /* Create a context on CUDA device `device` (cfg may be NULL for defaults).

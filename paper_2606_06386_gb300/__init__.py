@@ -23,7 +23,7 @@ _BUILD = os.path.join(_HERE, "_build")
 SO_PATH = os.path.join(_BUILD, "libmpdiv.so")
 HEADER = os.path.join(_ROOT, "include", "mpdiv.h")
 SOURCES = ["mpdiv_p.cu", "mpdiv_p16.cu", "mpdiv_q.cu", "mpdiv_t.cu", "mpdiv_k1.cu", "mpdiv_k2.cu", "mpdiv_k4.cu", "mpdiv_k8.cu", "mpdiv_k16.cu",
-           "mpdiv_k32.cu", "mpdiv_n.cu", "mpdiv_n8.cu", "mpdiv_n16.cu",
+           "mpdiv_k32.cu", "mpdiv_n.cu", "mpdiv_n8.cu", "mpdiv_n16.cu", "mpdiv_n32.cu",
            "mpdiv_n2.cu", "mpdiv_n3.cu", "mpdiv_noalloc.cu", "mpdiv.cu", "mpdiv_tune.cu", "mpdiv_serve.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

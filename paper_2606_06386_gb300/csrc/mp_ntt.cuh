@@ -65,46 +65,100 @@ __device__ __forceinline__ uint32_t mod_mont(uint32_t x, uint32_t y, uint32_t p,
   return u >= p ? u - p : u;
 }
 
-// Forward transforms of Z0 and Z1 (2^logn residues each) modulo prime j.
+// Two stages of the forward transform on the four residues z[0], z[h], z[2h],
+// z[3h] (a radix-4 pass): the stage of half-length m = 2h with twiddles w1 =
+// omega_{2m}^i and w2 = omega_{2m}^(i+h), then the stage of half-length h with
+// w3 = omega_m^i; (w, ws) pairs are a constant and its Shoup companion.
+__device__ __forceinline__ void dif4(uint32_t* z, int h, uint32_t p, uint32_t w1, uint32_t w1s, uint32_t w2,
+                                     uint32_t w2s, uint32_t w3, uint32_t w3s) {
+  const uint32_t a0 = z[0], a1 = z[h], a2 = z[2 * h], a3 = z[3 * h];
+  const uint32_t b0 = mod_add(a0, a2, p), b2 = mod_shoup(a0 + p - a2, w1, w1s, p);
+  const uint32_t b1 = mod_add(a1, a3, p), b3 = mod_shoup(a1 + p - a3, w2, w2s, p);
+  z[0] = mod_add(b0, b1, p);
+  z[h] = mod_shoup(b0 + p - b1, w3, w3s, p);
+  z[2 * h] = mod_add(b2, b3, p);
+  z[3 * h] = mod_shoup(b2 + p - b3, w3, w3s, p);
+}
+
+// Two stages of the inverse transform on z[0], z[h], z[2h], z[3h]: the stage
+// of half-length h with u1 = omega_{2h}^-i on both pairs, then the stage of
+// half-length 2h with u2 = omega_{4h}^-i and u3 = omega_{4h}^-(i+h).
+__device__ __forceinline__ void dit4(uint32_t* z, int h, uint32_t p, uint32_t u1, uint32_t u1s, uint32_t u2,
+                                     uint32_t u2s, uint32_t u3, uint32_t u3s) {
+  const uint32_t a0 = z[0], a1 = z[h], a2 = z[2 * h], a3 = z[3 * h];
+  uint32_t t = mod_shoup(a1, u1, u1s, p);
+  const uint32_t b0 = mod_add(a0, t, p), b1 = mod_sub(a0, t, p);
+  t = mod_shoup(a3, u1, u1s, p);
+  const uint32_t b2 = mod_add(a2, t, p), b3 = mod_sub(a2, t, p);
+  t = mod_shoup(b2, u2, u2s, p);
+  z[0] = mod_add(b0, t, p);
+  z[2 * h] = mod_sub(b0, t, p);
+  t = mod_shoup(b3, u3, u3s, p);
+  z[h] = mod_add(b1, t, p);
+  z[3 * h] = mod_sub(b1, t, p);
+}
+
+// The stage of half-length 1 (twiddle 1) on the pairs (z[2g], z[2g+1]),
+// read and written as 8-byte words (Z 8-byte aligned).
+__device__ __forceinline__ void ntt_pairs(const Blk& b, uint32_t* Z, int half, uint32_t p) {
+  uint2* Z2 = reinterpret_cast<uint2*>(Z);
+  for (int g = b.tid; g < half; g += b.nt) {
+    const uint2 v = Z2[g];
+    Z2[g] = make_uint2(mod_add(v.x, v.y, p), mod_sub(v.x, v.y, p));
+  }
+}
+
+// Forward transforms of Z0 and Z1 (2^logn residues each) modulo prime j:
+// radix-4 passes from the longest stage down, then the last radix-2 stage
+// when logn is odd. One barrier per pass.
 template <bool WHOLE>
 __device__ __forceinline__ void ntt_forward2(const Blk& b, uint32_t* Z0, uint32_t* Z1, int logn, const uint32_t* tab,
                                              int j) {
   const uint32_t p = __ldg(tab + mp_ntt::kP + j);
-  const uint32_t* fw = tab + j * mp_ntt::kPerPrime + mp_ntt::kFw;
-  const uint32_t* fws = tab + j * mp_ntt::kPerPrime + mp_ntt::kFws;
-  const int half = 1 << (logn - 1);
-  for (int lm = logn - 1; lm >= 0; lm--) {
-    const int m = 1 << lm;
-    for (int t = b.tid; t < half; t += b.nt) {
-      const int i = t & (m - 1);
-      const int lo = ((t >> lm) << (lm + 1)) + i, hi = lo + m;
-      const uint32_t w = __ldg(fw + m + i), ws = __ldg(fws + m + i);
-      const uint32_t a0 = Z0[lo], c0 = Z0[hi], a1 = Z1[lo], c1 = Z1[hi];
-      Z0[lo] = mod_add(a0, c0, p);
-      Z0[hi] = mod_shoup(a0 + p - c0, w, ws, p);
-      Z1[lo] = mod_add(a1, c1, p);
-      Z1[hi] = mod_shoup(a1 + p - c1, w, ws, p);
+  const uint2* fw = reinterpret_cast<const uint2*>(tab + j * mp_ntt::kPerPrime + mp_ntt::kFw);
+  const int quarter = (1 << logn) >> 2;
+  int lm = logn - 1;
+  for (; lm >= 1; lm -= 2) {
+    const int m = 1 << lm, h = m >> 1;
+#pragma unroll 2
+    for (int g = b.tid; g < quarter; g += b.nt) {
+      const int i = g & (h - 1);
+      const int base = ((g >> (lm - 1)) << (lm + 1)) + i;
+      const uint2 w1 = __ldg(fw + m + i), w2 = __ldg(fw + m + h + i), w3 = __ldg(fw + h + i);
+      dif4(Z0 + base, h, p, w1.x, w1.y, w2.x, w2.y, w3.x, w3.y);
+      dif4(Z1 + base, h, p, w1.x, w1.y, w2.x, w2.y, w3.x, w3.y);
     }
+    group_sync<WHOLE>(b);
+  }
+  if (lm == 0) {
+    ntt_pairs(b, Z0, 1 << (logn - 1), p);
+    ntt_pairs(b, Z1, 1 << (logn - 1), p);
     group_sync<WHOLE>(b);
   }
 }
 
-// Inverse transform of Z (bit-reversed order in, natural order out, times N).
+// Inverse transform of Z (bit-reversed order in, natural order out, times N):
+// the radix-2 stage of half-length 1 first when logn is odd, then radix-4
+// passes upward.
 template <bool WHOLE>
 __device__ __forceinline__ void ntt_inverse(const Blk& b, uint32_t* Z, int logn, const uint32_t* tab, int j) {
   const uint32_t p = __ldg(tab + mp_ntt::kP + j);
-  const uint32_t* iw = tab + j * mp_ntt::kPerPrime + mp_ntt::kIw;
-  const uint32_t* iws = tab + j * mp_ntt::kPerPrime + mp_ntt::kIws;
-  const int half = 1 << (logn - 1);
-  for (int lm = 0; lm < logn; lm++) {
-    const int m = 1 << lm;
-    for (int t = b.tid; t < half; t += b.nt) {
-      const int i = t & (m - 1);
-      const int lo = ((t >> lm) << (lm + 1)) + i, hi = lo + m;
-      const uint32_t a = Z[lo];
-      const uint32_t c = mod_shoup(Z[hi], __ldg(iw + m + i), __ldg(iws + m + i), p);
-      Z[lo] = mod_add(a, c, p);
-      Z[hi] = mod_sub(a, c, p);
+  const uint2* iw = reinterpret_cast<const uint2*>(tab + j * mp_ntt::kPerPrime + mp_ntt::kIw);
+  const int quarter = (1 << logn) >> 2;
+  int lm = 0;
+  if (logn & 1) {
+    ntt_pairs(b, Z, 1 << (logn - 1), p);
+    group_sync<WHOLE>(b);
+    lm = 1;
+  }
+  for (; lm < logn; lm += 2) {
+    const int h = 1 << lm, m = 2 * h;
+#pragma unroll 2
+    for (int g = b.tid; g < quarter; g += b.nt) {
+      const int i = g & (h - 1);
+      const int base = ((g >> lm) << (lm + 2)) + i;
+      const uint2 u1 = __ldg(iw + h + i), u2 = __ldg(iw + m + i), u3 = __ldg(iw + m + h + i);
+      dit4(Z + base, h, p, u1.x, u1.y, u2.x, u2.y, u3.x, u3.y);
     }
     group_sync<WHOLE>(b);
   }

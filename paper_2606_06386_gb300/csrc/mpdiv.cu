@@ -48,9 +48,10 @@ void* kernel_for(KernKind kk, int warps) {
 }
 
 // Block size of the transform-enabled plain kernel that serves a request for
-// w warps (4, 8 or 16), and the kernel of a kind with the transform enabled
-// (the plain launch at that block size; the queue and test kernels at 16).
-int ntt_kernel_warps(int w) { return w <= 4 ? 4 : w <= 8 ? 8 : 16; }
+// w warps (4, 8, 16 or 32), and the kernel of a kind with the transform
+// enabled (the plain launch at that block size; the queue and test kernels at
+// 16).
+int ntt_kernel_warps(int w) { return w <= 4 ? 4 : w <= 8 ? 8 : w <= 16 ? 16 : 32; }
 void* ntt_kernel_for(KernKind kk, int warps) {
   if (kk == KK_UNIFORM) return mp_kernel_ntt_uniform(ntt_kernel_warps(warps));
   return mp_kernel_ntt_queue(kk);
@@ -88,7 +89,7 @@ static const uint32_t* ntt_tables(const mpdiv_ctx* ctx) {
   return (ctx->cfg.flags & MPDIV_FLAG_NTT_PRODUCTS) ? ctx->d_ntt : nullptr;
 }
 static int ntt_cutoff(const mpdiv_ctx* ctx) {
-  return ctx->cfg.transform_cutoff > 0 ? ctx->cfg.transform_cutoff : 1024;
+  return ctx->cfg.transform_cutoff > 0 ? ctx->cfg.transform_cutoff : 4096;  // measured break-even on GB300
 }
 
 // Shared memory of a division launch whose dividends have at most max_digits

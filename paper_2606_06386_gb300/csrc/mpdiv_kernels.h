@@ -18,9 +18,10 @@ void* mp_kernel_persistent16();         // mpdiv_p16.cu
 void* mp_kernel_w16_queue(int kind);    // mpdiv_q.cu: MP_K_RAGGED and MP_K_SHINV
 void* mp_kernel_prim(int warps);        // mpdiv_t.cu: the primitive test kernel (1, 2, 4, 8, 16, 32 warps)
 // kernels whose full products may use the number-theoretic transform
-void* mp_kernel_ntt_uniform(int warps);  // mpdiv_n.cu: 4, 8 or 16 warps (ntt_kernel_warps)
-void* mp_kernel_ntt_mul(int warps);      // mpdiv_n.cu: the multiplication cost unit, 4, 8 or 16 warps
+void* mp_kernel_ntt_uniform(int warps);  // mpdiv_n.cu: 4, 8, 16 or 32 warps (ntt_kernel_warps)
+void* mp_kernel_ntt_mul(int warps);      // mpdiv_n.cu: the multiplication cost unit, 4, 8, 16 or 32 warps
 void* mp_kernel_ntt_uniform8();          // mpdiv_n8.cu
 void* mp_kernel_ntt_uniform16();         // mpdiv_n16.cu
+void* mp_kernel_ntt_uniform32();         // mpdiv_n32.cu
 void* mp_kernel_ntt_queue(int kind);     // mpdiv_n2.cu: MP_K_RAGGED and MP_K_SHINV, 16 warps
 void* mp_kernel_ntt_shinv();             // mpdiv_n3.cu

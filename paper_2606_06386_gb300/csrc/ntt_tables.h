@@ -17,10 +17,11 @@ constexpr uint32_t kPrime[3] = {2113929217u, 2013265921u, 1811939329u};
 constexpr uint32_t kRoot[3] = {5u, 31u, 13u};
 
 // Table layout (32-bit words). For prime j at j*4*kMax: the forward twiddles
-// fw[m + i] = omega_{2m}^i (m = 1, 2, 4, ..., kMax/2; i < m; omega_{2m} a
-// primitive 2m-th root of unity), their Shoup companions floor(w 2^32 / p),
-// the inverse twiddles omega_{2m}^-i and their companions, kMax words each.
-constexpr int kFw = 0, kFws = kMax, kIw = 2 * kMax, kIws = 3 * kMax;
+// w_k = omega_{2m}^i for k = m + i (m = 1, 2, 4, ..., kMax/2; i < m;
+// omega_{2m} a primitive 2m-th root of unity), each followed by its Shoup
+// companion floor(w 2^32 / p) (the pair for k at kFw + 2k, one 8-byte load);
+// then the inverse twiddles omega_{2m}^-i with companions at kIw + 2k.
+constexpr int kFw = 0, kIw = 2 * kMax;
 constexpr int kPerPrime = 4 * kMax;
 // Constants after the three prime blocks:
 constexpr int kConst = 3 * kPerPrime;
@@ -53,16 +54,16 @@ inline void build_tables(uint32_t* t) {
   for (int j = 0; j < 3; j++) {
     const uint32_t p = kPrime[j];
     uint32_t* b = t + j * kPerPrime;
-    b[kFw] = b[kFws] = b[kIw] = b[kIws] = 0u;  // index 0 is not used
+    b[kFw] = b[kFw + 1] = b[kIw] = b[kIw + 1] = 0u;  // pair 0 is not used
     for (int m = 1; m < kMax; m *= 2) {
       const uint32_t w = powmod(kRoot[j], (p - 1u) / (2u * (uint32_t)m), p);
       const uint32_t wi = invmod(w, p);
       uint32_t f = 1u, g = 1u;
       for (int i = 0; i < m; i++) {
-        b[kFw + m + i] = f;
-        b[kFws + m + i] = shoup_companion(f, p);
-        b[kIw + m + i] = g;
-        b[kIws + m + i] = shoup_companion(g, p);
+        b[kFw + 2 * (m + i)] = f;
+        b[kFw + 2 * (m + i) + 1] = shoup_companion(f, p);
+        b[kIw + 2 * (m + i)] = g;
+        b[kIw + 2 * (m + i) + 1] = shoup_companion(g, p);
         f = mulmod(f, w, p);
         g = mulmod(g, wi, p);
       }

@@ -42,6 +42,7 @@ static uint32_t pw(uint32_t x, uint64_t e, uint32_t p) {
 // radix-2 recursion of the DFT, evaluated with the table's roots) and the
 // Chinese remainder theorem on 128-bit integers.
 static void dft(std::vector<uint32_t>& a, uint32_t p, const uint32_t* fw, bool inv, const uint32_t* iw) {
+  // fw, iw: (twiddle, companion) pairs; twiddle k at index 2k
   const size_t n = a.size();
   if (n == 1) return;
   std::vector<uint32_t> ev(n / 2), od(n / 2);
@@ -51,9 +52,9 @@ static void dft(std::vector<uint32_t>& a, uint32_t p, const uint32_t* fw, bool i
   }
   dft(ev, p, fw, inv, iw);
   dft(od, p, fw, inv, iw);
-  const size_t m = n / 2;  // omega_n^k = table[m + k] for k < m
+  const size_t m = n / 2;  // omega_n^k = twiddle m + k for k < m
   for (size_t k = 0; k < m; k++) {
-    const uint32_t w = inv ? iw[m + k] : fw[m + k];
+    const uint32_t w = inv ? iw[2 * (m + k)] : fw[2 * (m + k)];
     const uint32_t t = (uint32_t)((uint64_t)w * od[k] % p);
     a[k] = (uint32_t)(((uint64_t)ev[k] + t) % p);
     a[k + m] = (uint32_t)(((uint64_t)ev[k] + p - t) % p);
@@ -136,15 +137,15 @@ int main() {
     CHECK((uint32_t)(tab[kPinv + j] * p) == 0xffffffffu);  // -p^-1 * p = -1 mod 2^32
     const uint32_t* b = tab.data() + j * kPerPrime;
     for (int m = 1; m < kMax; m *= 2) {
-      const uint32_t w = (m >= 2) ? b[kFw + m + 1] : p - 1;  // omega_{2m}
-      CHECK(pw(w, (uint64_t)m, p) == p - 1);                 // order exactly 2m
-      if (m >= 2) CHECK(pw(w, 2, p) == (m >= 4 ? b[kFw + m / 2 + 1] : p - 1));
+      const uint32_t w = (m >= 2) ? b[kFw + 2 * (m + 1)] : p - 1;  // omega_{2m}
+      CHECK(pw(w, (uint64_t)m, p) == p - 1);                       // order exactly 2m
+      if (m >= 2) CHECK(pw(w, 2, p) == (m >= 4 ? b[kFw + 2 * (m / 2 + 1)] : p - 1));
       for (int i = 0; i < m; i++) {
-        const uint32_t f = b[kFw + m + i], g = b[kIw + m + i];
+        const uint32_t f = b[kFw + 2 * (m + i)], g = b[kIw + 2 * (m + i)];
         CHECK(f == pw(w, (uint64_t)i, p));
         CHECK((uint64_t)f * g % p == 1);
-        CHECK(b[kFws + m + i] == (uint32_t)(((uint64_t)f << 32) / p));
-        CHECK(b[kIws + m + i] == (uint32_t)(((uint64_t)g << 32) / p));
+        CHECK(b[kFw + 2 * (m + i) + 1] == (uint32_t)(((uint64_t)f << 32) / p));
+        CHECK(b[kIw + 2 * (m + i) + 1] == (uint32_t)(((uint64_t)g << 32) / p));
       }
     }
     for (int s = 0; s <= kLogMax; s++) {
@@ -171,7 +172,7 @@ int main() {
     const int j = it % 3;
     const uint32_t p = kPrime[j];
     const int idx = 1 + (int)(rng() % (kMax - 1));
-    const uint32_t w = tab[j * kPerPrime + kFw + idx], ws = tab[j * kPerPrime + kFws + idx];
+    const uint32_t w = tab[j * kPerPrime + kFw + 2 * idx], ws = tab[j * kPerPrime + kFw + 2 * idx + 1];
     const uint32_t x = (uint32_t)rng();
     const uint32_t q = (uint32_t)(((uint64_t)x * ws) >> 32);
     const uint32_t r = x * w - q * p;
