@@ -169,3 +169,41 @@ def test_transform_ragged_queue():
     Q, R, S = host_u32(q), host_u32(r), st.cpu().numpy()
     qo, ro, so, _ = oracle.divmod_ragged_u32(u_flat, u_off, u_len, v_flat, v_off, v_len, q_off, q_len, r_off, r_len)
     assert (S == so).all() and (Q == qo).all() and (R == ro).all()
+
+
+def test_transform_with_karatsuba_steps():
+    # products below the transform cutoff that are Newton-step products go
+    # through one Karatsuba level, the longer ones through the transform
+    for n, kl in [(4096, 2048), (2048, 1024), (4096, 100)]:
+        U, V = I.sweep(n, kl, 12)
+        Q, R, S, _ = run_uniform(U, V, flags=NTT, kcut=512, tcut=3000)
+        Qo, Ro, So = oracle_uniform(U, V)
+        assert_same(Q, R, S, Qo, Ro, So)
+
+
+def test_transform_serving():
+    # the serving loop on a context with the transform: one queue launch per
+    # batch; every result equals the oracle's
+    import paper_2606_06386_gb300 as mp
+
+    rnd = np.random.default_rng(11)
+    u_len = rnd.integers(1500, 4097, 24).astype(np.int32)
+    v_len = np.maximum(1, (u_len * rnd.uniform(0.2, 1.0, 24)).astype(np.int32))
+    u_flat, u_off, v_flat, v_off = I.ragged_operands(u_len, v_len, seed=72)
+    items = [(u_flat[u_off[i]:u_off[i] + u_len[i]].copy(), v_flat[v_off[i]:v_off[i] + v_len[i]].copy())
+             for i in range(len(u_len))]
+    c = mp.mpdiv_init(0, flags=NTT, transform_cutoff=1024)
+    try:
+        mp.mpdiv_serve_start(c, pool_digits=1 << 22, max_batch=8, max_inflight=2)
+        tickets = [mp.mpdiv_serve_submit(c, u, v) for u, v in items]
+        got = []
+        for t, (u, v) in zip(tickets, items):
+            rc, q, r, st = mp.mpdiv_serve_poll(c, t, len(u), len(v), timeout_us=60_000_000)
+            assert rc == mp.MPDIV_OK and st == 0
+            got.append((q, r))
+        mp.mpdiv_serve_stop(c)
+    finally:
+        mp.mpdiv_destroy(c)
+    for (u, v), (q, r) in zip(items, got):
+        qo, ro, _ = oracle.divmod_u32(u, v, len(u), len(v))
+        assert (q == qo).all() and (r == ro).all()
