@@ -383,6 +383,34 @@ __device__ inline void load_global(const Blk& b, uint32_t* dst, int len, F src) 
   b.sync();
 }
 
+// Whether operands and results move between global and shared memory as
+// 128-bit vectors where their alignment allows (load_digits, store_digits).
+// The translation units of one- and two-warp kernels define it to 0: there the
+// vector paths' extra registers raised spills and cost 2.5 % at 2^15 bits.
+#ifndef MP_VECTOR_IO
+#define MP_VECTOR_IO 1
+#endif
+
+// Digits g[0..len) of global memory to dst[0..len) in shared memory, then a
+// group barrier. Where g's first 16-byte boundary falls on one of dst's, the
+// body between the boundaries moves as coalesced 128-bit loads and stores
+// (thread t the t-th 4-digit chunk); the head before it and the tail after it
+// go digit by digit. Nothing at or beyond g[len] is read.
+__device__ inline void load_digits(const Blk& b, uint32_t* dst, int len, const uint32_t* g) {
+  const int head = min(len, (int)(((16u - ((uint32_t)(uintptr_t)g & 15u)) & 15u) >> 2));
+  if (!MP_VECTOR_IO || (((uint32_t)(uintptr_t)(dst + head)) & 15u) != 0u) {
+    load_global(b, dst, len, [&](int i) { return g[i]; });
+    return;
+  }
+  const int nv = (len - head) >> 2;
+  const uint4* gv = reinterpret_cast<const uint4*>(g + head);
+  uint4* dv = reinterpret_cast<uint4*>(dst + head);
+  for (int c = b.tid; c < nv; c += b.nt) dv[c] = gv[c];
+  for (int i = b.tid; i < head; i += b.nt) dst[i] = g[i];
+  for (int i = head + 4 * nv + b.tid; i < len; i += b.nt) dst[i] = g[i];
+  b.sync();
+}
+
 // ---------------------------------------------------------------- multiply
 __device__ __forceinline__ void mac3(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t a, uint32_t bb) {
   asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"

@@ -82,10 +82,14 @@ __host__ __device__ __forceinline__ int cap_ov(int capP) { return ov_words(capP)
 // strip width with clipped products, PAD with full ones.
 __host__ __device__ __forceinline__ int layout_pad(bool clip, int tcols) { return clip ? pad_for(tcols) : PAD; }
 
+// Buffer starts are rounded up to 16 bytes (four digits), so that digits move
+// between global and shared memory as 128-bit vectors.
+__host__ __device__ __forceinline__ int align4(int words) { return (words + 3) & ~3; }
+
 __host__ __device__ __forceinline__ int layout_words(int h, int kl, bool clip, int pad) {
   const int capP = cap_p(h, kl, clip);
   const int capOV = cap_ov(capP);
-  return 5 * pad + kl + (h - kl + 9) + (kl + 32) + (h - kl + 16) + capP + capOV;
+  return 5 * pad + kl + (h - kl + 9) + (kl + 32) + (h - kl + 16) + capP + capOV + 5 * 3;
 }
 
 // Words of dynamic shared memory that cover every item with at most h digits
@@ -102,15 +106,15 @@ __device__ __forceinline__ Layout make_layout(uint32_t* sm, int h, int kl, bool 
   L.capR = h - kl + 16;
   L.capP = cap_p(h, kl, clip);
   L.capOV = cap_ov(L.capP);
-  int off = pad;
+  int off = align4(pad);
   L.V = sm + off;
-  off += L.capV + pad;
+  off = align4(off + L.capV + pad);
   L.W = sm + off;
-  off += L.capW + pad;
+  off = align4(off + L.capW + pad);
   L.X = sm + off;
-  off += L.capX + pad;
+  off = align4(off + L.capX + pad);
   L.R = sm + off;
-  off += L.capR + pad;
+  off = align4(off + L.capR + pad);
   L.P = sm + off;
   off += L.capP;
   L.OV = sm + off;
@@ -368,9 +372,31 @@ __device__ __forceinline__ int shinv(const Blk& b, const Layout& L, int h, int k
 }
 
 // Store digits [0, n) of S to global g[0..cap), zero-padded; S digits at or
-// above n are treated as zero.
+// above n are treated as zero and not read. Where g's first 16-byte boundary
+// falls on one of S's, the body moves as coalesced 128-bit vectors.
 __device__ __forceinline__ void store_digits(const Blk& b, uint32_t* g, int cap, const uint32_t* S, int n) {
-  for (int i = b.tid; i < cap; i += b.nt) g[i] = (i < n) ? S[i] : 0u;
+  const int head = min(cap, (int)(((16u - ((uint32_t)(uintptr_t)g & 15u)) & 15u) >> 2));
+  if (!MP_VECTOR_IO || S == nullptr || (((uint32_t)(uintptr_t)(S + head)) & 15u) != 0u) {
+    for (int i = b.tid; i < cap; i += b.nt) g[i] = (i < n) ? S[i] : 0u;
+    return;
+  }
+  const int nv = (cap - head) >> 2;
+  uint4* gv = reinterpret_cast<uint4*>(g + head);
+  for (int c = b.tid; c < nv; c += b.nt) {
+    const int i = head + 4 * c;
+    uint4 v;
+    if (i + 3 < n) {
+      v = *reinterpret_cast<const uint4*>(S + i);
+    } else {
+      v.x = i < n ? S[i] : 0u;
+      v.y = i + 1 < n ? S[i + 1] : 0u;
+      v.z = i + 2 < n ? S[i + 2] : 0u;
+      v.w = i + 3 < n ? S[i + 3] : 0u;
+    }
+    gv[c] = v;
+  }
+  for (int i = b.tid; i < head; i += b.nt) g[i] = (i < n) ? S[i] : 0u;
+  for (int i = head + 4 * nv + b.tid; i < cap; i += b.nt) g[i] = (i < n) ? S[i] : 0u;
 }
 
 // The whole of Algorithm 3 for one item. Returns a status; q and r are always
@@ -411,7 +437,7 @@ __device__ __forceinline__ int div_item(const Blk& b, uint32_t* sm, int smem_wor
   if (NTT && ntt_tab != nullptr && !clip) layout_ntt_scratch(L, sm, smem_words, ntt_tab, ntt_cut);
   for (int i = b.tid; i < L.total; i += b.nt) sm[i] = 0u;
   b.sync();
-  load_global(b, L.V, kl, [&](int i) { return gv[i]; });
+  load_digits(b, L.V, kl, gv);
   int lw = 0, iters = 0;
   int st = shinv<NTT>(b, L, h, kl, &lw, &iters, clip);
   *iters_out = iters;
@@ -430,7 +456,7 @@ __device__ __forceinline__ int div_item(const Blk& b, uint32_t* sm, int smem_wor
   uint32_t* U = L.U;
   uint32_t* P = L.P;
   const bool full = !clip;
-  load_global(b, U, h, [&](int i) { return gu[i]; });
+  load_digits(b, U, h, gu);
   const int np = h + lw;
   // full: the exact product; clipped (Section 5's clipped products): only the
   // digit products at columns h - QGUARD and up (stored from that column up),

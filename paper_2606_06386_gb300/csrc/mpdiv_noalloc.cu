@@ -14,6 +14,7 @@
 // head and the bucket counters, then builds the order, then runs the division
 // kernel. Two calls whose work overlaps on the GPU (for instance on two
 // streams) race on the array and corrupt each other's queue; serialise them.
+#define MP_VECTOR_IO 0  // ragged offsets are rarely 16-byte aligned; scalar staging spills less
 #include <algorithm>
 #include <mutex>
 
