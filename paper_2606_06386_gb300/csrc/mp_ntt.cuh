@@ -1,6 +1,7 @@
-// Exact products by number-theoretic transforms: the FFT-based multiplication
-// that the paper leaves to future work for larger sizes (Sections 5 and 6),
-// with the transform length chosen per product, so that it follows the
+// Exact products by number-theoretic transforms: the NTT/FFT multiplication
+// that the paper names for larger sizes (Section 3.4) and leaves to future
+// work, integrated with the changing precisions of the division (Section 6):
+// the transform length is chosen per product, so that it follows the
 // precision as the Newton iteration doubles it.
 //
 // The digits of X and Y are the coefficients of two polynomials in B. Their
