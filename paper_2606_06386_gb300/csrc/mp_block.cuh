@@ -383,19 +383,21 @@ __device__ inline void load_global(const Blk& b, uint32_t* dst, int len, F src) 
   b.sync();
 }
 
-// Whether operands and results move between global and shared memory as
-// 128-bit vectors where their alignment allows (load_digits, store_digits).
-// The translation units of one- and two-warp kernels define it to 0: there the
-// vector paths' extra registers raised spills and cost 2.5 % at 2^15 bits.
+// Whether operands and results move between global and shared memory in
+// 16-byte units where their alignment allows (load_digits, store_digits). The
+// translation units of the one- and two-warp kernels and of the ragged queue
+// kernel define it to 0: there the vector paths' registers raised spills
+// (2^15 bits: -2.5 %), and ragged offsets are rarely aligned.
 #ifndef MP_VECTOR_IO
 #define MP_VECTOR_IO 1
 #endif
 
 // Digits g[0..len) of global memory to dst[0..len) in shared memory, then a
 // group barrier. Where g's first 16-byte boundary falls on one of dst's, the
-// body between the boundaries moves as coalesced 128-bit loads and stores
-// (thread t the t-th 4-digit chunk); the head before it and the tail after it
-// go digit by digit. Nothing at or beyond g[len] is read.
+// body between the boundaries is staged by asynchronous 16-byte copies
+// (cp.async, global to shared without registers; thread t the t-th 4-digit
+// chunk, coalesced), waited for before the barrier; the head before it and
+// the tail after it go digit by digit. Nothing at or beyond g[len] is read.
 __device__ inline void load_digits(const Blk& b, uint32_t* dst, int len, const uint32_t* g) {
   const int head = min(len, (int)(((16u - ((uint32_t)(uintptr_t)g & 15u)) & 15u) >> 2));
   if (!MP_VECTOR_IO || (((uint32_t)(uintptr_t)(dst + head)) & 15u) != 0u) {
@@ -403,11 +405,14 @@ __device__ inline void load_digits(const Blk& b, uint32_t* dst, int len, const u
     return;
   }
   const int nv = (len - head) >> 2;
-  const uint4* gv = reinterpret_cast<const uint4*>(g + head);
-  uint4* dv = reinterpret_cast<uint4*>(dst + head);
-  for (int c = b.tid; c < nv; c += b.nt) dv[c] = gv[c];
+  const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(dst + head);
+  const uint32_t* g0 = g + head;
+  for (int c = b.tid; c < nv; c += b.nt)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s0 + 16u * (uint32_t)c), "l"(g0 + 4 * c)
+                 : "memory");
   for (int i = b.tid; i < head; i += b.nt) dst[i] = g[i];
   for (int i = head + 4 * nv + b.tid; i < len; i += b.nt) dst[i] = g[i];
+  asm volatile("cp.async.wait_all;" ::: "memory");
   b.sync();
 }
 

@@ -3,7 +3,7 @@
 // group barrier spans two warps (a separate translation unit, so that the
 // block sizes build in parallel).
 #define MP_MUL_NOINLINE 1  // the strip multiply as one called copy (see mp_block.cuh)
-#define MP_VECTOR_IO 0     // digit-by-digit global loads and stores (see mp_block.cuh)
+#define MP_VECTOR_IO 0  // digit-by-digit operand loads and result stores (see mp_block.cuh)
 #include "mp_kernels.cuh"
 #include "mpdiv_kernels.h"
 

@@ -14,7 +14,7 @@
 // head and the bucket counters, then builds the order, then runs the division
 // kernel. Two calls whose work overlaps on the GPU (for instance on two
 // streams) race on the array and corrupt each other's queue; serialise them.
-#define MP_VECTOR_IO 0  // ragged offsets are rarely 16-byte aligned; scalar staging spills less
+#define MP_VECTOR_IO 0  // digit-by-digit operand loads and result stores (see mp_block.cuh)
 #include <algorithm>
 #include <mutex>
 

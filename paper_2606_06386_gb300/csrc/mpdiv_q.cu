@@ -1,7 +1,7 @@
 // The one-block-per-item queue kernel and the shifted-inverse test entry, both
 // in 16-warp blocks, in a translation unit of their own so that they build in
 // parallel with the rest.
-#define MP_VECTOR_IO 0  // ragged offsets are rarely 16-byte aligned; scalar staging spills less
+#define MP_VECTOR_IO 0  // digit-by-digit operand loads and result stores (see mp_block.cuh)
 #include "mp_kernels.cuh"
 #include "mpdiv_kernels.h"
 
