@@ -310,6 +310,10 @@ def run_sweep(args, dev, dist, rank, ws):
     prod_big = sizes[big]["products"]
     achieved = prod_big / (per_size_ms[big] / 1e3) / 1e12
     peak = SM_COUNT_GB300 * PRODUCTS_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    # the multiply pipe measured on this GPU (after the timed regions): the
+    # strip multiply's digit-product idiom in registers, and plain multiply-adds
+    mac3_rate, _ = mp.mpdiv_measure_peak(ctx, 0)
+    imad_rate, _ = mp.mpdiv_measure_peak(ctx, 1)
     per_size = {}
     for i, d in enumerate(sizes):
         bits = 32 * d["n"]
@@ -344,7 +348,11 @@ def run_sweep(args, dev, dist, rank, ws):
                      "peak_basis": "derived: 152 SMs x 32 digit products/clk/SM (64 IMAD/clk/SM, lo+hi per "
                                    "32x32->64 product) x 2070 MHz max SM clock",
                      "work_basis": "algorithmic 32x32-bit digit products of Algorithms 1-3 at operand precision, "
-                                   "counted by the kernel"},
+                                   "counted by the kernel",
+                     "measured": {"digit_products_Tps": mac3_rate / 1e12, "imad_Tops": imad_rate / 1e12,
+                                  "frac_of_measured_idiom": achieved / (mac3_rate / 1e12),
+                                  "basis": "mpdiv_measure_peak on this GPU: in-register mad.lo.cc/madc.hi.cc/addc "
+                                           "digit products and mad.lo.u32, 8 blocks x 256 threads per SM"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": len(sizes) * K,
     }

@@ -108,6 +108,7 @@ _SIGS = {
     "mpdiv_autotune": (ctypes.c_int, [_P, _I32, _I32, _I32]),
     "mpdiv_debug_primitive": (ctypes.c_int, [_P, _I32, _I64, _P, _I32, _P, _I32, _I32, _P, _I32, _P, _I32, _P]),
     "mpdiv_mul_batch": (ctypes.c_int, [_P, _I64, _P, _P, _I32, _I64, _P, _I64, _P]),
+    "mpdiv_measure_peak": (ctypes.c_int, [_P, _I32, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "mpdiv_tuning": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "mpdiv_serve_start": (ctypes.c_int, [_P, ctypes.POINTER(mpdiv_serve_config)]),
     "mpdiv_serve_submit": (ctypes.c_int, [_P, _P, _I32, _P, _I32, ctypes.POINTER(_U64)]),
@@ -275,6 +276,14 @@ def mpdiv_mul_batch(ctx, u, v, out, stream=None) -> None:
         raise ValueError("shape mismatch")
     _check(ctx, lib().mpdiv_mul_batch(ctx, u.shape[0], _ptr(u), _ptr(v), u.shape[1], u.stride(0), _ptr(out),
                                       out.stride(0), _stream(stream)))
+
+
+def mpdiv_measure_peak(ctx, kind: int = 0, iters: int = 0):
+    """(rate per second, ms) of the multiply-pipe microbenchmark: kind 0 digit
+    products of the strip multiply's idiom, kind 1 32-bit multiply-adds."""
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().mpdiv_measure_peak(ctx, kind, iters, ctypes.byref(rate), ctypes.byref(ms)))
+    return rate.value, ms.value
 
 
 def mpdiv_autotune(ctx, u_limbs: int, v_limbs: int, n_items: int) -> int:

@@ -658,6 +658,44 @@ extern "C" int mpdiv_tuning(mpdiv_ctx* ctx, int32_t u_limbs, int32_t* warps, int
   return MPDIV_OK;
 }
 
+// ------------------------------------------------------------------ multiply-pipe microbenchmark
+extern "C" int mpdiv_measure_peak(mpdiv_ctx* ctx, int32_t kind, int32_t iters, double* rate, double* ms) {
+  if (!ctx) return MPDIV_EINVAL;
+  if ((kind != 0 && kind != 1) || iters < 0 || !rate || !ms)
+    return mpdiv_set_error(ctx, MPDIV_EINVAL, "bad microbenchmark arguments");
+  if (iters == 0) iters = 4096;
+  cudaSetDevice(ctx->device);
+  int per_round = 0;
+  void* k = mp_kernel_peak(kind, &per_round);
+  const int threads = 256, blocks = 8 * ctx->num_sms;
+  uint32_t* out = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = mpdiv_cuda_check(ctx, cudaMalloc(&out, sizeof(uint32_t) * blocks * threads), "cudaMalloc(microbenchmark)");
+  if (rc == MPDIV_OK) rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "cudaStreamCreate");
+  if (rc == MPDIV_OK) rc = mpdiv_cuda_check(ctx, cudaEventCreate(&e0), "cudaEventCreate");
+  if (rc == MPDIV_OK) rc = mpdiv_cuda_check(ctx, cudaEventCreate(&e1), "cudaEventCreate");
+  void* args[] = {&out, &iters};
+  if (rc == MPDIV_OK)
+    rc = mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, 0, s), "microbenchmark warm-up");
+  if (rc == MPDIV_OK) rc = mpdiv_cuda_check(ctx, cudaEventRecord(e0, s), "cudaEventRecord");
+  if (rc == MPDIV_OK)
+    rc = mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, 0, s), "microbenchmark launch");
+  if (rc == MPDIV_OK) rc = mpdiv_cuda_check(ctx, cudaEventRecord(e1, s), "cudaEventRecord");
+  if (rc == MPDIV_OK) rc = mpdiv_cuda_check(ctx, cudaEventSynchronize(e1), "microbenchmark");
+  float t = 0.f;
+  if (rc == MPDIV_OK) rc = mpdiv_cuda_check(ctx, cudaEventElapsedTime(&t, e0, e1), "cudaEventElapsedTime");
+  if (rc == MPDIV_OK) {
+    *ms = t;
+    *rate = (double)blocks * threads * iters * per_round / (t * 1e-3);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  if (out) cudaFree(out);
+  return rc;
+}
+
 // ------------------------------------------------------------------ multiplication (cost unit)
 extern "C" int mpdiv_mul_batch(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* u, const uint32_t* v, int32_t n_limbs,
                                int64_t stride, uint32_t* out, int64_t out_stride, void* stream) {

@@ -228,3 +228,17 @@ def test_strip_fold_carry_ripple(cols):
     O = host_u32(out)
     want = (oracle.to_int(u) * oracle.to_int(v)) % (B**n)
     assert oracle.to_int(O[0]) == want and oracle.to_int(O[1]) == want
+
+
+def test_multiply_pipe_microbenchmark():
+    # the roofline's measured ceiling: digit products of the strip multiply's
+    # idiom and plain 32-bit multiply-adds on every SM; each digit product
+    # takes two multiply results (low and high word)
+    import paper_2606_06386_gb300 as mp
+
+    c = ctx()
+    prod, ms0 = mp.mpdiv_measure_peak(c, 0, 1024)
+    imad, ms1 = mp.mpdiv_measure_peak(c, 1, 1024)
+    assert ms0 > 0 and ms1 > 0
+    assert 0 < prod < imad
+    assert imad < 2 * 64 * 152 * 2.1e9  # far below nonsense: 64 multiply results/clk/SM at most twice over
