@@ -81,8 +81,7 @@ struct RaggedLaunch {
   const int32_t *u_len_host, *v_len_host;
   const int32_t* order;  // device order array (nullptr: computed and cached here)
   int32_t* head;         // device queue head (nullptr: the context's)
-  int64_t n;
-  int warps;       // unused: the persistent kernel takes its shape per size class, the queue kernel 16 warps
+  int64_t n;       // the persistent kernel takes its shape per size class, the queue kernel 16 warps
   bool use_graph;  // capture/replay as a CUDA graph
   bool grid_items; // one block per item instead of one wave of resident blocks
   bool split;      // the self-splitting persistent kernel
