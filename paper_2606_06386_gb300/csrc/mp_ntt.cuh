@@ -66,103 +66,189 @@ __device__ __forceinline__ uint32_t mod_mont(uint32_t x, uint32_t y, uint32_t p,
   return u >= p ? u - p : u;
 }
 
-// Two stages of the forward transform on the four residues z[0], z[h], z[2h],
-// z[3h] (a radix-4 pass): the stage of half-length m = 2h with twiddles w1 =
-// omega_{2m}^i and w2 = omega_{2m}^(i+h), then the stage of half-length h with
-// w3 = omega_m^i; (w, ws) pairs are a constant and its Shoup companion.
-__device__ __forceinline__ void dif4(uint32_t* z, int h, uint32_t p, uint32_t w1, uint32_t w1s, uint32_t w2,
-                                     uint32_t w2s, uint32_t w3, uint32_t w3s) {
-  const uint32_t a0 = z[0], a1 = z[h], a2 = z[2 * h], a3 = z[3 * h];
-  const uint32_t b0 = mod_add(a0, a2, p), b2 = mod_shoup(a0 + p - a2, w1, w1s, p);
-  const uint32_t b1 = mod_add(a1, a3, p), b3 = mod_shoup(a1 + p - a3, w2, w2s, p);
-  z[0] = mod_add(b0, b1, p);
-  z[h] = mod_shoup(b0 + p - b1, w3, w3s, p);
-  z[2 * h] = mod_add(b2, b3, p);
-  z[3 * h] = mod_shoup(b2 + p - b3, w3, w3s, p);
+// Two stages of the forward transform on four residues a0..a3 (a radix-4
+// butterfly): the stage of half-length m = 2h on (a0, a2) with w1 =
+// omega_{2m}^i and on (a1, a3) with w2 = omega_{2m}^(i+h), then the stage of
+// half-length h on (a0, a1) and (a2, a3) with w3 = omega_m^i. Each uint2 is a
+// constant and its Shoup companion.
+__device__ __forceinline__ void dif4v(uint32_t& a0, uint32_t& a1, uint32_t& a2, uint32_t& a3, uint32_t p, uint2 w1,
+                                      uint2 w2, uint2 w3) {
+  const uint32_t b0 = mod_add(a0, a2, p), b2 = mod_shoup(a0 + p - a2, w1.x, w1.y, p);
+  const uint32_t b1 = mod_add(a1, a3, p), b3 = mod_shoup(a1 + p - a3, w2.x, w2.y, p);
+  a0 = mod_add(b0, b1, p);
+  a1 = mod_shoup(b0 + p - b1, w3.x, w3.y, p);
+  a2 = mod_add(b2, b3, p);
+  a3 = mod_shoup(b2 + p - b3, w3.x, w3.y, p);
 }
 
-// Two stages of the inverse transform on z[0], z[h], z[2h], z[3h]: the stage
-// of half-length h with u1 = omega_{2h}^-i on both pairs, then the stage of
-// half-length 2h with u2 = omega_{4h}^-i and u3 = omega_{4h}^-(i+h).
-__device__ __forceinline__ void dit4(uint32_t* z, int h, uint32_t p, uint32_t u1, uint32_t u1s, uint32_t u2,
-                                     uint32_t u2s, uint32_t u3, uint32_t u3s) {
-  const uint32_t a0 = z[0], a1 = z[h], a2 = z[2 * h], a3 = z[3 * h];
-  uint32_t t = mod_shoup(a1, u1, u1s, p);
+// Two stages of the inverse transform on a0..a3: the stage of half-length h
+// on (a0, a1) and (a2, a3) with u1 = omega_{2h}^-i, then the stage of
+// half-length 2h on (a0, a2) with u2 = omega_{4h}^-i and on (a1, a3) with
+// u3 = omega_{4h}^-(i+h).
+__device__ __forceinline__ void dit4v(uint32_t& a0, uint32_t& a1, uint32_t& a2, uint32_t& a3, uint32_t p, uint2 u1,
+                                      uint2 u2, uint2 u3) {
+  uint32_t t = mod_shoup(a1, u1.x, u1.y, p);
   const uint32_t b0 = mod_add(a0, t, p), b1 = mod_sub(a0, t, p);
-  t = mod_shoup(a3, u1, u1s, p);
+  t = mod_shoup(a3, u1.x, u1.y, p);
   const uint32_t b2 = mod_add(a2, t, p), b3 = mod_sub(a2, t, p);
-  t = mod_shoup(b2, u2, u2s, p);
-  z[0] = mod_add(b0, t, p);
-  z[2 * h] = mod_sub(b0, t, p);
-  t = mod_shoup(b3, u3, u3s, p);
-  z[h] = mod_add(b1, t, p);
-  z[3 * h] = mod_sub(b1, t, p);
+  t = mod_shoup(b2, u2.x, u2.y, p);
+  a0 = mod_add(b0, t, p);
+  a2 = mod_sub(b0, t, p);
+  t = mod_shoup(b3, u3.x, u3.y, p);
+  a1 = mod_add(b1, t, p);
+  a3 = mod_sub(b1, t, p);
 }
 
-// The stage of half-length 1 (twiddle 1) on the pairs (z[2g], z[2g+1]),
-// read and written as 8-byte words (Z 8-byte aligned).
-__device__ __forceinline__ void ntt_pairs(const Blk& b, uint32_t* Z, int half, uint32_t p) {
-  uint2* Z2 = reinterpret_cast<uint2*>(Z);
-  for (int g = b.tid; g < half; g += b.nt) {
-    const uint2 v = Z2[g];
-    Z2[g] = make_uint2(mod_add(v.x, v.y, p), mod_sub(v.x, v.y, p));
+// dif4v / dit4v on z[0], z[h], z[2h], z[3h] in shared memory.
+__device__ __forceinline__ void dif4(uint32_t* z, int h, uint32_t p, uint2 w1, uint2 w2, uint2 w3) {
+  uint32_t a0 = z[0], a1 = z[h], a2 = z[2 * h], a3 = z[3 * h];
+  dif4v(a0, a1, a2, a3, p, w1, w2, w3);
+  z[0] = a0;
+  z[h] = a1;
+  z[2 * h] = a2;
+  z[3 * h] = a3;
+}
+__device__ __forceinline__ void dit4(uint32_t* z, int h, uint32_t p, uint2 u1, uint2 u2, uint2 u3) {
+  uint32_t a0 = z[0], a1 = z[h], a2 = z[2 * h], a3 = z[3 * h];
+  dit4v(a0, a1, a2, a3, p, u1, u2, u3);
+  z[0] = a0;
+  z[h] = a1;
+  z[2 * h] = a2;
+  z[3 * h] = a3;
+}
+
+// One radix-4 forward pass over stages lm and lm - 1 (lm >= 1) of Z0 and Z1,
+// or one inverse pass over stages lm and lm + 1 of Z, each thread a group of
+// four residues at stride h.
+__device__ __forceinline__ void dif_pass2(const Blk& b, uint32_t* Z0, uint32_t* Z1, int logn, int lm, uint32_t p,
+                                          const uint2* fw) {
+  const int m = 1 << lm, h = m >> 1, quarter = (1 << logn) >> 2;
+#pragma unroll 2
+  for (int g = b.tid; g < quarter; g += b.nt) {
+    const int i = g & (h - 1);
+    const int base = ((g >> (lm - 1)) << (lm + 1)) + i;
+    const uint2 w1 = __ldg(fw + m + i), w2 = __ldg(fw + m + h + i), w3 = __ldg(fw + h + i);
+    dif4(Z0 + base, h, p, w1, w2, w3);
+    dif4(Z1 + base, h, p, w1, w2, w3);
+  }
+}
+__device__ __forceinline__ void dit_pass(const Blk& b, uint32_t* Z, int logn, int lm, uint32_t p, const uint2* iw) {
+  const int h = 1 << lm, m = 2 * h, quarter = (1 << logn) >> 2;
+#pragma unroll 2
+  for (int g = b.tid; g < quarter; g += b.nt) {
+    const int i = g & (h - 1);
+    const int base = ((g >> lm) << (lm + 2)) + i;
+    dit4(Z + base, h, p, __ldg(iw + h + i), __ldg(iw + m + i), __ldg(iw + m + h + i));
   }
 }
 
-// Forward transforms of Z0 and Z1 (2^logn residues each) modulo prime j:
-// radix-4 passes from the longest stage down, then the last radix-2 stage
-// when logn is odd. One barrier per pass.
+// Z = N 2^-32 (X * Y) modulo prime j, the cyclic convolution of length
+// N = 2^logn (logn >= 3, nx, ny <= N) through the transforms: the forward
+// transforms of X and Y (into Z and T) run from the longest stage down and
+// read the operands' digits, reduced, in their first pass; the last forward
+// pass, the pointwise Montgomery product and the first inverse pass are one
+// pass over contiguous groups (4 residues when logn is even, 2 when odd), read
+// and written as vectors; the remaining inverse passes run upward. One barrier
+// per pass.
 template <bool WHOLE>
-__device__ __forceinline__ void ntt_forward2(const Blk& b, uint32_t* Z0, uint32_t* Z1, int logn, const uint32_t* tab,
-                                             int j) {
-  const uint32_t p = __ldg(tab + mp_ntt::kP + j);
+__device__ __forceinline__ void ntt_conv_prime(const Blk& b, uint32_t* Z, uint32_t* T, const uint32_t* X, int nx,
+                                               const uint32_t* Y, int ny, int logn, const uint32_t* tab, int j) {
+  const uint32_t p = __ldg(tab + mp_ntt::kP + j), pinv = __ldg(tab + mp_ntt::kPinv + j);
   const uint2* fw = reinterpret_cast<const uint2*>(tab + j * mp_ntt::kPerPrime + mp_ntt::kFw);
-  const int quarter = (1 << logn) >> 2;
-  int lm = logn - 1;
-  for (; lm >= 1; lm -= 2) {
-    const int m = 1 << lm, h = m >> 1;
+  const uint2* iw = reinterpret_cast<const uint2*>(tab + j * mp_ntt::kPerPrime + mp_ntt::kIw);
+  const int N = 1 << logn, quarter = N >> 2;
+  {  // stages logn - 1 and logn - 2 from the operands (one block of N: base = i = g)
+    const int m = N >> 1, h = quarter;
 #pragma unroll 2
     for (int g = b.tid; g < quarter; g += b.nt) {
-      const int i = g & (h - 1);
-      const int base = ((g >> (lm - 1)) << (lm + 1)) + i;
-      const uint2 w1 = __ldg(fw + m + i), w2 = __ldg(fw + m + h + i), w3 = __ldg(fw + h + i);
-      dif4(Z0 + base, h, p, w1.x, w1.y, w2.x, w2.y, w3.x, w3.y);
-      dif4(Z1 + base, h, p, w1.x, w1.y, w2.x, w2.y, w3.x, w3.y);
+      const uint2 w1 = __ldg(fw + m + g), w2 = __ldg(fw + m + h + g), w3 = __ldg(fw + h + g);
+      uint32_t x0 = g < nx ? mod_red(X[g], p) : 0u, x1 = g + h < nx ? mod_red(X[g + h], p) : 0u;
+      uint32_t x2 = g + 2 * h < nx ? mod_red(X[g + 2 * h], p) : 0u;
+      uint32_t x3 = g + 3 * h < nx ? mod_red(X[g + 3 * h], p) : 0u;
+      dif4v(x0, x1, x2, x3, p, w1, w2, w3);
+      Z[g] = x0;
+      Z[g + h] = x1;
+      Z[g + 2 * h] = x2;
+      Z[g + 3 * h] = x3;
+      uint32_t y0 = g < ny ? mod_red(Y[g], p) : 0u, y1 = g + h < ny ? mod_red(Y[g + h], p) : 0u;
+      uint32_t y2 = g + 2 * h < ny ? mod_red(Y[g + 2 * h], p) : 0u;
+      uint32_t y3 = g + 3 * h < ny ? mod_red(Y[g + 3 * h], p) : 0u;
+      dif4v(y0, y1, y2, y3, p, w1, w2, w3);
+      T[g] = y0;
+      T[g + h] = y1;
+      T[g + 2 * h] = y2;
+      T[g + 3 * h] = y3;
     }
     group_sync<WHOLE>(b);
   }
-  if (lm == 0) {
-    ntt_pairs(b, Z0, 1 << (logn - 1), p);
-    ntt_pairs(b, Z1, 1 << (logn - 1), p);
+  int lm = logn - 3;
+  for (; lm >= 2; lm -= 2) {
+    dif_pass2(b, Z, T, logn, lm, p, fw);
+    group_sync<WHOLE>(b);
+  }
+  if (lm == 1) {  // stages 1 and 0 forward, pointwise, stages 0 and 1 inverse: 4 contiguous residues
+    const uint2 w1 = __ldg(fw + 2), w2 = __ldg(fw + 3), w3 = __ldg(fw + 1);
+    const uint2 u1 = __ldg(iw + 1), u2 = __ldg(iw + 2), u3 = __ldg(iw + 3);
+    uint4* Z4 = reinterpret_cast<uint4*>(Z);
+    const uint4* T4 = reinterpret_cast<const uint4*>(T);
+    for (int g = b.tid; g < quarter; g += b.nt) {
+      uint4 z = Z4[g], t = T4[g];
+      dif4v(z.x, z.y, z.z, z.w, p, w1, w2, w3);
+      dif4v(t.x, t.y, t.z, t.w, p, w1, w2, w3);
+      z.x = mod_mont(z.x, t.x, p, pinv);
+      z.y = mod_mont(z.y, t.y, p, pinv);
+      z.z = mod_mont(z.z, t.z, p, pinv);
+      z.w = mod_mont(z.w, t.w, p, pinv);
+      dit4v(z.x, z.y, z.z, z.w, p, u1, u2, u3);
+      Z4[g] = z;
+    }
+  } else {  // stage 0 forward, pointwise, stage 0 inverse: pairs (twiddle 1)
+    uint2* Z2 = reinterpret_cast<uint2*>(Z);
+    const uint2* T2 = reinterpret_cast<const uint2*>(T);
+    for (int g = b.tid; g < (N >> 1); g += b.nt) {
+      const uint2 z = Z2[g], t = T2[g];
+      const uint32_t y0 = mod_mont(mod_add(z.x, z.y, p), mod_add(t.x, t.y, p), p, pinv);
+      const uint32_t y1 = mod_mont(mod_sub(z.x, z.y, p), mod_sub(t.x, t.y, p), p, pinv);
+      Z2[g] = make_uint2(mod_add(y0, y1, p), mod_sub(y0, y1, p));
+    }
+  }
+  group_sync<WHOLE>(b);
+  for (lm = (logn & 1) ? 1 : 2; lm < logn; lm += 2) {
+    dit_pass(b, Z, logn, lm, p, iw);
     group_sync<WHOLE>(b);
   }
 }
 
-// Inverse transform of Z (bit-reversed order in, natural order out, times N):
-// the radix-2 stage of half-length 1 first when logn is odd, then radix-4
-// passes upward.
+// The same for N = 2 or 4 (logn 1 or 2): a load pass, then the stages one by
+// one on the residues in shared memory.
 template <bool WHOLE>
-__device__ __forceinline__ void ntt_inverse(const Blk& b, uint32_t* Z, int logn, const uint32_t* tab, int j) {
-  const uint32_t p = __ldg(tab + mp_ntt::kP + j);
+__device__ __forceinline__ void ntt_conv_prime_small(const Blk& b, uint32_t* Z, uint32_t* T, const uint32_t* X,
+                                                     int nx, const uint32_t* Y, int ny, int logn,
+                                                     const uint32_t* tab, int j) {
+  const uint32_t p = __ldg(tab + mp_ntt::kP + j), pinv = __ldg(tab + mp_ntt::kPinv + j);
+  const uint2* fw = reinterpret_cast<const uint2*>(tab + j * mp_ntt::kPerPrime + mp_ntt::kFw);
   const uint2* iw = reinterpret_cast<const uint2*>(tab + j * mp_ntt::kPerPrime + mp_ntt::kIw);
-  const int quarter = (1 << logn) >> 2;
-  int lm = 0;
-  if (logn & 1) {
-    ntt_pairs(b, Z, 1 << (logn - 1), p);
-    group_sync<WHOLE>(b);
-    lm = 1;
-  }
-  for (; lm < logn; lm += 2) {
-    const int h = 1 << lm, m = 2 * h;
-#pragma unroll 2
-    for (int g = b.tid; g < quarter; g += b.nt) {
-      const int i = g & (h - 1);
-      const int base = ((g >> lm) << (lm + 2)) + i;
-      const uint2 u1 = __ldg(iw + h + i), u2 = __ldg(iw + m + i), u3 = __ldg(iw + m + h + i);
-      dit4(Z + base, h, p, u1.x, u1.y, u2.x, u2.y, u3.x, u3.y);
+  const int N = 1 << logn;
+  if (b.tid == 0) {  // at most 4 residues: one thread
+    uint32_t z[4], t[4];
+    for (int i = 0; i < N; i++) {
+      z[i] = i < nx ? mod_red(X[i], p) : 0u;
+      t[i] = i < ny ? mod_red(Y[i], p) : 0u;
     }
-    group_sync<WHOLE>(b);
+    if (logn == 2) {
+      dif4v(z[0], z[1], z[2], z[3], p, __ldg(fw + 2), __ldg(fw + 3), __ldg(fw + 1));
+      dif4v(t[0], t[1], t[2], t[3], p, __ldg(fw + 2), __ldg(fw + 3), __ldg(fw + 1));
+      for (int i = 0; i < 4; i++) z[i] = mod_mont(z[i], t[i], p, pinv);
+      dit4v(z[0], z[1], z[2], z[3], p, __ldg(iw + 1), __ldg(iw + 2), __ldg(iw + 3));
+    } else {
+      const uint32_t y0 = mod_mont(mod_add(z[0], z[1], p), mod_add(t[0], t[1], p), p, pinv);
+      const uint32_t y1 = mod_mont(mod_sub(z[0], z[1], p), mod_sub(t[0], t[1], p), p, pinv);
+      z[0] = mod_add(y0, y1, p);
+      z[1] = mod_sub(y0, y1, p);
+    }
+    for (int i = 0; i < N; i++) Z[i] = z[i];
   }
+  group_sync<WHOLE>(b);
 }
 
 // The product below is a called function (one copy per group kind serves
@@ -195,17 +281,10 @@ static __device__ __noinline__ int ntt_mul_group(int tid, int nw, int bar, int* 
   const int logn = ntt_log(n), N = 1 << logn;
   uint32_t* T = S + 3 * N;
   for (int j = 0; j < 3; j++) {
-    const uint32_t p = __ldg(tab + mp_ntt::kP + j), pinv = __ldg(tab + mp_ntt::kPinv + j);
-    uint32_t* Z = S + j * N;
-    for (int i = b.tid; i < N; i += b.nt) {
-      Z[i] = i < nx ? mod_red(X[i], p) : 0u;
-      T[i] = i < ny ? mod_red(Y[i], p) : 0u;
-    }
-    group_sync<WHOLE>(b);
-    ntt_forward2<WHOLE>(b, Z, T, logn, tab, j);
-    for (int i = b.tid; i < N; i += b.nt) Z[i] = mod_mont(Z[i], T[i], p, pinv);
-    group_sync<WHOLE>(b);
-    ntt_inverse<WHOLE>(b, Z, logn, tab, j);
+    if (logn >= 3)
+      ntt_conv_prime<WHOLE>(b, S + j * N, T, X, nx, Y, ny, logn, tab, j);
+    else
+      ntt_conv_prime_small<WHOLE>(b, S + j * N, T, X, nx, Y, ny, logn, tab, j);
   }
   // Garner: c_k = x1 + p1 x2 + p1 p2 x3 with x_j < p_j, written as three words
   {
