@@ -236,6 +236,8 @@ def run_sweep(args, dev, dist, rank, ws):
     total_ms = _max_over_ranks(dist, total_ms, dev)
     per_size_ms = [statistics.mean(evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(K))
                    for i in range(len(sizes))]
+    per_size_median = [statistics.median(evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(K))
+                       for i in range(len(sizes))]
     items_step = sum(d["b"] for d in sizes)
     value = items_step * K * ws / (total_ms / 1e3)
     # the paper's cost unit (Table 1, "Our Mul"): the n-digit product kept to n
@@ -318,7 +320,8 @@ def run_sweep(args, dev, dist, rank, ws):
     for i, d in enumerate(sizes):
         bits = 32 * d["n"]
         per_size[f"2^{bits.bit_length() - 1}"] = {
-            "div_per_s": d["b"] / (per_size_ms[i] / 1e3), "ms": per_size_ms[i], "batch": d["b"],
+            "div_per_s": d["b"] / (per_size_ms[i] / 1e3), "ms": per_size_ms[i], "ms_median": per_size_median[i],
+            "batch": d["b"],
             "digit_products_per_div": d["products"] / d["b"],
             "cost_units_per_div": d["products"] / d["b"] / (d["n"] * (d["n"] + 1) / 2),
             "Tprod_per_s": d["products"] / (per_size_ms[i] / 1e3) / 1e12,
@@ -362,9 +365,15 @@ def run_sweep(args, dev, dist, rank, ws):
     if rank == 0 and not args.no_cpu_baseline:
         sample = [(d["U"][: d["b"] // 2], d["V"][: d["b"] // 2]) for d in sizes]
         v, cores, dt, n = cpu_baseline(sample)
+        # one host thread on a sixteenth of that sample
+        sample1 = [(d["U"][: d["b"] // 32], d["V"][: d["b"] // 32]) for d in sizes]
+        v1, _, dt1, n1 = cpu_baseline(sample1, nthreads=1)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"first half of each size's batch ({n} divisions, {dt:.1f} s), "
-                                         "Knuth Algorithm D in C++ on all host threads"}
+                                         "Knuth Algorithm D in C++ on all host threads",
+                               "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                                 "sample": f"first 1/32 of each size's batch ({n1} divisions, "
+                                                           f"{dt1:.1f} s)"}}
     mp.mpdiv_destroy(ctx)
     return out
 
@@ -710,7 +719,7 @@ def run_reference(args, rank, ws):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=25)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep", choices=["sweep", "mixed", "serve", "stress", "paper"])
