@@ -406,9 +406,10 @@ __device__ inline void load_digits(const Blk& b, uint32_t* dst, int len, const u
   }
   const int nv = (len - head) >> 2;
   const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(dst + head);
-  const uint32_t* g0 = g + head;
+  const size_t g0 = __cvta_generic_to_global(g + head);
   for (int c = b.tid; c < nv; c += b.nt)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s0 + 16u * (uint32_t)c), "l"(g0 + 4 * c)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s0 + 16u * (uint32_t)c),
+                 "l"(g0 + 16u * (size_t)c)
                  : "memory");
   for (int i = b.tid; i < head; i += b.nt) dst[i] = g[i];
   for (int i = head + 4 * nv + b.tid; i < len; i += b.nt) dst[i] = g[i];
