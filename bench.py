@@ -307,6 +307,30 @@ def run_sweep(args, dev, dist, rank, ws):
     e2e_ms = _max_over_ranks(dist, e0.elapsed_time(e1), dev)
     e2e_value = items_step * Ke * ws / (e2e_ms / 1e3)
 
+    # the batched form of the same work: the step's 15,360 divisions as one
+    # persistent launch over the size-sorted queue, results checked against
+    # the plain launches' digits
+    u_len = np.concatenate([np.full(d["b"], d["n"], np.int32) for d in sizes])
+    v_len = np.concatenate([np.full(d["b"], d["kl"], np.int32) for d in sizes])
+    q_len, r_len = (u_len - v_len + 1).astype(np.int32), v_len.copy()
+    offs = lambda ln: np.concatenate([[0], np.cumsum(ln)[:-1]]).astype(np.int64)  # noqa: E731
+    td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    bq = torch.zeros(int(q_len.sum()), dtype=torch.int32, device=dev)
+    br = torch.zeros(int(r_len.sum()), dtype=torch.int32, device=dev)
+    bst = torch.full((len(u_len),), -1, dtype=torch.int32, device=dev)
+    bu = torch.cat([d["u"].reshape(-1) for d in sizes])
+    bv = torch.cat([d["v"].reshape(-1) for d in sizes])
+    bargs = [bu, td(offs(u_len)), td(u_len), bv, td(offs(v_len)), td(v_len), bq, td(offs(q_len)), td(q_len), br,
+             td(offs(r_len)), td(r_len), bst]
+    batched = lambda: mp.mpdiv_batch_ragged(ctx, *bargs, None, None, torch.from_numpy(u_len),  # noqa: E731
+                                            torch.from_numpy(v_len), stream)
+    batched()
+    torch.cuda.synchronize(dev)
+    same = (int((bst != 0).sum().item()) == 0 and torch.equal(bq, torch.cat([d["q"].reshape(-1) for d in sizes]))
+            and torch.equal(br, torch.cat([d["r"].reshape(-1) for d in sizes])))
+    ms_batched = _time(batched, stream, K)
+    del bu, bv, bq, br
+
     # roofline of the dominant launch (2^18-bit dividends)
     big = max(range(len(sizes)), key=lambda i: per_size_ms[i])
     prod_big = sizes[big]["products"]
@@ -357,6 +381,11 @@ def run_sweep(args, dev, dist, rank, ws):
                                   "basis": "mpdiv_measure_peak on this GPU: in-register mad.lo.cc/madc.hi.cc/addc "
                                            "digit products and mad.lo.u32, 8 blocks x 256 threads per SM"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "batched_single_launch": {"div_per_s": items_step * ws / (ms_batched / 1e3), "ms": ms_batched,
+                                  "over_plain": (items_step * ws / (ms_batched / 1e3)) / value,
+                                  "same_digits_as_plain": same,
+                                  "how": "the step's divisions as one persistent launch over the size-sorted queue "
+                                         "(mpdiv_batch_ragged, CUDA graph), timed after the plain launches"},
         "gpu_launches": len(sizes) * K,
     }
     clocks = clk.summary()
