@@ -7,7 +7,14 @@ uniform random operands, one plain launch (one thread block per division) per
 size. One step = the four launches (15,360 divisions). Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sweep|mixed|serve|stress|paper]
+                    [--workload sweep|mixed|serve|stress|paper] [--products clipped|full|ntt]
+
+The sweep's line also carries: per_size (mean and median launch time, digit
+products, the division/multiplication time ratio), roofline (the 2^18-bit
+launch against the derived multiply-pipe peak, with the pipe measured on the
+same GPU in roofline.measured), e2e (through host buffers), the same
+divisions as one batched persistent launch (batched_single_launch), the
+CPU oracle baseline and the SM clocks seen during the timed region.
 
 --impl reference times the CPU oracle (Knuth's Algorithm D, C++) on this
 machine's host cores over a bounded sample of the same workload per step.
