@@ -242,3 +242,37 @@ def test_multiply_pipe_microbenchmark():
     assert ms0 > 0 and ms1 > 0
     assert 0 < prod < imad
     assert imad < 2 * 64 * 152 * 2.1e9  # far below nonsense: 64 multiply results/clk/SM at most twice over
+
+
+@pytest.mark.parametrize("offset,n,kl", [(1, 1024, 512), (2, 2048, 1024), (3, 4096, 2048), (4, 1027, 515), (1, 8192, 4096)])
+def test_operand_and_result_alignment(offset, n, kl):
+    # operand and result rows that start off a 16-byte boundary (a base
+    # pointer offset by 1..3 digits, or an odd row length): the 16-byte
+    # staging must fall back to digit-by-digit copies or peel the unaligned
+    # head and tail, with the same digits
+    import torch
+    import paper_2606_06386_gb300 as mp
+
+    k = 8
+    U, V = I.sweep(n, kl, k)
+    qn, rn = n - kl + 1, kl
+
+    def slab(rows, cols, src=None):
+        t = torch.full((offset + rows * cols + 3,), -1, dtype=torch.int32, device="cuda:0")
+        v = t[offset : offset + rows * cols].view(rows, cols)
+        if src is not None:
+            v.copy_(dev(src))
+        return t, v
+
+    _, u = slab(k, n, U)
+    _, v = slab(k, kl, V)
+    qb, q = slab(k, qn)
+    rb, r = slab(k, rn)
+    st = torch.full((k,), -7, dtype=torch.int32, device="cuda:0")
+    mp.mpdiv_batch(ctx(), u, v, q, r, st)
+    torch.cuda.synchronize()
+    Qo, Ro, So = oracle_uniform(U, V, qn, rn)
+    assert_same(host_u32(q), host_u32(r), st.cpu().numpy(), Qo, Ro, So)
+    # nothing written outside the result rows
+    assert (qb[:offset] == -1).all() and (qb[offset + k * qn :] == -1).all()
+    assert (rb[:offset] == -1).all() and (rb[offset + k * rn :] == -1).all()
