@@ -181,3 +181,38 @@ def test_concurrent_polls_of_one_ticket():
         mp.mpdiv_serve_stop(c)
     finally:
         mp.mpdiv_destroy(c)
+
+
+def test_serving_full_size_mix():
+    # the full size range of the serving workload (2^15..2^18-bit dividends,
+    # divisors of 0.25..1.0 of their length) plus a few 2^19-bit requests and
+    # degenerate ones (u < v, v = 1): every result equals the oracle's
+    import paper_2606_06386_gb300 as mp
+
+    n = 96
+    u_len, v_len = I.mixed_sizes(n, seed=I.SEED_BASE + 32)
+    u_len = u_len.astype(np.int32)
+    v_len = v_len.astype(np.int32)
+    u_len[:3] = 16384
+    v_len[:3] = [8192, 64, 16384]
+    u_len[3], v_len[3] = 100, 200  # u shorter than v: q = 0, r = u
+    u_flat, u_off, v_flat, v_off = I.ragged_operands(u_len, v_len, seed=32)
+    v_flat[v_off[4] : v_off[4] + v_len[4]] = 0
+    v_flat[v_off[4]] = 1  # v = 1
+    items = [(u_flat[u_off[i] : u_off[i] + u_len[i]].copy(), v_flat[v_off[i] : v_off[i] + v_len[i]].copy())
+             for i in range(n)]
+    c = mp.mpdiv_init(0)
+    try:
+        mp.mpdiv_serve_start(c, pool_digits=1 << 23, max_batch=32, max_inflight=3)
+        tickets = [_submit_retry(mp, c, u, v) for u, v in items]
+        got = []
+        for t, (u, v) in zip(tickets, items):
+            rc, q, r, st = mp.mpdiv_serve_poll(c, t, len(u), len(v), timeout_us=60_000_000)
+            assert rc == mp.MPDIV_OK and st == 0
+            got.append((q, r))
+        mp.mpdiv_serve_stop(c)
+    finally:
+        mp.mpdiv_destroy(c)
+    for (u, v), (q, r) in zip(items, got):
+        qo, ro, _ = oracle.divmod_u32(u, v, len(u), len(v))
+        assert (q == qo).all() and (r == ro).all()
