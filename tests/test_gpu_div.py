@@ -276,3 +276,30 @@ def test_operand_and_result_alignment(offset, n, kl):
     # nothing written outside the result rows
     assert (qb[:offset] == -1).all() and (qb[offset + k * qn :] == -1).all()
     assert (rb[:offset] == -1).all() and (rb[offset + k * rn :] == -1).all()
+
+
+def test_bench_sweep_configuration_sampled():
+    # the benchmark's own workload and launch configuration: the four sweep
+    # sizes at their full batch sizes (8192/4096/2048/1024 divisions), shapes
+    # picked by the tuner as bench.py does, one plain launch per size; 64
+    # sampled items per size against the oracle, every status zero
+    import torch
+    import paper_2606_06386_gb300 as mp
+
+    c = mp.mpdiv_init(0)
+    try:
+        rnd = np.random.default_rng(2024)
+        for n, kl, b in I.SWEEP:
+            U, V = I.sweep(n, kl, b)
+            mp.mpdiv_autotune(c, n, kl, b)
+            q = torch.empty((b, n - kl + 1), dtype=torch.int32, device="cuda:0")
+            r = torch.empty((b, kl), dtype=torch.int32, device="cuda:0")
+            st = torch.full((b,), -7, dtype=torch.int32, device="cuda:0")
+            mp.mpdiv_batch(c, dev(U), dev(V), q, r, st)
+            torch.cuda.synchronize()
+            assert (st == 0).all()
+            idx = np.sort(rnd.choice(b, 64, replace=False))
+            Qo, Ro, So = oracle_uniform(U[idx], V[idx], n - kl + 1, kl)
+            assert_same(host_u32(q)[idx], host_u32(r)[idx], st.cpu().numpy()[idx], Qo, Ro, So)
+    finally:
+        mp.mpdiv_destroy(c)
