@@ -192,3 +192,19 @@ def test_configured_block_size_rounds_to_a_built_kernel(warps):
     Qo, Ro, So = oracle_uniform(U, V)
     assert_same(Q, R, S, Qo, Ro, So)
     assert mp.mpdiv_tuning(ctx(warps=warps), 700)[0] == min(32, 1 << (warps - 1).bit_length())
+
+
+def test_bench_mixed_configuration_every_item():
+    # the mixed workload exactly as the benchmark runs it: 8192 divisions,
+    # 2^15..2^18-bit dividends, shapes tuned per size class first, one
+    # persistent launch (replayed as a graph); every item against the oracle
+    import paper_2606_06386_gb300 as mp
+
+    c = mp.mpdiv_init(0)
+    try:
+        for n in (1024, 2048, 4096, 8192):
+            mp.mpdiv_autotune(c, n, n // 2, 1024)
+        u_len, v_len = I.mixed_sizes()
+        _ragged(u_len, v_len, seed=I.SEED_BASE + 2, c=c)
+    finally:
+        mp.mpdiv_destroy(c)
