@@ -86,8 +86,14 @@ class Trace:
         return total
 
 
-def powdiff(v: int, w: int, h: int, ell: int, B: int, tr: Trace) -> tuple[int, int]:
-    """Algorithm 2: (sign, |B^h - v*w|), sign 1 when B^h - v*w >= 0."""
+def powdiff(v: int, w: int, h: int, ell: int, B: int, tr: Trace, lo: int = 0) -> tuple[int, int]:
+    """Algorithm 2: (sign, |B^h - v*w|), sign 1 when B^h - v*w >= 0.
+
+    With ``lo`` > 0 the close product (MultMod) sums only the digit products
+    at columns lo and up (the clipped PowDiff of ``step``): P is then
+    (v w - D) mod B^L with D the dropped sum, 0 <= D < min(prec v, prec w)
+    B^(lo+1), and the signed result B^h - v w comes out larger by D.
+    """
     L = prec(v, B) + prec(w, B) - ell + 1
     if v == 0 or w == 0 or L >= h:
         P = tr.mult("powdiff_full", v, w, B)
@@ -95,7 +101,10 @@ def powdiff(v: int, w: int, h: int, ell: int, B: int, tr: Trace) -> tuple[int, i
             return 1, B**h - P
         return 0, P - B**h
     # MultMod: the product kept modulo B^L (the close product)
-    P = tr.mult("powdiff_mod", v, w, B, keep=L) % B**L
+    P = tr.mult("powdiff_mod", v, w, B, keep=L, lo=min(lo, L))
+    if lo > 0:
+        P -= low_pairs(v, w, lo, B)
+    P %= B**L
     if P == 0:
         return 1, 0
     if (P // B ** (L - 1)) % B == 0:
@@ -123,9 +132,14 @@ def step(h: int, v: int, w: int, m: int, ell: int, g: int, B: int, tr: Trace,
     columns from e - guard up are summed exactly. The shifted product is then
     at most one short (the skipped sum is below B^(e-1) times the shorter
     operand's digit count), and the floor's sticky digit is read from the
-    summed columns only.
+    summed columns only. PowDiff's close product is clipped too, below column
+    lo = e - prec(w) - 1 - guard: its dropped sum D < B^(lo+2) makes w x
+    larger by w D < B^(prec(w) + lo + 2) = B^(e - 1), so the shifted product
+    is at most one larger. Each Step result is then within -1..+2 units of
+    Algorithm 1's.
     """
-    sign, x = powdiff(v, w, h - m, ell - g, B, tr)
+    lo = max(0, h - 2 * m - prec(w, B) - 1 - guard) if clip else 0
+    sign, x = powdiff(v, w, h - m, ell - g, B, tr, lo)
     if not clip:
         tmp = tr.mult("step", w, x, B)
     else:

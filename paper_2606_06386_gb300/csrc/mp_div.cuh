@@ -11,8 +11,9 @@
 //
 // By default the products are clipped (the refinement Section 5 proposes):
 // Step's w x and the quotient's u w skip the digit products below their kept
-// columns (less two guard digits), and the remainder is taken modulo
-// B^(kl+1). MPDIV_FLAG_FULL_PRODUCTS runs the algorithms with the paper's full
+// columns (less two guard digits), PowDiff's close product skips the digit
+// products whose sum moves Step's result by less than one unit, and the
+// remainder is taken modulo B^(kl+1). MPDIV_FLAG_FULL_PRODUCTS runs the algorithms with the paper's full
 // products instead. The corrections of Algorithm 3 run at most twice each way
 // with full products (Theorem 2 allows one) and four times with clipped ones;
 // more would set MPDIV_ST_CORRECTION_OVERFLOW.
@@ -296,7 +297,18 @@ __device__ __forceinline__ int shinv(const Blk& b, const Layout& L, int h, int k
       px = (px > 0) ? prec(b, X, px) : 0;
     } else {
       if (Lc > L.capP || Lc > L.capX) return ST_INTERNAL;
-      mul_exact<NTT>(b, L, P, Lc, X, pv, W, pw);  // MultMod: v' w mod B^L
+      if (clip_step) {
+        // MultMod clipped with the Newton step: only the digit products at
+        // columns plo = e - pw - 1 - QGUARD and up (the columns below are
+        // zero). The dropped sum D < B^(plo+2) makes the signed x larger by D,
+        // so w x grows by less than B^(e-1) and Step's result by at most one
+        // unit, which the later steps absorb
+        const int plo = max(0, e - pw - 1 - QGUARD);
+        for (int i = b.tid; i < min(plo, Lc); i += b.nt) P[i] = 0u;
+        mul(b, P, Lc, X, pv, W, pw, L.OV, plo);
+      } else {
+        mul_exact<NTT>(b, L, P, Lc, X, pv, W, pw);  // MultMod: v' w mod B^L
+      }
       // one pass gives the sign test, the negation's pivot and |x|'s length
       int z, t1, t2;
       scan3(b, P, Lc, &z, &t1, &t2);

@@ -147,8 +147,8 @@ def _first_bad(mutant):
 def test_planted_mistakes_are_caught(monkeypatch):
     orig_pd = M.powdiff
 
-    def flipped(v, w, h, ell, B, tr):
-        s, x = orig_pd(v, w, h, ell, B, tr)
+    def flipped(v, w, h, ell, B, tr, lo=0):
+        s, x = orig_pd(v, w, h, ell, B, tr, lo)
         return (1 - s if x else s), x
 
     monkeypatch.setattr(M, "powdiff", flipped)
@@ -264,3 +264,51 @@ def test_clipped_newton_steps_save_a_fifth_of_the_products():
     assert M.div_clipped(u, v, B32, t0) == M.div_clipped(u, v, B32, t1, clip_step=True) == divmod(u, v)
     assert t1.digit_products() < 0.8 * t0.digit_products()
     assert t1.digit_products() < 0.9 * n * (n + 1) / 2
+
+
+@pytest.mark.parametrize("B", [16, 256, 1 << 16])
+def test_clipped_powdiff_error_is_the_dropped_sum(B, monkeypatch):
+    # PowDiff's close product summed from column lo up drops the digit products
+    # below lo. At every call the clipped Newton iteration makes, the signed
+    # result B^h - v w comes out larger by exactly the dropped sum (no wrap
+    # modulo B^L), which is below min(prec v, prec w) (B - 1)^2 B^(lo-1) times
+    # B/(B-1) < min(prec v, prec w) B^(lo+1); the exact value from Python
+    # integers.
+    orig = M.powdiff
+    seen = {"calls": 0, "moved": 0}
+
+    def checking(v, w, h, ell, B_, tr, lo=0):
+        s, x = orig(v, w, h, ell, B_, tr, lo)
+        if lo > 0:
+            s0, x0 = orig(v, w, h, ell, B_, M.Trace(), 0)
+            assert (s0, x0) == ((1, B_**h - v * w) if B_**h >= v * w else (0, v * w - B_**h))
+            d = (x if s else -x) - (x0 if s0 else -x0)
+            assert 0 <= d < min(M.prec(v, B_), M.prec(w, B_)) * B_ ** (lo + 1), (v, w, h, ell, lo)
+            seen["calls"] += 1
+            seen["moved"] += d > 0
+        return s, x
+
+    monkeypatch.setattr(M, "powdiff", checking)
+    rnd = random.Random(B + 3)
+    for _ in range(300):
+        n = rnd.randint(6, 30)
+        kl = rnd.randint(2, n - 1)
+        v = rnd.randrange(B ** (kl - 1), B**kl)
+        M.shinv(v, n, B, None, True)
+    assert seen["calls"] > 100 and seen["moved"] > 20
+
+
+def test_clipped_powdiff_saves_a_third_of_its_products():
+    # at 2^16 bits (2048 / 1024 digits): PowDiff's close products lose about a
+    # third of their digit pairs, and the division stays exact
+    rnd = random.Random(35)
+    n, kl = 2048, 1024
+    u = rnd.getrandbits(32 * n) | (1 << (32 * n - 1))
+    v = rnd.getrandbits(32 * kl) | (1 << (32 * kl - 1))
+    tr = M.Trace()
+    assert M.div_clipped(u, v, B32, tr, clip_step=True) == divmod(u, v)
+    mod = [p for p in tr.products if p[0] == "powdiff_mod"]
+    kept = sum(max(0, min(k, keep - i) - max(0, lo - i)) for _, m, k, keep, lo in mod for i in range(m))
+    full = sum(max(0, min(k, keep - i)) for _, m, k, keep, lo in mod for i in range(m))
+    assert any(lo > 0 for *_, lo in mod)
+    assert 0.6 * full < kept < 0.72 * full
