@@ -63,7 +63,9 @@ extern "C" {
 #define MPDIV_FLAG_FULL_PRODUCTS 2 /* Algorithms 1-3 with the paper's full products w*x in Step,
                                       u*shinv and v*q (default: clipped products, Section 5: Step's
                                       w*x from the columns at or above the dropped ones less two,
-                                      the quotient from the columns at or above h-2 of u*shinv,
+                                      PowDiff's close product from the columns that can move the
+                                      Step result by a unit or more, the quotient from the
+                                      columns at or above h-2 of u*shinv,
                                       the remainder from v*q mod B^(prec(v)+1); same q and r,
                                       fewer products; the shifted inverse itself can then differ
                                       from Algorithm 1's by one unit) */
