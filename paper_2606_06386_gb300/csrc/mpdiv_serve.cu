@@ -298,9 +298,9 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
   if (cfg) S->cfg = *cfg;
   if (S->cfg.pool_digits <= 0) S->cfg.pool_digits = 64ll << 20;
   if (S->cfg.max_batch <= 0) S->cfg.max_batch = 4096;
-  if (S->cfg.max_inflight <= 0) S->cfg.max_inflight = 32;
+  if (S->cfg.max_inflight <= 0) S->cfg.max_inflight = 16;
   if (S->cfg.max_pending <= 0) S->cfg.max_pending = 1 << 20;
-  if (S->cfg.low_water <= 0) S->cfg.low_water = 2048;
+  if (S->cfg.low_water <= 0) S->cfg.low_water = 1536;
   if (S->cfg.max_wait_us <= 0) S->cfg.max_wait_us = 2000;
   const int64_t half = (S->cfg.pool_digits / 2) & ~int64_t(3);
   S->in_ring.cap = half;
