@@ -57,11 +57,11 @@ SM_COUNT_GB300 = 152
 PRODUCTS_PER_CLK_SM = 32  # 64 32-bit IMAD results/clk/SM, two (lo, hi) per 32x32->64 digit product
 SM_MAX_MHZ = 2070.0
 # DRAM bytes per 2^18-bit division of k_div_uniform, from one ncu capture of
-# that kernel (dram__bytes_read.sum + dram__bytes_write.sum = 15,108,608 + 0
+# that kernel (dram__bytes_read.sum + dram__bytes_write.sum = 15,112,704 + 0
 # bytes over a 304-division launch, 8 warps, 5 columns per lane): the operands
 # read once, the results held in L2; the roofline's traffic is this times the
 # launch's divisions
-DRAM_BYTES_PER_DIV_2E18 = 15108608 / 304
+DRAM_BYTES_PER_DIV_2E18 = 15112704 / 304
 
 
 def _peaks():
