@@ -223,10 +223,11 @@ int mpdiv_mul_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, const ui
 typedef struct mpdiv_serve_config {
   int64_t pool_digits;  /* digits of device operand/result pool (0: 64 Mi digits) */
   int32_t max_batch;    /* most requests per batch (0: 4096) */
-  int32_t max_inflight; /* batches in flight at once, each on its own stream (0: 16) */
+  int32_t max_inflight; /* batches in flight at once, each on its own stream (0: 32) */
   int32_t max_pending;  /* submitted-but-unfinished requests before EBUSY (0: 1<<20) */
-  int32_t low_water;    /* below this many requests on the GPU, queued requests launch at
-                           once; above it they gather into larger batches (0: 1536) */
+  int32_t low_water;    /* below this many requests on the GPU, queued requests launch as
+                           soon as there are 8 of them per batch in flight; above it they
+                           gather into larger batches (0: 2048) */
   int32_t max_wait_us;  /* longest a queued request waits for its batch to grow (0: 2000) */
 } mpdiv_serve_config;
 

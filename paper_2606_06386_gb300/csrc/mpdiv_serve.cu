@@ -10,8 +10,12 @@
 // of the self-splitting persistent kernel over the batch's queue, and one
 // device-to-host copy of the batch's results, all on the batch's own stream.
 // Up to max_inflight batches run at once. While fewer than low_water requests
-// are on the GPU, queued requests launch at once; under load they gather into
-// larger batches (up to max_batch, or until the oldest has waited max_wait_us).
+// are on the GPU, queued requests launch as soon as there are at least
+// kBatchStep of them for every batch already in flight (so an idle server
+// launches each request at once, and a busy one launches fewer, larger
+// batches instead of being bound by the launch path); otherwise they gather
+// into larger batches (up to max_batch, or until the oldest has waited
+// max_wait_us).
 // The kernel is the division path of the plain launch, so a result does not
 // depend on the batch a request lands in.
 #include <algorithm>
@@ -29,6 +33,10 @@
 #include "serve_ring.h"
 
 namespace {
+
+// Requests a launch needs per batch already in flight while the GPU is below
+// its low-water mark (see the header comment).
+constexpr int kBatchStep = 8;
 
 using Clock = std::chrono::steady_clock;
 
@@ -218,8 +226,8 @@ void MpServer::run() {
     bool admit = false;
     if (free_slot && !queue.empty() && queue.front()->ready.load(std::memory_order_acquire) && sched_error == 0) {
       const int64_t waited_us = (t - queue.front()->t_submit) / 1000;
-      admit = inflight_items < cfg.low_water || (int64_t)queue.size() >= cfg.max_batch ||
-              waited_us >= cfg.max_wait_us || quit;
+      admit = (inflight_items < cfg.low_water && (int64_t)queue.size() >= (int64_t)kBatchStep * busy) ||
+              (int64_t)queue.size() >= cfg.max_batch || waited_us >= cfg.max_wait_us || quit;
     }
     if (admit) {
       // the oldest ready requests, contiguous in the input ring, within the output ring
@@ -298,9 +306,9 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
   if (cfg) S->cfg = *cfg;
   if (S->cfg.pool_digits <= 0) S->cfg.pool_digits = 64ll << 20;
   if (S->cfg.max_batch <= 0) S->cfg.max_batch = 4096;
-  if (S->cfg.max_inflight <= 0) S->cfg.max_inflight = 16;
+  if (S->cfg.max_inflight <= 0) S->cfg.max_inflight = 32;
   if (S->cfg.max_pending <= 0) S->cfg.max_pending = 1 << 20;
-  if (S->cfg.low_water <= 0) S->cfg.low_water = 1536;
+  if (S->cfg.low_water <= 0) S->cfg.low_water = 2048;
   if (S->cfg.max_wait_us <= 0) S->cfg.max_wait_us = 2000;
   const int64_t half = (S->cfg.pool_digits / 2) & ~int64_t(3);
   S->in_ring.cap = half;
