@@ -312,3 +312,24 @@ def test_clipped_powdiff_saves_a_third_of_its_products():
     full = sum(max(0, min(k, keep - i)) for _, m, k, keep, lo in mod for i in range(m))
     assert any(lo > 0 for *_, lo in mod)
     assert 0.6 * full < kept < 0.72 * full
+
+
+def test_clipped_iteration_bound_at_realistic_sizes():
+    # readings 14-15 at base 2^32 and hundreds of digits, where every Newton
+    # step and PowDiff of the clipped iteration drops columns: the shifted
+    # inverse stays within -1..+2 of floor(B^h / v) (the Knuth oracle) and
+    # the clipped division is exact
+    rnd = random.Random(36)
+    clipped = 0
+    for _ in range(24):
+        n = rnd.randint(100, 600)
+        kl = rnd.randint(2, n - 1)
+        u = rnd.getrandbits(32 * n) | (1 << (32 * n - 1))
+        v = rnd.getrandbits(32 * kl) | (1 << (32 * kl - 1 - rnd.randint(0, 31)))
+        tr = M.Trace()
+        w = M.shinv(v, n, B32, tr, True)
+        exact = O.to_int(O.shinv_u32(O.from_int(v, kl), n))
+        assert w - exact in (-1, 0, 1, 2)
+        clipped += any(p[0] == "powdiff_mod" and p[4] > 0 for p in tr.products)
+        assert M.div_clipped(u, v, B32, None, 2, True) == divmod(u, v)
+    assert clipped >= 16  # the PowDiff clip acts unless the divisor is nearly as long as the dividend
