@@ -7,9 +7,9 @@ and it shares no code with the CUDA path.
 * ``knuthd.cpp`` -- the plain definition (q, r) = (floor(u/v), u mod v) by
   Knuth's Algorithm D on 32-bit digits, plus floor(B^h / v) (Definition 1 of
   the paper) and an independent schoolbook checker. Built on demand with g++.
-* ``shinv_model.py`` -- the paper's Algorithms 1-3 restated with Python's
-  unbounded integers; used to check the iteration count and the exact shifted
-  inverse that the GPU path computes.
+* ``shinv_model.py`` -- the paper's Algorithms 1-3 restated, as printed, with
+  Python's unbounded integers: the Refine loop count, the shifted inverse of
+  Algorithm 1 and the digit products the algorithms make (Section 2.3's cost).
 
 Digits are little-endian uint32 numpy arrays throughout.
 """

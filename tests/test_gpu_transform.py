@@ -111,7 +111,7 @@ def test_transform_shinv_equals_full_model():
     for i, (v, h) in enumerate(zip(vs, hs)):
         assert S[i] == 0, i
         tr = M.Trace()
-        assert oracle.to_int(O[i]) == M.shinv(v, h, B, tr, False), (i, h)
+        assert oracle.to_int(O[i]) == M.shinv(v, h, B, tr), (i, h)
         assert IT[i] == tr.iterations
 
 

@@ -1,5 +1,8 @@
 """Pins for the exact-integer model of Algorithms 1-3 (oracle/shinv_model.py).
 
+Every pin checks the model against something other than itself: the paper's
+printed worked examples, the Knuth-D oracle, closed forms, or brute force.
+
 * The whole-shifted Newton step of Eq. (3) must reproduce the iterates and
   quotients printed in the paper's worked examples (tests/golden).
 * Algorithm 1 must return floor(B^h / v) + lambda with lambda in {0, 1}
@@ -7,6 +10,11 @@
 * Algorithm 3 must return exactly (u quo v, u rem v), with delta in {-1, 0, 1}.
 * The Refine loop runs ceil(max(log2(h-k-1), 0)) + 2 times.
 * Planted mistakes (sign of PowDiff, one Refine iteration short) must be caught.
+* The digit-product count of a trace (Section 2.3's cost, Fig. 3's n-digit
+  product kept to n digits) equals a brute-force count taken by an
+  instrumented schoolbook multiplication whose value is checked against
+  Python's product; closed forms pin the quotient and remainder products; and
+  planted off-by-one counts are caught.
 """
 
 import os
@@ -147,8 +155,8 @@ def _first_bad(mutant):
 def test_planted_mistakes_are_caught(monkeypatch):
     orig_pd = M.powdiff
 
-    def flipped(v, w, h, ell, B, tr, lo=0):
-        s, x = orig_pd(v, w, h, ell, B, tr, lo)
+    def flipped(v, w, h, ell, B, tr):
+        s, x = orig_pd(v, w, h, ell, B, tr)
         return (1 - s if x else s), x
 
     monkeypatch.setattr(M, "powdiff", flipped)
@@ -173,163 +181,101 @@ def test_product_sizes_stay_near_cost_model(n, kl):
     assert total <= 7 * n * (n + 1) / 2
 
 
-def test_clipped_division_is_exact_and_cheaper():
-    # Section 5's clipped products: the quotient from the top columns only and
-    # the remainder modulo B^(k+2); the corrections restore the exact result
-    rnd = random.Random(26)
-    for _ in range(300):
-        u, v = _rand_pair(rnd, 24)
-        tr = M.Trace()
-        assert M.div_clipped(u, v, B32, tr) == divmod(u, v)
-    n, kl = 512, 256
-    u = rnd.getrandbits(32 * n) | (1 << (32 * n - 1))
-    v = rnd.getrandbits(32 * kl) | (1 << (32 * kl - 1))
-    tf, tc = M.Trace(), M.Trace()
-    M.div(u, v, B32, tf)
-    M.div_clipped(u, v, B32, tc)
-    assert tc.digit_products() < 0.7 * tf.digit_products()
+# ---------------------------------------------------------------- the digit-product count
+def counted_schoolbook(a: int, b: int, B: int, keep=None, lo: int = 0):
+    """Schoolbook multiplication digit by digit over the pairs (i, j) with
+    lo <= i + j < keep, counting each digit product it makes: (sum, count)."""
+    A = [(a // B**i) % B for i in range(M.prec(a, B))]
+    C = [(b // B**j) % B for j in range(M.prec(b, B))]
+    hi = len(A) + len(C) if keep is None else keep
+    s = count = 0
+    for i, ai in enumerate(A):
+        for j, cj in enumerate(C):
+            if lo <= i + j < hi:
+                s += ai * cj * B ** (i + j)
+                count += 1
+    return s, count
 
 
-def test_clipped_quotient_is_at_most_one_short():
-    rnd = random.Random(27)
-    for _ in range(200):
-        n = rnd.randint(3, 30)
-        kl = rnd.randint(2, n)
-        u = rnd.getrandbits(32 * n) | (1 << (32 * n - 1))
-        v = rnd.getrandbits(32 * kl) | (1 << (32 * kl - 1))
-        h = M.prec(u, B32)
-        w = M.shinv(v, h, B32)
-        lo = h - 2
-        low = sum(((w >> (32 * j)) & (B32 - 1)) * (u % B32 ** (lo - j)) * B32**j for j in range(M.prec(w, B32)) if lo - j > 0)
-        q_full = (u * w) // B32**h
-        q_clip = (u * w - low) // B32**h
-        assert q_full - q_clip in (0, 1)
+def _count_pin_failures(count):
+    """Shapes where count(m, n, keep) disagrees with the brute-force count of
+    an instrumented schoolbook product whose value is checked against Python's
+    product modulo B^keep. Operands have nonzero top digits and arbitrary
+    (also zero) inner digits."""
+    rnd = random.Random(41)
+    B = 16
+    bad = []
+    shapes = [(1, 1, None), (1, 5, None), (5, 1, 3), (3, 3, 1), (4, 7, 4), (7, 4, 4), (6, 6, 11), (6, 6, 12),
+              (9, 2, 10), (2, 9, 2)]
+    shapes += [(rnd.randint(1, 12), rnd.randint(1, 12), None) for _ in range(20)]
+    shapes += [(m, n, rnd.randint(1, m + n)) for m, n in ((rnd.randint(1, 12), rnd.randint(1, 12)) for _ in range(60))]
+    for m, n, keep in shapes:
+        a = rnd.randrange(B ** (m - 1), B**m)
+        b = rnd.randrange(B ** (n - 1), B**n)
+        s, c = counted_schoolbook(a, b, B, keep)
+        mod = B ** (m + n if keep is None else keep)
+        assert s % mod == (a * b) % mod  # the enumerated pairs are exactly those of the product mod B^keep
+        if count(m, n, keep) != c:
+            bad.append((m, n, keep))
+    return bad
 
 
-def test_clipped_newton_step_is_at_most_one_unit_off():
-    # Step with w*x clipped below e - 2 (e = digits Step drops): each Step result
-    # is Algorithm 1's or one unit away (down on the + branch, up on the -
-    # branch); at base 16 the clip changes some steps
-    seen = {"steps": 0, "changed": 0}
-    orig = M.step
-
-    def checking_step(h, v, w, m, ell, g, B, tr, clip=False, guard=2):
-        a = orig(h, v, w, m, ell, g, B, M.Trace())
-        b = orig(h, v, w, m, ell, g, B, M.Trace(), True, guard)
-        seen["steps"] += 1
-        seen["changed"] += a != b
-        assert b - a in (-1, 0, 1)
-        return orig(h, v, w, m, ell, g, B, tr, clip, guard)
-
-    rnd = random.Random(33)
-    M.step = checking_step
-    try:
-        for _ in range(1500):
-            n = rnd.randint(3, 14)
-            kl = rnd.randint(2, n)
-            u = rnd.randrange(16 ** (n - 1), 16**n)
-            v = rnd.randrange(16 ** (kl - 1), 16**kl)
-            M.shinv(v, M.prec(u, 16), 16, None, True)
-    finally:
-        M.step = orig
-    assert seen["changed"] > 0 and seen["steps"] > 1000
+def test_digit_product_count_equals_brute_force():
+    assert _count_pin_failures(M.pairs_below) == []
+    # through a trace: one record per product, summed
+    tr = M.Trace()
+    rnd = random.Random(42)
+    expect = 0
+    for _ in range(30):
+        m, n = rnd.randint(1, 10), rnd.randint(1, 10)
+        keep = rnd.choice([None, rnd.randint(1, m + n)])
+        a = rnd.randrange(16 ** (m - 1), 16**m)
+        b = rnd.randrange(16 ** (n - 1), 16**n)
+        tr.mult("x", a, b, 16, keep)
+        expect += counted_schoolbook(a, b, 16, keep)[1]
+    assert tr.digit_products() == expect
 
 
-@pytest.mark.parametrize("B", [16, 256, 1 << 16, B32])
-def test_clipped_newton_steps_keep_division_exact(B):
-    # the shifted inverse with clipped Newton steps stays within -1..+2 of
-    # floor(B^h / v) (the Knuth oracle at base 2^32, integer floor otherwise),
-    # and the clipped division (Section 5) returns the exact quotient and remainder
-    rnd = random.Random(B % 1000 + 7)
-    for _ in range(300):
-        n = rnd.randint(3, 40 if B == B32 else 14)
-        kl = rnd.randint(2, n)
-        u = rnd.randrange(B ** (n - 1), B**n)
-        v = rnd.randrange(B ** (kl - 1), B**kl)
-        h = M.prec(u, B)
-        w = M.shinv(v, h, B, None, True)
-        exact = O.to_int(O.shinv_u32(O.from_int(v, kl), h)) if B == B32 else B**h // v
-        assert w - exact in (-1, 0, 1, 2)
-        assert M.div_clipped(u, v, B, None, 2, True) == divmod(u, v)
+def test_planted_off_by_one_counts_are_caught():
+    mutants = [
+        lambda m, n, keep: m * n if keep is None else sum(max(0, min(n, keep - i + 1)) for i in range(m)),
+        lambda m, n, keep: m * n if keep is None else sum(max(0, min(n, keep - i - 1)) for i in range(m)),
+        lambda m, n, keep: m * n if keep is None else sum(max(0, min(n, keep - i)) for i in range(m - 1)),
+        lambda m, n, keep: m * n if keep is None else sum(max(0, min(n + 1, keep - i)) for i in range(m)),
+        lambda m, n, keep: m * n,  # the close product counted as a full one
+        lambda m, n, keep: (m + 1) * n if keep is None else M.pairs_below(m, n, keep),
+    ]
+    for f in mutants:
+        assert _count_pin_failures(f), f
 
 
-def test_clipped_newton_steps_save_a_fifth_of_the_products():
-    # half-length divisor at 2^15 bits: clipping Step's w*x as well removes
-    # about three quarters of the Newton steps' digit products
-    rnd = random.Random(34)
+def test_full_trace_at_2e15_bits_matches_closed_forms_and_the_cost_model():
+    # Algorithms 1-3 as printed at n = 1024, k_l = 512 (2^15-bit dividend,
+    # half-length divisor). The quotient product u * shinv_h(v) costs
+    # prec(u) prec(floor(B^h / v)) (+ one digit when Theorem 2's lambda = 1),
+    # the remainder product v q costs prec(v) prec(q) with q from the Knuth
+    # oracle, and the whole division about 2.10 units of n(n+1)/2 (1.10 M
+    # products: 0.316 M in Shinv, 0.525 M in the quotient, 0.263 M in the
+    # remainder), Section 2.3's 5-7 full multiplications read with Fig. 3's
+    # n-digit unit.
+    rnd = random.Random(43)
     n, kl = 1024, 512
     u = rnd.getrandbits(32 * n) | (1 << (32 * n - 1))
     v = rnd.getrandbits(32 * kl) | (1 << (32 * kl - 1))
-    t0, t1 = M.Trace(), M.Trace()
-    assert M.div_clipped(u, v, B32, t0) == M.div_clipped(u, v, B32, t1, clip_step=True) == divmod(u, v)
-    assert t1.digit_products() < 0.8 * t0.digit_products()
-    assert t1.digit_products() < 0.9 * n * (n + 1) / 2
-
-
-@pytest.mark.parametrize("B", [16, 256, 1 << 16])
-def test_clipped_powdiff_error_is_the_dropped_sum(B, monkeypatch):
-    # PowDiff's close product summed from column lo up drops the digit products
-    # below lo. At every call the clipped Newton iteration makes, the signed
-    # result B^h - v w comes out larger by exactly the dropped sum (no wrap
-    # modulo B^L), which is below min(prec v, prec w) (B - 1)^2 B^(lo-1) times
-    # B/(B-1) < min(prec v, prec w) B^(lo+1); the exact value from Python
-    # integers.
-    orig = M.powdiff
-    seen = {"calls": 0, "moved": 0}
-
-    def checking(v, w, h, ell, B_, tr, lo=0):
-        s, x = orig(v, w, h, ell, B_, tr, lo)
-        if lo > 0:
-            s0, x0 = orig(v, w, h, ell, B_, M.Trace(), 0)
-            assert (s0, x0) == ((1, B_**h - v * w) if B_**h >= v * w else (0, v * w - B_**h))
-            d = (x if s else -x) - (x0 if s0 else -x0)
-            assert 0 <= d < min(M.prec(v, B_), M.prec(w, B_)) * B_ ** (lo + 1), (v, w, h, ell, lo)
-            seen["calls"] += 1
-            seen["moved"] += d > 0
-        return s, x
-
-    monkeypatch.setattr(M, "powdiff", checking)
-    rnd = random.Random(B + 3)
-    for _ in range(300):
-        n = rnd.randint(6, 30)
-        kl = rnd.randint(2, n - 1)
-        v = rnd.randrange(B ** (kl - 1), B**kl)
-        M.shinv(v, n, B, None, True)
-    assert seen["calls"] > 100 and seen["moved"] > 20
-
-
-def test_clipped_powdiff_saves_a_third_of_its_products():
-    # at 2^16 bits (2048 / 1024 digits): PowDiff's close products lose about a
-    # third of their digit pairs, and the division stays exact
-    rnd = random.Random(35)
-    n, kl = 2048, 1024
-    u = rnd.getrandbits(32 * n) | (1 << (32 * n - 1))
-    v = rnd.getrandbits(32 * kl) | (1 << (32 * kl - 1))
     tr = M.Trace()
-    assert M.div_clipped(u, v, B32, tr, clip_step=True) == divmod(u, v)
-    mod = [p for p in tr.products if p[0] == "powdiff_mod"]
-    kept = sum(max(0, min(k, keep - i) - max(0, lo - i)) for _, m, k, keep, lo in mod for i in range(m))
-    full = sum(max(0, min(k, keep - i)) for _, m, k, keep, lo in mod for i in range(m))
-    assert any(lo > 0 for *_, lo in mod)
-    assert 0.6 * full < kept < 0.72 * full
-
-
-def test_clipped_iteration_bound_at_realistic_sizes():
-    # readings 14-15 at base 2^32 and hundreds of digits, where every Newton
-    # step and PowDiff of the clipped iteration drops columns: the shifted
-    # inverse stays within -1..+2 of floor(B^h / v) (the Knuth oracle) and
-    # the clipped division is exact
-    rnd = random.Random(36)
-    clipped = 0
-    for _ in range(24):
-        n = rnd.randint(100, 600)
-        kl = rnd.randint(2, n - 1)
-        u = rnd.getrandbits(32 * n) | (1 << (32 * n - 1))
-        v = rnd.getrandbits(32 * kl) | (1 << (32 * kl - 1 - rnd.randint(0, 31)))
-        tr = M.Trace()
-        w = M.shinv(v, n, B32, tr, True)
-        exact = O.to_int(O.shinv_u32(O.from_int(v, kl), n))
-        assert w - exact in (-1, 0, 1, 2)
-        clipped += any(p[0] == "powdiff_mod" and p[4] > 0 for p in tr.products)
-        assert M.div_clipped(u, v, B32, None, 2, True) == divmod(u, v)
-    assert clipped >= 16  # the PowDiff clip acts unless the divisor is nearly as long as the dividend
+    q, r, delta = M.div(u, v, B32, tr)
+    qo, ro, st = O.divmod_u32(O.from_int(u, n), O.from_int(v, kl))
+    assert st == 0 and (q, r) == (O.to_int(qo), O.to_int(ro))
+    by_tag = {}
+    for tag, m, k, keep in tr.products:
+        by_tag[tag] = by_tag.get(tag, 0) + M.pairs_below(m, k, keep)
+    shinv_exact = O.to_int(O.shinv_u32(O.from_int(v, kl), n))
+    assert by_tag["quotient"] == n * M.prec(shinv_exact, B32) == 1024 * 513
+    q0 = q - delta
+    assert by_tag["remainder"] == kl * M.prec(q0, B32)
+    newton = by_tag["powdiff_full"] + by_tag.get("powdiff_mod", 0) + by_tag["step"]
+    assert abs(newton - 0.316e6) < 0.01 * 0.316e6
+    total = tr.digit_products()
+    assert total == newton + by_tag["quotient"] + by_tag["remainder"]
+    assert abs(total - 1.10e6) < 0.01 * 1.10e6
+    assert abs(total / (n * (n + 1) / 2) - 2.10) < 0.01
