@@ -14,7 +14,13 @@ products, the division/multiplication time ratio), roofline (the 2^18-bit
 launch against the derived multiply-pipe peak, with the pipe measured on the
 same GPU in roofline.measured), e2e (through host buffers), the same
 divisions as one batched persistent launch (batched_single_launch), the
-CPU oracle baseline and the SM clocks seen during the timed region.
+CPU oracle baseline and the SM clocks seen during the timed region. At its end
+it carries compact results of the other configurations, each with its clocks
+(--no-configs leaves them out): mixed (8192 mixed-precision divisions, the
+batched launch against one plain launch per size class), serve (200,000
+Poisson arrivals at 50/80/95 % of the plain capacity, 95 % three times: p50,
+p99, sustained rate) and stress (the five 2^18-bit variants: rate, Newton
+iterations, nonzero statuses).
 
 --impl reference times the CPU oracle (Knuth's Algorithm D, C++) on this
 machine's host cores over a bounded sample of the same workload per step.
@@ -361,6 +367,7 @@ def run_sweep(args, dev, dist, rank, ws):
             "warps_per_block": tuned[d["n"]],
             "mul_columns": mp.mpdiv_tuning(ctx, d["n"])[1],
             "karatsuba_cutoff": mp.mpdiv_tuning(ctx, d["n"])[2],
+            "registers": mp.mpdiv_tuning(ctx, d["n"])[3],
         }
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
@@ -410,8 +417,47 @@ def run_sweep(args, dev, dist, rank, ws):
                                "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
                                                  "sample": f"first 1/32 of each size's batch ({n1} divisions, "
                                                            f"{dt1:.1f} s)"}}
+    if not args.no_configs:
+        out.update(other_configs_summary(mp, ctx, dev, stream, args))
     mp.mpdiv_destroy(ctx)
     return out
+
+
+def _sig(x, digits=4):
+    """x rounded to a few significant digits (compact JSON)."""
+    if x is None or x == 0:
+        return x
+    return float(f"{x:.{digits}g}")
+
+
+def _clk(c):
+    return None if c is None else {"sm_mhz": c["sm_mhz"], "max": c["sm_max_mhz"], "reasons": c["reasons"]}
+
+
+def other_configs_summary(mp, ctx, dev, stream, args):
+    """Compact results of the mixed (config 3), serving (config 4) and stress
+    (config 5) workloads on the sweep's context (shapes tuned per size class),
+    each with the clocks seen while it ran; appended at the end of the sweep's
+    JSON line."""
+    m, _, _ = measure_mixed(mp, ctx, dev, stream, max(5, args.steps // 2), 3, per_n=False)
+    mixed = {"div_s": _sig(m["div_per_s"]), "plain_class_div_s": _sig(m["plain_per_size_class"]["div_per_s"]),
+             "over_plain": _sig(m["batched_over_plain_class"]), "n": m["n"], "clk": _clk(m["clocks"])}
+    cap, sv = measure_serve(mp, ctx, dev, stream, args.requests, args.max_batch, args.max_inflight, args.low_water,
+                            repeat_top=3)
+    loads = {}
+    for k, x in sv.items():
+        d = {"div_s": _sig(x["sustained_div_per_s"]), "p50_ms": _sig(x["p50_ms"], 3), "p99_ms": _sig(x["p99_ms"], 3),
+             "ok": x["ok"], "clk": _clk(x["clocks"])}
+        if "runs" in x:
+            d["p99_ms_runs"] = [_sig(r["p99_ms"], 3) for r in x["runs"]]
+            d["ok"] = min(r["ok"] for r in x["runs"])
+        loads[k] = d
+    serve = {"requests": args.requests, "cap_div_s": _sig(cap), **loads}
+    st, _, _, sclk = measure_stress(mp, ctx, dev, stream, 3)
+    stress = {k.split("_")[0]: {"div_s": _sig(x["div_per_s"]), "it": [x["newton_iters_min"], x["newton_iters_max"]],
+                                "st_nz": x["status_nonzero"]} for k, x in st.items()}
+    stress["clk"] = _clk(sclk)
+    return {"mixed": mixed, "serve": serve, "stress": stress}
 
 
 def _ragged_setup(u_len, v_len, seed, dev):
@@ -471,6 +517,144 @@ def _time(fn, stream, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def measure_mixed(mp, ctx, dev, stream, steps, warmup, per_n=True):
+    """Config 3: one persistent launch of 8192 mixed-precision divisions
+    (size-sorted queue, replayed as a CUDA graph) against one plain launch per
+    padded size class (and, with per_n, one per distinct dividend length). The
+    context's shapes should be tuned per size class first."""
+    import torch
+
+    u_len, v_len = I.mixed_sizes(8192)
+    R = _ragged_setup(u_len, v_len, seed=I.SEED_BASE + 2, dev=dev)
+    prod = torch.zeros(R["n"], dtype=torch.int64, device=dev)
+    mp.mpdiv_batch_ragged(ctx, *R["args"], None, prod, R["u_len_host"], R["v_len_host"], stream)
+    torch.cuda.synchronize(dev)
+    if int((R["args"][12] != 0).sum().item()):
+        raise RuntimeError("nonzero status in the mixed batch")
+    products = int(prod.sum().item())
+    persistent = lambda: mp.mpdiv_batch_ragged(ctx, *R["args"], None, None, R["u_len_host"], R["v_len_host"],  # noqa
+                                               stream)
+    for _ in range(warmup):
+        persistent()
+    classes = _class_batches(R, None, dev, key=lambda n: 1 << max(10, (n - 1).bit_length()))
+
+    def plain(batches):
+        for b in batches:
+            mp.mpdiv_batch(ctx, b["u"], b["v"], b["q"], b["r"], b["st"], None, None, stream)
+
+    plain(classes)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(dev.index or 0) as clk:
+        ms_persist = _time(persistent, stream, steps)
+        ms_class = _time(lambda: plain(classes), stream, steps)
+    n = R["n"]
+    res = {"n": n, "ms": ms_persist, "div_per_s": n / (ms_persist / 1e3),
+           "plain_per_size_class": {"div_per_s": n / (ms_class / 1e3), "launches": len(classes), "ms": ms_class},
+           "batched_over_plain_class": ms_class / ms_persist,
+           "digit_products_per_div": products / n, "Tprod_per_s": products / (ms_persist / 1e3) / 1e12,
+           "clocks": clk.summary()}
+    if per_n:
+        per_n_b = _class_batches(R, None, dev, key=lambda m: m)
+        plain(per_n_b)
+        ms_n = _time(lambda: plain(per_n_b), stream, 2)
+        res["plain_per_distinct_n"] = {"div_per_s": n / (ms_n / 1e3), "launches": len(per_n_b), "ms": ms_n}
+    return res, R, classes
+
+
+def measure_serve(mp, ctx, dev, stream, n_req, max_batch, max_inflight, low_water, loads=(0.5, 0.8, 0.95),
+                  repeat_top=1):
+    """Config 4: Poisson arrivals of mixed-precision requests through the
+    serving loop at fractions of the plain path's measured capacity (one plain
+    launch per size class); the last load is run repeat_top times."""
+    u_len, v_len = I.mixed_sizes(8192)
+    R = _ragged_setup(u_len, v_len, seed=I.SEED_BASE + 2, dev=dev)
+    classes = _class_batches(R, None, dev, key=lambda n: 1 << max(10, (n - 1).bit_length()))
+
+    def plain():
+        for b in classes:
+            mp.mpdiv_batch(ctx, b["u"], b["v"], b["q"], b["r"], b["st"], None, None, stream)
+
+    plain()
+    cap = R["n"] / (_time(plain, stream, 3) / 1e3)
+    pick = np.arange(n_req) % R["n"]  # request i divides mixed item i mod 8192
+    ul = R["u_len"][pick].astype(np.int32)
+    vl = R["v_len"][pick].astype(np.int32)
+    uo = R["u_off"][pick].astype(np.int64)
+    vo = R["v_off"][pick].astype(np.int64)
+    qo = R["q_off"][pick].astype(np.int64)  # results of repeated items land in the same slots
+    ro = R["r_off"][pick].astype(np.int64)
+    res = {}
+    for li, frac in enumerate(loads):
+        runs = []
+        for rep in range(repeat_top if li == len(loads) - 1 else 1):
+            rate = frac * cap
+            arr = (I.poisson_arrivals(n_req, rate, seed=I.SEED_BASE + 3 + rep, stream=int(frac * 100)) * 1e9
+                   ).astype(np.int64)
+            q = np.zeros(int(R["q_len"].sum()), np.uint32)
+            r = np.zeros(int(R["r_len"].sum()), np.uint32)
+            st = np.full(n_req, -9, np.int32)
+            lat = np.zeros(n_req, np.int64)
+            mp.mpdiv_serve_start(ctx, pool_digits=256 << 20, max_batch=max_batch, max_inflight=max_inflight,
+                                 low_water=low_water)
+            with ClockSampler(dev.index or 0) as clk:
+                t0 = time.perf_counter()
+                rej = mp.mpdiv_serve_replay(ctx, arr, R["u_flat"], uo, ul, R["v_flat"], vo, vl, q, qo, ul.copy(), r,
+                                            ro, vl.copy(), st, lat)
+                wall = time.perf_counter() - t0
+            completed, launches, batched = mp.mpdiv_serve_stats(ctx)
+            mp.mpdiv_serve_stop(ctx)
+            span = ((arr + lat).max() - arr.min()) / 1e9
+            runs.append({
+                "offered_div_per_s": rate, "sustained_div_per_s": n_req / span,
+                "p50_ms": float(np.percentile(lat, 50)) / 1e6, "p99_ms": float(np.percentile(lat, 99)) / 1e6,
+                "max_ms": float(lat.max()) / 1e6, "ok": int((st == 0).sum()), "launches": launches,
+                "mean_batch": batched / max(1, launches), "busy_retries": rej, "wall_s": wall,
+                "clocks": clk.summary()})
+        out = dict(runs[0])
+        if len(runs) > 1:
+            out["runs"] = [{k: x[k] for k in ("sustained_div_per_s", "p50_ms", "p99_ms", "ok")} for x in runs]
+            out["p99_ms_median"] = float(np.median([x["p99_ms"] for x in runs]))
+        res[f"{int(frac * 100)}%"] = out
+    return cap, res
+
+
+def measure_stress(mp, ctx, dev, stream, reps):
+    """Config 5: the five 2^18-bit adversarial variants, 1024 divisions each,
+    with Newton iteration counts and statuses."""
+    import torch
+
+    res = {}
+    total_items, total_ms = 0, 0.0
+    with ClockSampler(dev.index or 0) as clk:
+        for variant in I.STRESS_VARIANTS:
+            U, V = I.stress(variant)
+            u, v = _to_dev(U, dev), _to_dev(V, dev)
+            n = U.shape[0]
+            q = torch.zeros((n, U.shape[1]), dtype=torch.int32, device=dev)
+            r = torch.zeros((n, V.shape[1]), dtype=torch.int32, device=dev)
+            st = torch.full((n,), -1, dtype=torch.int32, device=dev)
+            it = torch.zeros(n, dtype=torch.int32, device=dev)
+            pr = torch.zeros(n, dtype=torch.int64, device=dev)
+            mp.mpdiv_batch(ctx, u, v, q, r, st, it, pr, stream)
+            torch.cuda.synchronize(dev)
+            bad = int((st != 0).sum().item())
+            ms = _time(lambda: mp.mpdiv_batch(ctx, u, v, q, r, st, None, None, stream), stream, reps)
+            its = it.cpu().numpy()
+            res[variant] = {"div_per_s": n / (ms / 1e3), "ms": ms, "status_nonzero": bad,
+                            "newton_iters_min": int(its.min()), "newton_iters_max": int(its.max()),
+                            "digit_products_per_div": float(pr.sum().item()) / n,
+                            "Tprod_per_s": float(pr.sum().item()) / (ms / 1e3) / 1e12}
+            total_items += n
+            total_ms += ms
+            del u, v, q, r, st, it, pr
+    return res, total_items, total_ms, clk.summary()
+
+
+def _tune_classes(mp, ctx):
+    for c in (1024, 2048, 4096, 8192):  # tuned shape per size class, for both launch forms
+        mp.mpdiv_autotune(ctx, c, c // 2, 1024)
+
+
 def run_mixed(args, dev, dist, rank, ws):
     """One persistent launch of 8192 mixed-precision divisions (size-sorted queue,
     CUDA graph replay) against plain launches per padded size class and per
@@ -481,37 +665,12 @@ def run_mixed(args, dev, dist, rank, ws):
 
     mp.build()
     ctx = mp.mpdiv_init(dev.index or 0)
-    for c in (1024, 2048, 4096, 8192):  # tuned shape per size class, for both launch forms
-        mp.mpdiv_autotune(ctx, c, c // 2, 1024)
-    u_len, v_len = I.mixed_sizes(8192)
-    R = _ragged_setup(u_len, v_len, seed=I.SEED_BASE + 2, dev=dev)
+    _tune_classes(mp, ctx)
     stream = torch.cuda.current_stream(dev)
-    prod = torch.zeros(R["n"], dtype=torch.int64, device=dev)
-    mp.mpdiv_batch_ragged(ctx, *R["args"], None, prod, R["u_len_host"], R["v_len_host"], stream)
-    torch.cuda.synchronize(dev)
-    if int((R["args"][12] != 0).sum().item()):
-        raise RuntimeError("nonzero status in the mixed batch")
-    products = int(prod.sum().item())
-    persistent = lambda: mp.mpdiv_batch_ragged(ctx, *R["args"], None, None, R["u_len_host"], R["v_len_host"],  # noqa
-                                               stream)
-    for _ in range(args.warmup):
-        persistent()
     _barrier(dist, dev)
-    with ClockSampler(dev.index or 0) as clk:
-        ms_persist = _time(persistent, stream, args.steps)
-    classes = _class_batches(R, None, dev, key=lambda n: 1 << max(10, (n - 1).bit_length()))
-    per_n = _class_batches(R, None, dev, key=lambda n: n)
-
-    def plain(batches):
-        for b in batches:
-            mp.mpdiv_batch(ctx, b["u"], b["v"], b["q"], b["r"], b["st"], None, None, stream)
-
-    plain(classes)
-    plain(per_n)
-    ms_class = _time(lambda: plain(classes), stream, max(3, args.steps // 2))
-    ms_n = _time(lambda: plain(per_n), stream, 2)
-    ms_persist = _max_over_ranks(dist, ms_persist, dev)
-    n = R["n"]
+    m, _, _ = measure_mixed(mp, ctx, dev, stream, args.steps, args.warmup)
+    ms_persist = _max_over_ranks(dist, m["ms"], dev)
+    n = m["n"]
     out = {
         "metric": METRIC, "value": n * ws / (ms_persist / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_persist, "higher_is_better": True, "scaling": "weak",
@@ -520,16 +679,15 @@ def run_mixed(args, dev, dist, rank, ws):
                                "(0.25+0.75y) x dividend length; one persistent launch over a size-sorted queue, "
                                "replayed as a CUDA graph",
                    "l2": "inputs 113 MB, re-read each step (compute-bound: ~1 MB/ms)"},
-        "plain_per_size_class": {"div_per_s": n / (ms_class / 1e3), "launches": len(classes), "ms": ms_class},
-        "plain_per_distinct_n": {"div_per_s": n / (ms_n / 1e3), "launches": len(per_n), "ms": ms_n},
-        "batched_over_plain_class": ms_class / ms_persist,
-        "digit_products_per_div": products / n,
-        "Tprod_per_s": products / (ms_persist / 1e3) / 1e12,
+        "plain_per_size_class": m["plain_per_size_class"],
+        "plain_per_distinct_n": m["plain_per_distinct_n"],
+        "batched_over_plain_class": m["batched_over_plain_class"],
+        "digit_products_per_div": m["digit_products_per_div"],
+        "Tprod_per_s": m["Tprod_per_s"],
         "gpu_launches": args.steps,
     }
-    c = clk.summary()
-    if c is not None:
-        out["clocks"] = c
+    if m["clocks"] is not None:
+        out["clocks"] = m["clocks"]
     mp.mpdiv_destroy(ctx)
     return out
 
@@ -543,60 +701,18 @@ def run_serve(args, dev, dist, rank, ws):
 
     mp.build()
     ctx = mp.mpdiv_init(dev.index or 0)
-    for c in (1024, 2048, 4096, 8192):  # tuned shape per size class, for both launch forms
-        mp.mpdiv_autotune(ctx, c, c // 2, 1024)
-    u_len, v_len = I.mixed_sizes(8192)
-    R = _ragged_setup(u_len, v_len, seed=I.SEED_BASE + 2, dev=dev)
+    _tune_classes(mp, ctx)
     stream = torch.cuda.current_stream(dev)
-    classes = _class_batches(R, None, dev, key=lambda n: 1 << max(10, (n - 1).bit_length()))
-
-    def plain():
-        for b in classes:
-            mp.mpdiv_batch(ctx, b["u"], b["v"], b["q"], b["r"], b["st"], None, None, stream)
-
-    plain()
-    cap = R["n"] / (_time(plain, stream, 3) / 1e3)
+    cap, res = measure_serve(mp, ctx, dev, stream, args.requests, args.max_batch, args.max_inflight, args.low_water,
+                             repeat_top=3)
     n_req = args.requests
-    pick = np.arange(n_req) % R["n"]  # request i divides mixed item i mod 8192
-    res = {}
-    for frac in (0.5, 0.8, 0.95):
-        rate = frac * cap
-        arr = (I.poisson_arrivals(n_req, rate, seed=I.SEED_BASE + 3, stream=int(frac * 100)) * 1e9).astype(np.int64)
-        ul = R["u_len"][pick].astype(np.int32)
-        vl = R["v_len"][pick].astype(np.int32)
-        uo = R["u_off"][pick].astype(np.int64)
-        vo = R["v_off"][pick].astype(np.int64)
-        qo = R["q_off"][pick].astype(np.int64)  # results of repeated items land in the same slots
-        ro = R["r_off"][pick].astype(np.int64)
-        q = np.zeros(int(R["q_len"].sum()), np.uint32)
-        r = np.zeros(int(R["r_len"].sum()), np.uint32)
-        st = np.full(n_req, -9, np.int32)
-        lat = np.zeros(n_req, np.int64)
-        mp.mpdiv_serve_start(ctx, pool_digits=256 << 20, max_batch=args.max_batch, max_inflight=args.max_inflight,
-                             low_water=args.low_water)
-        with ClockSampler(dev.index or 0) as clk:
-            t0 = time.perf_counter()
-            rej = mp.mpdiv_serve_replay(ctx, arr, R["u_flat"], uo, ul, R["v_flat"], vo, vl, q, qo, ul.copy(), r,
-                                        ro, vl.copy(), st, lat)
-            wall = time.perf_counter() - t0
-        completed, launches, batched = mp.mpdiv_serve_stats(ctx)
-        mp.mpdiv_serve_stop(ctx)
-        ok = int((st == 0).sum())
-        done_t = arr + lat
-        span = (done_t.max() - arr.min()) / 1e9
-        res[f"{int(frac * 100)}%"] = {
-            "offered_div_per_s": rate, "sustained_div_per_s": n_req / span, "p50_ms": float(np.percentile(lat, 50)) / 1e6,
-            "p99_ms": float(np.percentile(lat, 99)) / 1e6, "max_ms": float(lat.max()) / 1e6, "ok": ok,
-            "launches": launches, "mean_batch": batched / max(1, launches), "busy_retries": rej, "wall_s": wall,
-            "clocks": clk.summary(),
-        }
     out = {
         "metric": METRIC, "value": res["95%"]["sustained_div_per_s"], "unit": UNIT, "n_gpus": ws,
         "steps": 1, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": f"serving: {n_req} Poisson-arrival requests, sizes as the mixed batch, offered at "
-                               "50/80/95% of the plain per-size-class capacity; latency from scheduled arrival "
-                               "to result pollable on the host"},
+                               "50/80/95% of the plain per-size-class capacity (95% three times); latency from "
+                               "scheduled arrival to result pollable on the host"},
         "plain_capacity_div_per_s": cap, "loads": res,
     }
     mp.mpdiv_destroy(ctx)
@@ -612,27 +728,7 @@ def run_stress(args, dev, dist, rank, ws):
     mp.build()
     ctx = mp.mpdiv_init(dev.index or 0)
     stream = torch.cuda.current_stream(dev)
-    res = {}
-    total_items, total_ms = 0, 0.0
-    for variant in I.STRESS_VARIANTS:
-        U, V = I.stress(variant)
-        u, v = _to_dev(U, dev), _to_dev(V, dev)
-        n = U.shape[0]
-        q = torch.zeros((n, U.shape[1]), dtype=torch.int32, device=dev)
-        r = torch.zeros((n, V.shape[1]), dtype=torch.int32, device=dev)
-        st = torch.full((n,), -1, dtype=torch.int32, device=dev)
-        it = torch.zeros(n, dtype=torch.int32, device=dev)
-        pr = torch.zeros(n, dtype=torch.int64, device=dev)
-        mp.mpdiv_batch(ctx, u, v, q, r, st, it, pr, stream)
-        torch.cuda.synchronize(dev)
-        ms = _time(lambda: mp.mpdiv_batch(ctx, u, v, q, r, st, None, None, stream), stream, max(3, args.steps // 4))
-        its = it.cpu().numpy()
-        res[variant] = {"div_per_s": n / (ms / 1e3), "ms": ms, "status_nonzero": int((st != 0).sum().item()),
-                        "newton_iters_min": int(its.min()), "newton_iters_max": int(its.max()),
-                        "digit_products_per_div": float(pr.sum().item()) / n,
-                        "Tprod_per_s": float(pr.sum().item()) / (ms / 1e3) / 1e12}
-        total_items += n
-        total_ms += ms
+    res, total_items, total_ms, clocks = measure_stress(mp, ctx, dev, stream, max(3, args.steps // 4))
     out = {
         "metric": METRIC, "value": total_items / (total_ms / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms, "higher_is_better": True, "scaling": "weak",
@@ -641,6 +737,8 @@ def run_stress(args, dev, dist, rank, ws):
                                "half, all ones, 1% sparse, v = B^k - 1)"},
         "variants": res,
     }
+    if clocks is not None:
+        out["clocks"] = clocks
     mp.mpdiv_destroy(ctx)
     return out
 
@@ -760,6 +858,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep", choices=["sweep", "mixed", "serve", "stress", "paper"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="sweep workload: leave out the mixed, serving and "
+                    "stress summaries at the end of the line")
     ap.add_argument("--products", default="clipped", choices=sorted(PRODUCT_FLAGS),
                     help="sweep workload: clipped products (default), the paper's full products, or full "
                     "products by the number-theoretic transform where it fits")

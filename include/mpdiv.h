@@ -131,8 +131,11 @@ int mpdiv_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, int32_t u_li
  * are device arrays; the host-side copies of u_len and v_len (u_len_host,
  * v_len_host, n_items entries each) are used to size and order the work.
  * Requirements as for mpdiv_batch, per item (r_len[i] >= v_len[i]).
- * When the same shape list is submitted again, the launch replays a captured
- * CUDA graph. */
+ * When the same shape list is submitted again (both length lists equal entry
+ * for entry), the launch replays a captured CUDA graph. The context's queue
+ * head and order array serve every call: the calls of one context run on the
+ * GPU one after another, whatever their streams, and a call with a new shape
+ * list first waits on the host for the previous call's launch to finish. */
 int mpdiv_batch_ragged(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, const int64_t *u_off,
                        const int32_t *u_len, const uint32_t *v, const int64_t *v_off, const int32_t *v_len,
                        uint32_t *q, const int64_t *q_off, const int32_t *q_len, uint32_t *r, const int64_t *r_off,
@@ -187,10 +190,13 @@ int mpdiv_debug_primitive(mpdiv_ctx *ctx, int32_t op, int64_t n_items, const uin
 int mpdiv_autotune(mpdiv_ctx *ctx, int32_t u_limbs, int32_t v_limbs, int32_t n_items);
 
 /* The launch shape the context uses for dividends of u_limbs digits: warps per
- * block, output columns per lane of the strip multiply and the Karatsuba
- * cutoff (0: never), tuned, configured or default. Any pointer may be NULL. */
+ * block, output columns per lane of the strip multiply, the Karatsuba cutoff
+ * (0: never) and the registers per thread of the plain kernel (64 or 128;
+ * 0: the 128-register build wherever the block size has one and shared memory
+ * already limits the SM to as few blocks as it allows), tuned, configured or
+ * default. Any pointer may be NULL. */
 int mpdiv_tuning(mpdiv_ctx *ctx, int32_t u_limbs, int32_t *warps, int32_t *mul_columns,
-                 int32_t *karatsuba_cutoff);
+                 int32_t *karatsuba_cutoff, int32_t *regs);
 
 /* Microbenchmark of the integer multiply pipe, the measured ceiling of the
  * roofline: kind 0 runs the strip multiply's digit product (mad.lo.cc /
@@ -280,18 +286,22 @@ int mpdiv_serve_replay(mpdiv_ctx *ctx, int64_t n, const int64_t *arrival_ns, con
  * The paper has no counterpart to this entry point; it exists for callers that
  * cannot allocate device memory when they divide (a memory pool that owns the
  * whole device, an allocator that forbids cudaMalloc after start-up, an
- * embedding with a fixed memory budget). It runs the same persistent
- * mixed-precision division kernel as mpdiv_batch_ragged, with the same
- * arguments and results (iters and products are not produced), but without a
- * context: it calls no cudaMalloc, cudaFree or other allocating routine and
- * captures no graph. Its queue head and size-ordered item list live in a fixed
- * scratch array in the library image, on every GPU that loads the library,
- * until the process exits.
+ * embedding with a fixed memory budget). It takes the same arguments as
+ * mpdiv_batch_ragged and returns the same q, r and status (iters and products
+ * are not produced), but runs without a context: it calls no cudaMalloc,
+ * cudaFree or other allocating routine and captures no graph. It runs the
+ * one-block-per-item queue kernel (16-warp blocks, 5 columns per lane, no
+ * Karatsuba, no tuned per-class shapes) over items ordered by a cost bucket,
+ * not mpdiv_batch_ragged's self-splitting persistent kernel, so its results
+ * are the same but its throughput is lower. Its queue head and ordered item
+ * list live in a fixed scratch array in the library image, on every GPU that
+ * loads the library, until the process exits.
  *  - At most MPDIV_NOALLOC_MAX_ITEMS items per call (the scratch holds one
  *    order slot per item); more returns MPDIV_EUNSUPPORTED with nothing run.
- *  - Runs on the current CUDA device. The first call on a device looks up the
- *    scratch array's device address (cudaGetSymbolAddress) once; make that
- *    first call outside any stream capture.
+ *  - Runs on the current CUDA device: every device pointer and the stream
+ *    must belong to it. The first call on a device looks up the scratch
+ *    array's device address (cudaGetSymbolAddress) once; make that first call
+ *    outside any stream capture.
  *  - Every call reuses the same scratch and clears what must start at zero.
  *    Calls whose work overlaps on the GPU (for example on two streams at once)
  *    race on the scratch: serialise them, for instance on one stream.

@@ -23,6 +23,7 @@ _BUILD = os.path.join(_HERE, "_build")
 SO_PATH = os.path.join(_BUILD, "libmpdiv.so")
 HEADER = os.path.join(_ROOT, "include", "mpdiv.h")
 SOURCES = ["mpdiv_p.cu", "mpdiv_p16.cu", "mpdiv_q.cu", "mpdiv_t.cu", "mpdiv_k1.cu", "mpdiv_k2.cu", "mpdiv_k4.cu", "mpdiv_k8.cu", "mpdiv_k16.cu",
+           "mpdiv_k4r.cu", "mpdiv_k8r.cu", "mpdiv_k16r.cu",
            "mpdiv_k32.cu", "mpdiv_n.cu", "mpdiv_n8.cu", "mpdiv_n16.cu", "mpdiv_n32.cu",
            "mpdiv_n2.cu", "mpdiv_n3.cu", "mpdiv_noalloc.cu", "mpdiv.cu", "mpdiv_tune.cu", "mpdiv_serve.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
@@ -109,7 +110,7 @@ _SIGS = {
     "mpdiv_debug_primitive": (ctypes.c_int, [_P, _I32, _I64, _P, _I32, _P, _I32, _I32, _P, _I32, _P, _I32, _P]),
     "mpdiv_mul_batch": (ctypes.c_int, [_P, _I64, _P, _P, _I32, _I64, _P, _I64, _P]),
     "mpdiv_measure_peak": (ctypes.c_int, [_P, _I32, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
-    "mpdiv_tuning": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "mpdiv_tuning": (ctypes.c_int, [_P, _I32] + [ctypes.POINTER(_I32)] * 4),
     "mpdiv_serve_start": (ctypes.c_int, [_P, ctypes.POINTER(mpdiv_serve_config)]),
     "mpdiv_serve_submit": (ctypes.c_int, [_P, _P, _I32, _P, _I32, ctypes.POINTER(_U64)]),
     "mpdiv_serve_poll": (ctypes.c_int, [_P, _U64, _P, _I32, _P, _I32, ctypes.POINTER(_I32), _I64]),
@@ -177,6 +178,23 @@ def _check_dev(*ts):
             raise ValueError("tensors must be contiguous CUDA tensors")
 
 
+def _one_device(*ts):
+    """The single CUDA device that every given tensor lives on (ValueError otherwise)."""
+    devs = {t.device for t in ts if t is not None}
+    if len(devs) != 1:
+        raise ValueError(f"tensors must all live on one CUDA device, got {sorted(str(d) for d in devs)}")
+    return devs.pop()
+
+
+def _host_lengths(t, n: int, name: str):
+    """A contiguous CPU int32 tensor of at least n digit counts (the C side reads n of them)."""
+    import torch
+
+    if t.device.type != "cpu" or t.dtype != torch.int32 or t.numel() < n:
+        raise ValueError(f"{name} must be a CPU int32 tensor with at least {n} entries")
+    return t.contiguous()
+
+
 # ---------------------------------------------------------------- context
 def mpdiv_init(device: int = 0, warps_per_block: int = 0, blocks_per_sm: int = 0, flags: int = 0,
                mul_columns: int = 0, karatsuba_cutoff: int = 0, transform_cutoff: int = 0):
@@ -214,13 +232,9 @@ def mpdiv_batch_ragged(ctx, u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r
     """Ragged batch over flat digit tensors with per-item int64 offsets and int32
     lengths (CUDA tensors); u_len_host / v_len_host are CPU int32 tensors."""
     _check_dev(u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r, r_off, r_len, status, iters, products)
-    if u_len_host is None:
-        u_len_host = u_len.cpu()
-    if v_len_host is None:
-        v_len_host = v_len.cpu()
-    u_len_host = u_len_host.contiguous()
-    v_len_host = v_len_host.contiguous()
     n = u_off.shape[0]
+    u_len_host = _host_lengths(u_len.cpu() if u_len_host is None else u_len_host, n, "u_len_host")
+    v_len_host = _host_lengths(v_len.cpu() if v_len_host is None else v_len_host, n, "v_len_host")
     _check(
         ctx,
         lib().mpdiv_batch_ragged(
@@ -234,16 +248,21 @@ def mpdiv_batch_ragged(ctx, u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r
 def mpdiv_batch_ragged_noalloc(u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r, r_off, r_len, status,
                                u_len_host=None, stream=None) -> int:
     """The allocation-free ragged launch (no context): same arrays as
-    mpdiv_batch_ragged. Returns the C return code (MPDIV_OK or a negative code)."""
+    mpdiv_batch_ragged, all on one CUDA device, on which the call runs (the C
+    entry point launches on the current device). Returns the C return code
+    (MPDIV_OK or a negative code)."""
+    import torch
+
     _check_dev(u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r, r_off, r_len, status)
-    if u_len_host is None:
-        u_len_host = u_len.cpu()
-    u_len_host = u_len_host.contiguous()
+    device = _one_device(u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r, r_off, r_len, status)
     n = u_off.shape[0]
-    return lib().mpdiv_batch_ragged_noalloc(
-        n, _ptr(u), _ptr(u_off), _ptr(u_len), _ptr(v), _ptr(v_off), _ptr(v_len), _ptr(q), _ptr(q_off),
-        _ptr(q_len), _ptr(r), _ptr(r_off), _ptr(r_len), _ptr(status), _ptr(u_len_host), _stream(stream),
-    )
+    u_len_host = _host_lengths(u_len.cpu() if u_len_host is None else u_len_host, n, "u_len_host")
+    with torch.cuda.device(device):
+        s = torch.cuda.current_stream(device).cuda_stream if stream is None else _stream(stream)
+        return lib().mpdiv_batch_ragged_noalloc(
+            n, _ptr(u), _ptr(u_off), _ptr(u_len), _ptr(v), _ptr(v_off), _ptr(v_len), _ptr(q), _ptr(q_off),
+            _ptr(q_len), _ptr(r), _ptr(r_off), _ptr(r_len), _ptr(status), _ptr(u_len_host), s,
+        )
 
 
 def mpdiv_debug_shinv(ctx, v, h_digits, out, iters, status, stream=None) -> None:
@@ -291,10 +310,12 @@ def mpdiv_autotune(ctx, u_limbs: int, v_limbs: int, n_items: int) -> int:
 
 
 def mpdiv_tuning(ctx, u_limbs: int):
-    """(warps per block, columns per lane, Karatsuba cutoff) used for dividends of u_limbs digits."""
-    w, t, k = _I32(), _I32(), _I32()
-    _check(ctx, lib().mpdiv_tuning(ctx, u_limbs, ctypes.byref(w), ctypes.byref(t), ctypes.byref(k)))
-    return w.value, t.value, k.value
+    """(warps per block, columns per lane, Karatsuba cutoff, registers per
+    thread) used for dividends of u_limbs digits (registers 0: chosen by
+    occupancy at launch)."""
+    w, t, k, g = _I32(), _I32(), _I32(), _I32()
+    _check(ctx, lib().mpdiv_tuning(ctx, u_limbs, ctypes.byref(w), ctypes.byref(t), ctypes.byref(k), ctypes.byref(g)))
+    return w.value, t.value, k.value, g.value
 
 
 # ---------------------------------------------------------------- serving

@@ -148,6 +148,12 @@ int mpdiv_default_kcut(mpdiv_ctx* ctx, int max_digits) {
   return 0;  // untuned: schoolbook only
 }
 
+int mpdiv_default_regs(mpdiv_ctx* ctx, int max_digits) {
+  std::lock_guard<std::mutex> g(ctx->tune_mu);
+  auto it = ctx->tuned.find(mpdiv_size_class(max_digits));
+  return it != ctx->tuned.end() ? it->second.regs : 0;
+}
+
 int mpdiv_size_class(int digits) {
   int c = 128;
   while (c < digits) c *= 2;
@@ -175,6 +181,12 @@ cudaError_t mpdiv_open_kernel_smem(void* k, int smem) {
 
 static int prepare_kernel(mpdiv_ctx* ctx, void* k, int smem) {
   return mpdiv_cuda_check(ctx, mpdiv_open_kernel_smem(k, smem), "cudaFuncSetAttribute(max dynamic shared memory)");
+}
+
+// The 128-register build of the plain kernel for a block of w warps (4, 8
+// or 16), or null.
+static void* wide_uniform_kernel(int w) {
+  return w == 4 ? mp_kernel_w4_wide() : w == 8 ? mp_kernel_w8_wide() : w == 16 ? mp_kernel_w16_wide() : nullptr;
 }
 
 // Resident blocks per SM of kernel k at that block size and shared memory (cached).
@@ -225,7 +237,10 @@ extern "C" int mpdiv_init(mpdiv_ctx** out, int device, const mpdiv_config* cfg) 
     }
   }
   if ((rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking),
-                             "cudaStreamCreate")) != MPDIV_OK) {
+                             "cudaStreamCreate")) != MPDIV_OK ||
+      (rc = mpdiv_cuda_check(ctx, cudaEventCreateWithFlags(&ctx->ragged_ev, cudaEventDisableTiming),
+                             "cudaEventCreate")) != MPDIV_OK) {
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     cudaFree(ctx->d_ntt);
     cudaFree(ctx->d_head);
     delete ctx;
@@ -246,6 +261,7 @@ extern "C" void mpdiv_destroy(mpdiv_ctx* ctx) {
   if (ctx->d_head) cudaFree(ctx->d_head);
   if (ctx->d_ntt) cudaFree(ctx->d_ntt);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->ragged_ev) cudaEventDestroy(ctx->ragged_ev);
   delete ctx;
 }
 
@@ -267,6 +283,21 @@ int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t st
   void* k = ntt_tables(ctx) ? ntt_kernel_for(KK_UNIFORM, warps) : kernel_for(KK_UNIFORM, warps);
   int rc = prepare_kernel(ctx, k, smem);
   if (rc) return rc;
+  // 128 registers per thread where the block size has such a build: when
+  // asked (tuned or configured), else when shared memory already holds the
+  // SM to as few blocks as that budget allows, so that it costs no occupancy
+  if (void* kw = ntt_tables(ctx) ? nullptr : wide_uniform_kernel(warps)) {
+    const int regs = L.regs > 0 ? L.regs : mpdiv_default_regs(ctx, max_digits);
+    bool wide = regs == 128;
+    if (regs == 0) {
+      if ((rc = prepare_kernel(ctx, kw, smem))) return rc;
+      wide = kernel_occupancy(ctx, kw, 32 * warps, smem) >= kernel_occupancy(ctx, k, 32 * warps, smem);
+    }
+    if (wide) {
+      if ((rc = prepare_kernel(ctx, kw, smem))) return rc;
+      k = kw;
+    }
+  }
   UniformArgs a{};
   a.u = L.u;
   a.v = L.v;
@@ -333,6 +364,7 @@ extern "C" int mpdiv_batch(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* u, i
   L.warps = 0;
   L.tcols = 0;
   L.kcut = -1;
+  L.regs = 0;
   return mpdiv_launch_uniform(ctx, L, (cudaStream_t)stream);
 }
 
@@ -406,15 +438,22 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
                   : (ntt_tables(ctx) ? ntt_kernel_for(KK_RAGGED, warps) : kernel_for(KK_RAGGED, warps));
   int rc = prepare_kernel(ctx, k, smem);
   if (rc) return rc;
-  // size-sorted order (cached by content of the shape list)
-  uint64_t hsh = 1469598103934665603ull;
-  for (int64_t i = 0; L.order == nullptr && i < L.n; i++) {
-    hsh = (hsh ^ (uint64_t)(uint32_t)L.u_len_host[i]) * 1099511628211ull;
-    hsh = (hsh ^ (uint64_t)(uint32_t)L.v_len_host[i]) * 1099511628211ull;
-  }
+  // size-sorted order, cached with a copy of the shape list it was made for:
+  // reused only when both length arrays are equal to the cached ones entry for
+  // entry
   std::lock_guard<std::mutex> g(ctx->ragged_mu);
-  const bool same_shapes = L.order != nullptr || (hsh == ctx->order_hash && L.n == ctx->order_n);
+  const bool same_shapes =
+      L.order != nullptr ||
+      (L.n == ctx->order_n && (size_t)L.n == ctx->order_u_len.size() &&
+       std::memcmp(ctx->order_u_len.data(), L.u_len_host, sizeof(int32_t) * L.n) == 0 &&
+       std::memcmp(ctx->order_v_len.data(), L.v_len_host, sizeof(int32_t) * L.n) == 0);
+  // launches with the context's queue head and order array are ordered on the
+  // GPU one after another, whatever their streams (ragged_ev marks the last one)
+  const bool ctx_queue = L.head == nullptr;
   if (!same_shapes) {
+    // the previous launch may still read the order array on another stream
+    if ((rc = mpdiv_cuda_check(ctx, cudaEventSynchronize(ctx->ragged_ev), "wait for the previous queue launch")))
+      return rc;
     std::vector<int32_t> order(L.n);
     std::iota(order.begin(), order.end(), 0);
     std::vector<double> cost(L.n);
@@ -437,7 +476,8 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
              ctx, cudaMemcpy(ctx->d_order, order.data(), sizeof(int32_t) * L.n, cudaMemcpyHostToDevice),
              "upload of the queue order")))
       return rc;
-    ctx->order_hash = hsh;
+    ctx->order_u_len.assign(L.u_len_host, L.u_len_host + L.n);
+    ctx->order_v_len.assign(L.v_len_host, L.v_len_host + L.n);
     ctx->order_n = L.n;
   }
   int occ = kernel_occupancy(ctx, k, 32 * warps, smem);
@@ -470,11 +510,16 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
   a.kcut = split ? -1 : mpdiv_default_kcut(ctx, max_u);
   a.ntt = ntt_tables(ctx);
   a.ntt_cut = ntt_cutoff(ctx);
+  if (ctx_queue &&
+      (rc = mpdiv_cuda_check(ctx, cudaStreamWaitEvent(stream, ctx->ragged_ev, 0), "order after the previous launch")))
+    return rc;
   if (!L.use_graph) {
     if ((rc = mpdiv_cuda_check(ctx, cudaMemsetAsync(a.head, 0, sizeof(int32_t), stream), "queue reset"))) return rc;
     void* args[] = {&a};
-    return mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * warps), args, smem, stream),
-                            "launch of the persistent division kernel");
+    rc = mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * warps), args, smem, stream),
+                          "launch of the persistent division kernel");
+    if (rc == MPDIV_OK && ctx_queue) rc = mpdiv_cuda_check(ctx, cudaEventRecord(ctx->ragged_ev, stream), "event");
+    return rc;
   }
   // CUDA graph: [reset queue head, persistent kernel], replayed while the
   // arguments are unchanged.
@@ -512,7 +557,9 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
   } else {
     ctx->graph_replays++;
   }
-  return mpdiv_cuda_check(ctx, cudaGraphLaunch(ctx->gexec, stream), "graph launch");
+  rc = mpdiv_cuda_check(ctx, cudaGraphLaunch(ctx->gexec, stream), "graph launch");
+  if (rc == MPDIV_OK && ctx_queue) rc = mpdiv_cuda_check(ctx, cudaEventRecord(ctx->ragged_ev, stream), "event");
+  return rc;
 }
 
 extern "C" int mpdiv_batch_ragged(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* u, const int64_t* u_off,
@@ -650,8 +697,9 @@ extern "C" int mpdiv_debug_primitive(mpdiv_ctx* ctx, int32_t op, int64_t n_items
 }
 
 extern "C" int mpdiv_tuning(mpdiv_ctx* ctx, int32_t u_limbs, int32_t* warps, int32_t* mul_columns,
-                            int32_t* karatsuba_cutoff) {
+                            int32_t* karatsuba_cutoff, int32_t* regs) {
   if (!ctx || u_limbs < 1) return MPDIV_EINVAL;
+  if (regs) *regs = mpdiv_default_regs(ctx, u_limbs);
   if (warps) *warps = mpdiv_default_warps(ctx, u_limbs);
   if (mul_columns) *mul_columns = mpdiv_default_tcols(ctx, u_limbs);
   if (karatsuba_cutoff) *karatsuba_cutoff = mpdiv_default_kcut(ctx, u_limbs);

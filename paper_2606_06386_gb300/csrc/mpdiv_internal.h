@@ -7,6 +7,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
@@ -29,6 +30,7 @@ struct mpdiv_ctx {
   std::mutex tune_mu;
   struct Shape {
     int warps, tcols, kcut;
+    int regs;  // registers per thread of the plain kernel: 64, 128, or 0 (chosen by occupancy)
   };
   std::map<int, Shape> tuned;
   // persistent launch: queue head, cached order, cached graph
@@ -39,8 +41,9 @@ struct mpdiv_ctx {
   int32_t* d_head = nullptr;
   int32_t* d_order = nullptr;
   size_t order_cap = 0;
-  uint64_t order_hash = 0;
+  std::vector<int32_t> order_u_len, order_v_len;  // the shape list the cached order was made for
   int64_t order_n = -1;
+  cudaEvent_t ragged_ev = nullptr;  // the last launch on the context's queue head and order array
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   mp::RaggedArgs g_args{};
@@ -61,6 +64,7 @@ struct UniformLaunch {
   int warps;  // 0: from the tuning table
   int tcols;  // 0: from the tuning table
   int kcut;   // -1: from the tuning table; 0: schoolbook only
+  int regs;   // registers per thread: 64, 128 (4, 8 and 16 warps), 0: from the tuning table, else by occupancy
 };
 
 struct RaggedLaunch {
@@ -97,6 +101,7 @@ int mpdiv_size_class(int digits);
 int mpdiv_default_warps(mpdiv_ctx* ctx, int max_digits);
 int mpdiv_default_tcols(mpdiv_ctx* ctx, int max_digits);
 int mpdiv_default_kcut(mpdiv_ctx* ctx, int max_digits);
+int mpdiv_default_regs(mpdiv_ctx* ctx, int max_digits);
 int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t stream);
 int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stream);
 void mpdiv_tune_load(mpdiv_ctx* ctx, const char* path);

@@ -12,6 +12,11 @@ void* mp_kernel_w8(int kind);  // also the self-splitting persistent kernel (8 -
 void* mp_kernel_w16(int kind);  // also the self-splitting persistent kernel (16 -> 8 -> 4 warps),
                                 // the one-block-per-item queue kernel and the shifted-inverse test entry
 void* mp_kernel_w32(int kind);
+// the plain division kernel with 128 registers per thread (mpdiv_k{4,8,16}r.cu):
+// 4 warps x 4 blocks, 8 warps x 2 blocks, 16 warps x 1 block per SM
+void* mp_kernel_w4_wide();
+void* mp_kernel_w8_wide();
+void* mp_kernel_w16_wide();
 void* mp_kernel_persistent(int warps);  // 8 (warps <= 8) or 16 warps per block
 void* mp_kernel_persistent8();          // mpdiv_p.cu
 void* mp_kernel_persistent16();         // mpdiv_p16.cu

@@ -44,7 +44,9 @@ constexpr int kOrder = 64 + 2 * kBuckets;
 __device__ __forceinline__ int cost_bucket(int n, int kl) {
   const long long a = (long long)max(1, n - kl + 1);
   const long long c = a * (long long)(n + kl) + 2 * a * min((long long)kl, a) + 64;
-  return min(kBuckets - 1, 63 - __clzll(c));
+  // lengths are validated on the host only, so keep the bucket in range for any
+  // device values (c >= 64 gives a bucket of at least 6)
+  return max(0, min(kBuckets - 1, 63 - __clzll((unsigned long long)max(c, 64LL))));
 }
 
 // One block: clear the head and counters, then order the items by cost bucket,

@@ -2,8 +2,9 @@
 // autotuning of block size, sequentialisation and multiplication
 // specialisation as future work): for a size class it times the plain kernel
 // at each candidate warps per block (1 and 2 for dividends of at most 1024
-// digits, then 4, 8, 16, 32) and columns per lane of the strip multiply (3, 5,
-// 7), then, in the full-product mode, at Karatsuba cutoffs for the Newton
+// digits, then 4, 8, 16, 32), columns per lane of the strip multiply (3, 5,
+// 7) and registers per thread (64, and 128 for 4, 8 and 16 warps), then, in
+// the full-product mode, at Karatsuba cutoffs for the Newton
 // step's full products (never, 2048, 1024, 512 digits), on synthetic
 // divisions, and records the fastest in the context's table, which can be
 // saved to and loaded from a text file (MPDIV_TUNE_FILE).
@@ -36,10 +37,15 @@ __global__ void k_fill(uint32_t* x, int64_t n_items, int digits, int64_t stride,
 void mpdiv_tune_load(mpdiv_ctx* ctx, const char* path) {
   FILE* f = fopen(path, "r");
   if (!f) return;
-  int cls, w, t, kc;
+  char line[128];
   std::lock_guard<std::mutex> g(ctx->tune_mu);
-  while (fscanf(f, "%d %d %d %d", &cls, &w, &t, &kc) == 4)
-    if (cls > 0 && w > 0 && w <= 32 && (t == 3 || t == 5 || t == 7) && kc >= 0) ctx->tuned[cls] = {w, t, kc};
+  while (fgets(line, sizeof line, f)) {
+    int cls, w, t, kc, regs = 0;  // the register budget column is optional (0: by occupancy)
+    if (sscanf(line, "%d %d %d %d %d", &cls, &w, &t, &kc, &regs) < 4) continue;
+    if (cls > 0 && w > 0 && w <= 32 && (t == 3 || t == 5 || t == 7) && kc >= 0 &&
+        (regs == 0 || regs == 64 || regs == 128))
+      ctx->tuned[cls] = {w, t, kc, regs};
+  }
   fclose(f);
 }
 
@@ -48,7 +54,7 @@ static void tune_save(mpdiv_ctx* ctx, const char* path) {
   if (!f) return;
   std::lock_guard<std::mutex> g(ctx->tune_mu);
   for (auto& kv : ctx->tuned)
-    fprintf(f, "%d %d %d %d\n", kv.first, kv.second.warps, kv.second.tcols, kv.second.kcut);
+    fprintf(f, "%d %d %d %d %d\n", kv.first, kv.second.warps, kv.second.tcols, kv.second.kcut, kv.second.regs);
   fclose(f);
 }
 
@@ -64,10 +70,20 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
   const size_t n = (size_t)n_items;
   int rc = MPDIV_OK;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  int best_w = 0, best_t = 5, best_k = 0;
+  int best_w = 0, best_t = 5, best_k = 0, best_r = 64;
   float best_ms = 1e30f;
-  const int w_first = u_limbs <= 1024 ? 0 : 2;  // index into 1, 2, 4, 8, 16, 32 warps
-  const int n_shape = (6 - w_first) * 3;
+  // launch shapes: warps per block (one and two warps only for dividends of at
+  // most 1024 digits) x columns per lane x registers per thread (128 where the
+  // block size has that build), schoolbook products
+  struct Cand {
+    int w, t, regs;
+  };
+  std::vector<Cand> shapes;
+  for (int w = u_limbs <= 1024 ? 1 : 4; w <= 32; w *= 2)
+    for (int t = 3; t <= 7; t += 2)
+      for (int regs : {64, 128})
+        if (regs == 64 || w == 4 || w == 8 || w == 16) shapes.push_back({w, t, regs});
+  const int n_shape = (int)shapes.size();
   if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&u, n * u_limbs * 4), "autotune alloc"))) goto done;
   if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&v, n * v_limbs * 4), "autotune alloc"))) goto done;
   if ((rc = mpdiv_cuda_check(ctx, cudaMalloc(&q, n * u_limbs * 4), "autotune alloc"))) goto done;
@@ -77,13 +93,13 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
   k_fill<<<256, 256>>>(v, n_items, v_limbs, v_limbs, 0x7654321ull);
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  // warps x columns with schoolbook products (one- and two-warp blocks only
-  // for dividends of at most 1024 digits), then the Karatsuba cutoff (0 =
-  // never, 2048, 1024, 512 digits) at the best shape
+  // the shapes, then the Karatsuba cutoff (0 = never, 2048, 1024, 512 digits)
+  // at the best shape
   for (int cand = 0; cand < n_shape + 3; cand++) {
     const bool shape = cand < n_shape;
-    const int w = shape ? 1 << (w_first + cand / 3) : best_w;
-    const int tc = shape ? 3 + 2 * (cand % 3) : best_t;
+    const int w = shape ? shapes[cand].w : best_w;
+    const int tc = shape ? shapes[cand].t : best_t;
+    const int regs = shape ? shapes[cand].regs : best_r;
     const int kc = shape ? 0 : (2048 >> (cand - n_shape));
     // Karatsuba splits only the full Newton-step products of the paper's
     // full-product mode; clipped steps leave nothing for it to split
@@ -105,6 +121,7 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
     L.warps = w;
     L.tcols = tc;
     L.kcut = kc;
+    L.regs = regs;
     if (mpdiv_launch_uniform(ctx, L, 0) != MPDIV_OK) continue;  // e.g. does not fit
     cudaEventRecord(e0, 0);
     mpdiv_launch_uniform(ctx, L, 0);
@@ -118,6 +135,7 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
       best_w = w;
       best_t = tc;
       best_k = kc;
+      best_r = regs;
     }
   }
   if (best_w == 0) {
@@ -126,7 +144,7 @@ extern "C" int mpdiv_autotune(mpdiv_ctx* ctx, int32_t u_limbs, int32_t v_limbs, 
   }
   {
     std::lock_guard<std::mutex> g(ctx->tune_mu);
-    ctx->tuned[mpdiv_size_class(u_limbs)] = {best_w, best_t, best_k};
+    ctx->tuned[mpdiv_size_class(u_limbs)] = {best_w, best_t, best_k, best_r};
   }
   if (const char* tf = getenv("MPDIV_TUNE_FILE")) tune_save(ctx, tf);
   rc = best_w;

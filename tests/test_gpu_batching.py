@@ -174,7 +174,7 @@ def test_autotune_picks_a_launch_shape():
     try:
         w = mp.mpdiv_autotune(c, 1024, 512, 1024)
         assert w in (1, 2, 4, 8, 16, 32)
-        tw, tc, kc = mp.mpdiv_tuning(c, 1000)
+        tw, tc, kc, _ = mp.mpdiv_tuning(c, 1000)
         assert tw == w and tc in (3, 5, 7) and kc in (0, 512, 1024, 2048)
     finally:
         mp.mpdiv_destroy(c)
@@ -206,5 +206,69 @@ def test_bench_mixed_configuration_every_item():
             mp.mpdiv_autotune(c, n, n // 2, 1024)
         u_len, v_len = I.mixed_sizes()
         _ragged(u_len, v_len, seed=I.SEED_BASE + 2, c=c)
+    finally:
+        mp.mpdiv_destroy(c)
+
+
+def test_order_cache_follows_the_shape_list_exactly():
+    # the cached size-sorted order is reused only for a shape list equal entry
+    # for entry: shape lists with the same item count, the same lengths in
+    # another order, and one divisor length changed, each in turn on one
+    # context, every item against the oracle (and each replayed as a graph)
+    import paper_2606_06386_gb300 as mp
+
+    c = mp.mpdiv_init(0)
+    try:
+        rnd = np.random.default_rng(11)
+        u_a = rnd.integers(200, 3000, size=96).astype(np.int32)
+        v_a = np.maximum(1, (u_a * rnd.uniform(0.2, 1.0, size=96)).astype(np.int32)).astype(np.int32)
+        u_b, v_b = u_a[::-1].copy(), v_a[::-1].copy()
+        u_c, v_c = u_a.copy(), v_a.copy()
+        v_c[50] = max(1, v_c[50] // 3)
+        for k, (u_len, v_len) in enumerate([(u_a, v_a), (u_b, v_b), (u_a, v_a), (u_c, v_c), (u_a, v_a)]):
+            _ragged(u_len, v_len, seed=30 + k, c=c)
+    finally:
+        mp.mpdiv_destroy(c)
+
+
+def test_ragged_calls_on_two_streams_of_one_context():
+    # two calls of one context on two streams, without a host wait between
+    # them, with different shape lists: the context orders them on the GPU
+    import torch
+    import paper_2606_06386_gb300 as mp
+
+    c = mp.mpdiv_init(0)
+    try:
+        sets = []
+        for seed, n in ((61, 120), (62, 80)):
+            rnd = np.random.default_rng(seed)
+            u_len = rnd.integers(100, 2500, size=n).astype(np.int32)
+            v_len = np.maximum(1, (u_len * rnd.uniform(0.2, 1.0, size=n)).astype(np.int32)).astype(np.int32)
+            u_flat, u_off, v_flat, v_off = I.ragged_operands(u_len, v_len, seed=seed)
+            q_len, r_len = u_len.copy(), v_len.copy()
+            q_off = np.concatenate([[0], np.cumsum(q_len)[:-1]]).astype(np.int64)
+            r_off = np.concatenate([[0], np.cumsum(r_len)[:-1]]).astype(np.int64)
+            T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")  # noqa: E731
+            q = torch.full((int(q_len.sum()),), -1, dtype=torch.int32, device="cuda:0")
+            r = torch.full((int(r_len.sum()),), -1, dtype=torch.int32, device="cuda:0")
+            st = torch.full((n,), -7, dtype=torch.int32, device="cuda:0")
+            args = (dev(u_flat), T(u_off), T(u_len), dev(v_flat), T(v_off), T(v_len), q, T(q_off), T(q_len), r,
+                    T(r_off), T(r_len), st)
+            host = (u_flat, u_off, u_len, v_flat, v_off, v_len, q_off, q_len, r_off, r_len)
+            sets.append((args, host, q, r, st))
+        torch.cuda.synchronize()
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        for _ in range(3):
+            for (args, *_), s in zip(sets, streams):
+                mp.mpdiv_batch_ragged(c, *args, stream=s)
+        torch.cuda.synchronize()
+        for args, host, q, r, st in sets:
+            qo, ro, so, _ = oracle.divmod_ragged_u32(*host)
+            assert (st.cpu().numpy() == so).all()
+            Q, R = host_u32(q), host_u32(r)
+            u_flat, u_off, u_len, v_flat, v_off, v_len, q_off, q_len, r_off, r_len = host
+            for i in range(len(u_len)):
+                assert (Q[q_off[i]:q_off[i] + q_len[i]] == qo[q_off[i]:q_off[i] + q_len[i]]).all(), i
+                assert (R[r_off[i]:r_off[i] + r_len[i]] == ro[r_off[i]:r_off[i] + r_len[i]]).all(), i
     finally:
         mp.mpdiv_destroy(c)

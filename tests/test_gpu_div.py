@@ -315,3 +315,31 @@ def test_bench_sweep_configuration_sampled():
             assert_same(host_u32(q)[idx], host_u32(r)[idx], st.cpu().numpy()[idx], Qo, Ro, So)
     finally:
         mp.mpdiv_destroy(c)
+
+
+@pytest.mark.parametrize("regs", [64, 128])
+@pytest.mark.parametrize("n,warps,cols", [(2048, 4, 3), (4096, 4, 5), (8192, 8, 5), (8192, 16, 7)])
+def test_register_budgets_of_the_plain_kernel(tmp_path, monkeypatch, n, warps, cols, regs):
+    # the plain kernel's 64- and 128-register builds (the latter for 4, 8 and
+    # 16 warps), chosen through a tuning file, give the oracle's digits
+    import paper_2606_06386_gb300 as mp
+
+    f = tmp_path / "tune.txt"
+    f.write_text(f"{n} {warps} {cols} 0 {regs}\n")
+    monkeypatch.setenv("MPDIV_TUNE_FILE", str(f))
+    c = mp.mpdiv_init(0)
+    monkeypatch.delenv("MPDIV_TUNE_FILE")
+    try:
+        assert mp.mpdiv_tuning(c, n) == (warps, cols, 0, regs)
+        import torch
+
+        U, V = I.sweep(n, n // 2, 24)
+        q = torch.zeros((24, n // 2 + 1), dtype=torch.int32, device="cuda:0")
+        r = torch.zeros((24, n // 2), dtype=torch.int32, device="cuda:0")
+        st = torch.full((24,), -1, dtype=torch.int32, device="cuda:0")
+        mp.mpdiv_batch(c, dev(U), dev(V), q, r, st)
+        torch.cuda.synchronize()
+        Qo, Ro, So = oracle_uniform(U, V, n // 2 + 1, n // 2)
+        assert_same(host_u32(q), host_u32(r), st.cpu().numpy(), Qo, Ro, So)
+    finally:
+        mp.mpdiv_destroy(c)
