@@ -59,6 +59,7 @@ UNIT = "div/s"
 # the default), the paper's full products, full products by the
 # number-theoretic transform where it fits (MPDIV_FLAG_NTT_PRODUCTS)
 PRODUCT_FLAGS = {"clipped": 0, "full": 2, "ntt": 6}
+PERSISTENT_QUEUE = 8  # MPDIV_FLAG_PERSISTENT_QUEUE: ragged batches by the self-splitting persistent kernel
 SM_COUNT_GB300 = 152
 PRODUCTS_PER_CLK_SM = 32  # 64 32-bit IMAD results/clk/SM, two (lo, hi) per 32x32->64 digit product
 SM_MAX_MHZ = 2070.0
@@ -335,14 +336,33 @@ def run_sweep(args, dev, dist, rank, ws):
     bv = torch.cat([d["v"].reshape(-1) for d in sizes])
     bargs = [bu, td(offs(u_len)), td(u_len), bv, td(offs(v_len)), td(v_len), bq, td(offs(q_len)), td(q_len), br,
              td(offs(r_len)), td(r_len), bst]
-    batched = lambda: mp.mpdiv_batch_ragged(ctx, *bargs, None, None, torch.from_numpy(u_len),  # noqa: E731
+    q_plain = torch.cat([d["q"].reshape(-1) for d in sizes])
+    r_plain = torch.cat([d["r"].reshape(-1) for d in sizes])
+
+    def batched_form(c):
+        """(ms, same digits as the plain launches) of the step's divisions in one call on context c."""
+        run = lambda: mp.mpdiv_batch_ragged(c, *bargs, None, None, torch.from_numpy(u_len),  # noqa: E731
                                             torch.from_numpy(v_len), stream)
-    batched()
-    torch.cuda.synchronize(dev)
-    same = (int((bst != 0).sum().item()) == 0 and torch.equal(bq, torch.cat([d["q"].reshape(-1) for d in sizes]))
-            and torch.equal(br, torch.cat([d["r"].reshape(-1) for d in sizes])))
-    ms_batched = _time(batched, stream, K)
-    del bu, bv, bq, br
+        bq.zero_()
+        br.zero_()
+        bst.fill_(-1)
+        run()
+        torch.cuda.synchronize(dev)
+        ok = int((bst != 0).sum().item()) == 0 and torch.equal(bq, q_plain) and torch.equal(br, r_plain)
+        for _ in range(2):
+            run()
+        return _time(run, stream, K), ok
+
+    # the default form (one plain launch per size class, forked in one graph)
+    # on the sweep's tuned context; the self-splitting persistent kernel on a
+    # context tuned the same way
+    ms_batched, same = batched_form(ctx)
+    ctx_p = mp.mpdiv_init(dev.index or 0, flags=PRODUCT_FLAGS[args.products] | PERSISTENT_QUEUE)
+    for d in sizes:
+        mp.mpdiv_autotune(ctx_p, d["n"], d["kl"], d["b"])
+    ms_persist, same_p = batched_form(ctx_p)
+    mp.mpdiv_destroy(ctx_p)
+    del bu, bv, bq, br, q_plain, r_plain
 
     # roofline of the dominant launch (2^18-bit dividends)
     big = max(range(len(sizes)), key=lambda i: per_size_ms[i])
@@ -398,8 +418,16 @@ def run_sweep(args, dev, dist, rank, ws):
         "batched_single_launch": {"div_per_s": items_step * ws / (ms_batched / 1e3), "ms": ms_batched,
                                   "over_plain": (items_step * ws / (ms_batched / 1e3)) / value,
                                   "same_digits_as_plain": same,
-                                  "how": "the step's divisions as one persistent launch over the size-sorted queue "
-                                         "(mpdiv_batch_ragged, CUDA graph), timed after the plain launches"},
+                                  "how": "the step's divisions in one mpdiv_batch_ragged call, replayed as one CUDA "
+                                         "graph: one plain launch per size class with its tuned shape, the four "
+                                         "launches forked as graph branches; timed after the plain launches",
+                                  "persistent_queue": {"div_per_s": items_step * ws / (ms_persist / 1e3),
+                                                       "ms": ms_persist,
+                                                       "over_plain": (items_step * ws / (ms_persist / 1e3)) / value,
+                                                       "same_digits_as_plain": same_p,
+                                                       "how": "MPDIV_FLAG_PERSISTENT_QUEUE: one launch of the "
+                                                              "self-splitting persistent kernel over the size-sorted "
+                                                              "queue"}},
         "gpu_launches": len(sizes) * K,
     }
     clocks = clk.summary()
@@ -447,7 +475,7 @@ def other_configs_summary(mp, ctx, dev, stream, args):
     loads = {}
     for k, x in sv.items():
         d = {"div_s": _sig(x["sustained_div_per_s"]), "p50_ms": _sig(x["p50_ms"], 3), "p99_ms": _sig(x["p99_ms"], 3),
-             "ok": x["ok"], "clk": _clk(x["clocks"])}
+             "ok": x["ok"], "batch": _sig(x["mean_batch"], 3), "clk": _clk(x["clocks"])}
         if "runs" in x:
             d["p99_ms_runs"] = [_sig(r["p99_ms"], 3) for r in x["runs"]]
             d["ok"] = min(r["ok"] for r in x["runs"])

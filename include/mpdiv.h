@@ -77,6 +77,14 @@ extern "C" {
                                       sizes (Section 6); same digits, fewer instructions for
                                       long operands */
 
+#define MPDIV_FLAG_PERSISTENT_QUEUE 8 /* ragged batches and serving run the self-splitting
+                                         persistent kernel over one size-sorted queue (blocks
+                                         split into halves and quarters for smaller items);
+                                         default: one plain launch per size class of the
+                                         batch, each with that class's tuned shape over its
+                                         items in cost order, the launches forked as
+                                         branches of one CUDA graph. Same q and r. */
+
 typedef struct mpdiv_ctx mpdiv_ctx; /* opaque; owned by the library */
 
 typedef struct mpdiv_config {
@@ -91,6 +99,9 @@ typedef struct mpdiv_config {
                            table (never if untuned) */
   int transform_cutoff; /* with MPDIV_FLAG_NTT_PRODUCTS: products whose operands have at least
                            this many digits together use the transform (0: 4096) */
+  int registers;        /* registers per thread of the plain kernel: 64, or 128 (block sizes of
+                           4, 8 and 16 warps, which have such a build); 0: per size class
+                           from the tuning table, else 64 */
 } mpdiv_config;
 
 /* Create a context on CUDA device `device` (cfg may be NULL for defaults).
@@ -123,8 +134,14 @@ int mpdiv_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, int32_t u_li
                 int64_t q_stride, uint32_t *r, int32_t r_limbs, int64_t r_stride, int32_t *status, int32_t *iters,
                 int64_t *products, void *stream);
 
-/* Ragged batch of mixed precisions in one persistent launch: items are taken
- * largest-first from a size-sorted queue by resident blocks. Item i reads
+/* Ragged batch of mixed precisions in one call. By default the items are
+ * grouped by the size class of their dividend (at most 1024, 2048, 4096, 8192
+ * digits, more), ordered most expensive first within each class, and each
+ * class runs as one plain launch with that class's tuned shape; the class
+ * launches are independent branches of one CUDA graph, so that the blocks of
+ * one class fill the last wave of another. With MPDIV_FLAG_PERSISTENT_QUEUE
+ * the batch is one launch of the self-splitting persistent kernel, whose
+ * resident blocks take items largest-first from a size-sorted queue. Item i reads
  * u + u_off[i] (u_len[i] digits), v + v_off[i] (v_len[i] digits) and writes
  * q + q_off[i] (q_len[i] digits), r + r_off[i] (r_len[i] digits), status[i],
  * iters[i] and products[i] (each may be NULL). Offsets are in digits. u_off..r_len and status
@@ -192,9 +209,8 @@ int mpdiv_autotune(mpdiv_ctx *ctx, int32_t u_limbs, int32_t v_limbs, int32_t n_i
 /* The launch shape the context uses for dividends of u_limbs digits: warps per
  * block, output columns per lane of the strip multiply, the Karatsuba cutoff
  * (0: never) and the registers per thread of the plain kernel (64 or 128;
- * 0: the 128-register build wherever the block size has one and shared memory
- * already limits the SM to as few blocks as it allows), tuned, configured or
- * default. Any pointer may be NULL. */
+ * 0: untuned, which runs 64), tuned, configured or default. Any pointer may be
+ * NULL. */
 int mpdiv_tuning(mpdiv_ctx *ctx, int32_t u_limbs, int32_t *warps, int32_t *mul_columns,
                  int32_t *karatsuba_cutoff, int32_t *regs);
 
@@ -222,10 +238,16 @@ int mpdiv_mul_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, const ui
 
 /* ---------------------------------------------------------------- serving
  * Continuous batching: a host scheduler thread admits submitted requests into
- * device-resident operand pools (by digit footprint), launches batches of
- * admitted requests as slots free up, with several batches in flight on
- * separate streams, and publishes results. Requests that arrive while batches
- * run join the next launch. */
+ * device-resident operand pools, launches batches of admitted requests as
+ * slots free up, with several batches in flight on separate streams, and
+ * publishes results. Requests that arrive while batches run join the next
+ * launch. Admission is by footprint: a request's footprint class is the size
+ * class of its dividend (class 0: at most 1024 digits, 1: 2048, 2: 4096,
+ * 3: 8192, 4: more), which sets the shared memory and block shape its
+ * division needs; each class has its own share of the operand pool, and a
+ * batch holds requests of one class only, so that a large request never sets
+ * the launch shape of small ones. Batches of different classes run at once. */
+#define MPDIV_SERVE_CLASSES 5
 typedef struct mpdiv_serve_config {
   int64_t pool_digits;  /* digits of device operand/result pool (0: 64 Mi digits) */
   int32_t max_batch;    /* most requests per batch (0: 4096) */
@@ -244,10 +266,11 @@ int mpdiv_serve_start(mpdiv_ctx *ctx, const mpdiv_serve_config *cfg);
 
 /* Submit one division from host memory; the operands are copied before the
  * call returns. *ticket identifies the request. MPDIV_EBUSY when the request
- * would exceed max_pending, finds the pool full (retry later) or can never fit
- * it, or when the ticket 2*max_pending (rounded up to a power of two) before
- * it has not been polled yet; MPDIV_EUNSUPPORTED for sizes beyond
- * MPDIV_MAX_LIMBS. Thread-safe. */
+ * would exceed max_pending, finds its class's share of the pool full (retry
+ * later) or can never fit it, or when the ticket 2*max_pending (rounded up to
+ * a power of two) before it has not been polled yet; MPDIV_EUNSUPPORTED for
+ * sizes beyond MPDIV_MAX_LIMBS; MPDIV_ECUDA once a batch has failed to launch
+ * (the server then refuses work until it is stopped). Thread-safe. */
 int mpdiv_serve_submit(mpdiv_ctx *ctx, const uint32_t *u_host, int32_t u_len, const uint32_t *v_host,
                        int32_t v_len, uint64_t *ticket);
 
@@ -257,7 +280,10 @@ int mpdiv_serve_submit(mpdiv_ctx *ctx, const uint32_t *u_host, int32_t u_len, co
  * status to *status. A finished ticket can be polled once; afterwards it is
  * MPDIV_EINVAL. Thread-safe; a finished ticket is collected without the
  * server's lock. timeout_us > 0 waits up to that long for completion
- * (MPDIV_ETIMEDOUT after); 0 returns at once. */
+ * (MPDIV_ETIMEDOUT after); 0 returns at once. A request whose batch failed to
+ * launch, or that was still queued when a batch failed, finishes with status
+ * MPDIV_ST_INTERNAL and zero digits: its poll collects it and returns
+ * MPDIV_ECUDA. */
 int mpdiv_serve_poll(mpdiv_ctx *ctx, uint64_t ticket, uint32_t *q_host, int32_t q_cap, uint32_t *r_host,
                      int32_t r_cap, int32_t *status, int64_t timeout_us);
 
@@ -266,8 +292,18 @@ int mpdiv_serve_poll(mpdiv_ctx *ctx, uint64_t ticket, uint32_t *q_host, int32_t 
 int mpdiv_serve_stop(mpdiv_ctx *ctx);
 
 /* Counters of the server: completed requests, launches, and the sum of
- * requests per launch (for the mean batch size). Any pointer may be NULL. */
-int mpdiv_serve_stats(mpdiv_ctx *ctx, int64_t *completed, int64_t *launches, int64_t *batched_items);
+ * requests per launch (for the mean batch size); per footprint class of a
+ * launch (the class of its largest dividend; MPDIV_SERVE_CLASSES entries
+ * each), the launches and their requests. Any pointer may be NULL. */
+int mpdiv_serve_stats(mpdiv_ctx *ctx, int64_t *completed, int64_t *launches, int64_t *batched_items,
+                      int64_t *class_launches, int64_t *class_items);
+
+/* Test entry: the server's launch with index launch_index (0 for the first
+ * launch since mpdiv_serve_start; -1: none) fails on the host, before any of
+ * its copies or kernels reach the GPU, as a failed launch would. This drives
+ * the failure path (failed requests, MPDIV_ECUDA from poll and submit) without
+ * a GPU fault. MPDIV_ESTATE if no server runs. */
+int mpdiv_debug_serve_fail_launch(mpdiv_ctx *ctx, int64_t launch_index);
 
 /* Open-loop replay of an arrival stream against the running server, for
  * latency measurement: request i (operands at u + u_off[i], v + v_off[i] in

@@ -37,8 +37,10 @@ MPDIV_ST_Q_OVERFLOW, MPDIV_ST_INTERNAL = 3, 4
 MPDIV_FLAG_INJECT_LAMBDA = 1
 MPDIV_FLAG_FULL_PRODUCTS = 2
 MPDIV_FLAG_NTT_PRODUCTS = 4
+MPDIV_FLAG_PERSISTENT_QUEUE = 8
 MPDIV_MAX_LIMBS = 16384
 MPDIV_NOALLOC_MAX_ITEMS = 65536
+MPDIV_SERVE_CLASSES = 5
 
 _lock = threading.Lock()
 _lib = None
@@ -83,7 +85,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 class mpdiv_config(ctypes.Structure):
     _fields_ = [("warps_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("flags", ctypes.c_int),
                 ("mul_columns", ctypes.c_int), ("karatsuba_cutoff", ctypes.c_int),
-                ("transform_cutoff", ctypes.c_int)]
+                ("transform_cutoff", ctypes.c_int), ("registers", ctypes.c_int)]
 
 
 class mpdiv_serve_config(ctypes.Structure):
@@ -115,7 +117,8 @@ _SIGS = {
     "mpdiv_serve_submit": (ctypes.c_int, [_P, _P, _I32, _P, _I32, ctypes.POINTER(_U64)]),
     "mpdiv_serve_poll": (ctypes.c_int, [_P, _U64, _P, _I32, _P, _I32, ctypes.POINTER(_I32), _I64]),
     "mpdiv_serve_stop": (ctypes.c_int, [_P]),
-    "mpdiv_serve_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "mpdiv_serve_stats": (ctypes.c_int, [_P] + [ctypes.POINTER(_I64)] * 5),
+    "mpdiv_debug_serve_fail_launch": (ctypes.c_int, [_P, _I64]),
     "mpdiv_batch_ragged_noalloc": (ctypes.c_int, [_I64] + [_P] * 15),
     "mpdiv_serve_replay": (
         ctypes.c_int,
@@ -197,8 +200,9 @@ def _host_lengths(t, n: int, name: str):
 
 # ---------------------------------------------------------------- context
 def mpdiv_init(device: int = 0, warps_per_block: int = 0, blocks_per_sm: int = 0, flags: int = 0,
-               mul_columns: int = 0, karatsuba_cutoff: int = 0, transform_cutoff: int = 0):
-    cfg = mpdiv_config(warps_per_block, blocks_per_sm, flags, mul_columns, karatsuba_cutoff, transform_cutoff)
+               mul_columns: int = 0, karatsuba_cutoff: int = 0, transform_cutoff: int = 0, registers: int = 0):
+    cfg = mpdiv_config(warps_per_block, blocks_per_sm, flags, mul_columns, karatsuba_cutoff, transform_cutoff,
+                       registers)
     h = _P()
     _check(None, lib().mpdiv_init(ctypes.byref(h), device, ctypes.byref(cfg)))
     return h
@@ -311,8 +315,7 @@ def mpdiv_autotune(ctx, u_limbs: int, v_limbs: int, n_items: int) -> int:
 
 def mpdiv_tuning(ctx, u_limbs: int):
     """(warps per block, columns per lane, Karatsuba cutoff, registers per
-    thread) used for dividends of u_limbs digits (registers 0: chosen by
-    occupancy at launch)."""
+    thread) used for dividends of u_limbs digits (registers 0: untuned, 64)."""
     w, t, k, g = _I32(), _I32(), _I32(), _I32()
     _check(ctx, lib().mpdiv_tuning(ctx, u_limbs, ctypes.byref(w), ctypes.byref(t), ctypes.byref(k), ctypes.byref(g)))
     return w.value, t.value, k.value, g.value
@@ -344,10 +347,15 @@ def mpdiv_serve_poll(ctx, ticket: int, q_cap: int, r_cap: int, timeout_us: int =
     q = np.zeros(q_cap, np.uint32)
     r = np.zeros(r_cap, np.uint32)
     st = _I32()
+    st.value = -1
     rc = lib().mpdiv_serve_poll(ctx, ticket, q.ctypes.data, q_cap, r.ctypes.data, r_cap, ctypes.byref(st), timeout_us)
     if rc == MPDIV_PENDING or rc == MPDIV_ETIMEDOUT:
         return rc, None, None, None
-    _check(ctx, rc)
+    try:
+        _check(ctx, rc)
+    except MpdivError as e:
+        e.status = st.value  # a failed request's status (MPDIV_ST_INTERNAL), -1 if none was written
+        raise
     return rc, q, r, st.value
 
 
@@ -355,10 +363,20 @@ def mpdiv_serve_stop(ctx) -> None:
     _check(ctx, lib().mpdiv_serve_stop(ctx))
 
 
-def mpdiv_serve_stats(ctx):
+def mpdiv_serve_stats(ctx, by_class: bool = False):
+    """(completed, launches, batched items); with by_class also the launches and
+    their requests per footprint class (two lists of MPDIV_SERVE_CLASSES)."""
     c, l, b = _I64(), _I64(), _I64()
-    _check(ctx, lib().mpdiv_serve_stats(ctx, ctypes.byref(c), ctypes.byref(l), ctypes.byref(b)))
+    cl, ci = (_I64 * MPDIV_SERVE_CLASSES)(), (_I64 * MPDIV_SERVE_CLASSES)()
+    _check(ctx, lib().mpdiv_serve_stats(ctx, ctypes.byref(c), ctypes.byref(l), ctypes.byref(b), cl, ci))
+    if by_class:
+        return c.value, l.value, b.value, list(cl), list(ci)
     return c.value, l.value, b.value
+
+
+def mpdiv_debug_serve_fail_launch(ctx, launch_index: int) -> None:
+    """Test entry: the server's launch with this index fails on the host (-1: none)."""
+    _check(ctx, lib().mpdiv_debug_serve_fail_launch(ctx, launch_index))
 
 
 def mpdiv_serve_replay(ctx, arrival_ns, u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r, r_off, r_len,

@@ -20,6 +20,13 @@ struct UniformArgs {
   int kcut;   // Karatsuba cutoff for full products (0: schoolbook only)
   const uint32_t* ntt;  // transform tables for full products (null: strip products only)
   int ntt_cut;          // the transform for products of at least this many digits
+  // Item list of a ragged batch (null: item i at the strides and digit counts
+  // above): the launch's i-th division is item list[i], whose operands and
+  // results are at the offsets and digit counts of the arrays below, and
+  // whose status (iterations, products) go to index list[i].
+  const int32_t* list;
+  const int64_t *u_off, *v_off, *q_off, *r_off;
+  const int32_t *u_len, *v_len, *q_len, *r_len;
 };
 
 struct RaggedArgs {

@@ -7,8 +7,10 @@
 
 namespace mp {
 
-// Plain launch: block b handles items b, b + gridDim.x, ... (NTT: full
-// products may use the transform, with its scratch after the item's layout)
+// Plain launch: block b handles items b, b + gridDim.x, ... of a uniform
+// batch, or of a ragged batch's item list (a.list: one size class of a
+// ragged batch, largest first). NTT: full products may use the transform,
+// with its scratch after the item's layout.
 template <int NW, int MINB, bool NTT = false>
 __global__ void __launch_bounds__(NW * 32, MINB) k_div_uniform(UniformArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
@@ -16,16 +18,29 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_uniform(UniformArgs a) {
   Blk b = make_block<NW>(red);
   b.tcols = a.tcols;
   b.kcut = a.kcut;
-  for (int64_t item = blockIdx.x; item < a.n; item += gridDim.x) {
+  for (int64_t slot = blockIdx.x; slot < a.n; slot += gridDim.x) {
     ItemIO io;
-    io.u = a.u + item * a.us;
-    io.un = a.un;
-    io.v = a.v + item * a.vs;
-    io.vn = a.vn;
-    io.q = a.q + item * a.qs;
-    io.qn = a.qn;
-    io.r = a.r + item * a.rs;
-    io.rn = a.rn;
+    int64_t item = slot;
+    if (a.list == nullptr) {
+      io.u = a.u + item * a.us;
+      io.un = a.un;
+      io.v = a.v + item * a.vs;
+      io.vn = a.vn;
+      io.q = a.q + item * a.qs;
+      io.qn = a.qn;
+      io.r = a.r + item * a.rs;
+      io.rn = a.rn;
+    } else {
+      item = a.list[slot];
+      io.u = a.u + a.u_off[item];
+      io.un = a.u_len[item];
+      io.v = a.v + a.v_off[item];
+      io.vn = a.v_len[item];
+      io.q = a.q + a.q_off[item];
+      io.qn = a.q_len[item];
+      io.r = a.r + a.r_off[item];
+      io.rn = a.r_len[item];
+    }
     int it = 0;
     unsigned long long work = 0ull;
     Blk bw = b;

@@ -148,7 +148,12 @@ int mpdiv_default_kcut(mpdiv_ctx* ctx, int max_digits) {
   return 0;  // untuned: schoolbook only
 }
 
+int mpdiv_ragged_form(const mpdiv_ctx* ctx) {
+  return (ctx->cfg.flags & MPDIV_FLAG_PERSISTENT_QUEUE) ? RF_SPLIT : RF_CLASSES;
+}
+
 int mpdiv_default_regs(mpdiv_ctx* ctx, int max_digits) {
+  if (ctx->cfg.registers == 64 || ctx->cfg.registers == 128) return ctx->cfg.registers;
   std::lock_guard<std::mutex> g(ctx->tune_mu);
   auto it = ctx->tuned.find(mpdiv_size_class(max_digits));
   return it != ctx->tuned.end() ? it->second.regs : 0;
@@ -202,12 +207,37 @@ static int kernel_occupancy(mpdiv_ctx* ctx, void* k, int threads, int smem) {
 }
 
 // ------------------------------------------------------------------ init / destroy
+// Streams and events of the class form's forked launches.
+static int mpdiv_create_side_streams(mpdiv_ctx* ctx) {
+  int rc = mpdiv_cuda_check(ctx, cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming), "cudaEventCreate");
+  for (int i = 0; i < kMaxRuns && rc == MPDIV_OK; i++) {
+    rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking), "cudaStreamCreate");
+    if (rc == MPDIV_OK)
+      rc = mpdiv_cuda_check(ctx, cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming), "cudaEventCreate");
+  }
+  return rc;
+}
+
+static void mpdiv_destroy_side_streams(mpdiv_ctx* ctx) {
+  for (int i = 0; i < kMaxRuns; i++) {
+    if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
+    if (ctx->join_ev[i]) cudaEventDestroy(ctx->join_ev[i]);
+    ctx->side[i] = nullptr;
+    ctx->join_ev[i] = nullptr;
+  }
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  ctx->fork_ev = nullptr;
+}
 extern "C" int mpdiv_init(mpdiv_ctx** out, int device, const mpdiv_config* cfg) {
   if (!out) return MPDIV_EINVAL;
   *out = nullptr;
   mpdiv_ctx* ctx = new mpdiv_ctx();
   ctx->device = device;
   if (cfg) ctx->cfg = *cfg;
+  if (ctx->cfg.registers != 0 && ctx->cfg.registers != 64 && ctx->cfg.registers != 128) {
+    delete ctx;
+    return MPDIV_EINVAL;
+  }
   int rc;
   if ((rc = mpdiv_cuda_check(ctx, cudaSetDevice(device), "cudaSetDevice")) != MPDIV_OK) {
     delete ctx;
@@ -239,7 +269,10 @@ extern "C" int mpdiv_init(mpdiv_ctx** out, int device, const mpdiv_config* cfg) 
   if ((rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking),
                              "cudaStreamCreate")) != MPDIV_OK ||
       (rc = mpdiv_cuda_check(ctx, cudaEventCreateWithFlags(&ctx->ragged_ev, cudaEventDisableTiming),
-                             "cudaEventCreate")) != MPDIV_OK) {
+                             "cudaEventCreate")) != MPDIV_OK ||
+      (rc = mpdiv_create_side_streams(ctx)) != MPDIV_OK) {
+    mpdiv_destroy_side_streams(ctx);
+    if (ctx->ragged_ev) cudaEventDestroy(ctx->ragged_ev);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     cudaFree(ctx->d_ntt);
     cudaFree(ctx->d_head);
@@ -262,6 +295,8 @@ extern "C" void mpdiv_destroy(mpdiv_ctx* ctx) {
   if (ctx->d_ntt) cudaFree(ctx->d_ntt);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->ragged_ev) cudaEventDestroy(ctx->ragged_ev);
+  if (ctx->cgexec) cudaGraphExecDestroy(ctx->cgexec);
+  mpdiv_destroy_side_streams(ctx);
   delete ctx;
 }
 
@@ -271,7 +306,9 @@ extern "C" const char* mpdiv_last_error(const mpdiv_ctx* ctx) {
 }
 
 // ------------------------------------------------------------------ plain batch
-int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t stream) {
+// Kernel, arguments and launch shape of a plain launch (the kernel's shared
+// memory attribute is raised here, outside any stream capture).
+int mpdiv_prepare_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, PreparedLaunch* P) {
   const int max_digits = L.un;
   const int tcols = L.tcols > 0 ? L.tcols : mpdiv_default_tcols(ctx, max_digits);
   const int smem = launch_smem_bytes(ctx, max_digits, tcols);
@@ -283,22 +320,20 @@ int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t st
   void* k = ntt_tables(ctx) ? ntt_kernel_for(KK_UNIFORM, warps) : kernel_for(KK_UNIFORM, warps);
   int rc = prepare_kernel(ctx, k, smem);
   if (rc) return rc;
-  // 128 registers per thread where the block size has such a build: when
-  // asked (tuned or configured), else when shared memory already holds the
-  // SM to as few blocks as that budget allows, so that it costs no occupancy
+  // 128 registers per thread where the block size has such a build and the
+  // tuner or the configuration asks for it. Not by default: on GB300 the
+  // 128-register builds ran 0.5-6 % slower than the 64-register ones at every
+  // sweep size, although shared memory held the SM to as few blocks as 128
+  // registers allow and the 64-register builds spill a few hundred bytes
   if (void* kw = ntt_tables(ctx) ? nullptr : wide_uniform_kernel(warps)) {
     const int regs = L.regs > 0 ? L.regs : mpdiv_default_regs(ctx, max_digits);
-    bool wide = regs == 128;
-    if (regs == 0) {
-      if ((rc = prepare_kernel(ctx, kw, smem))) return rc;
-      wide = kernel_occupancy(ctx, kw, 32 * warps, smem) >= kernel_occupancy(ctx, k, 32 * warps, smem);
-    }
-    if (wide) {
+    if (regs == 128) {
       if ((rc = prepare_kernel(ctx, kw, smem))) return rc;
       k = kw;
     }
   }
-  UniformArgs a{};
+  UniformArgs& a = P->args;
+  std::memset(&a, 0, sizeof a);  // launch descriptors are compared bytewise by the graph cache
   a.u = L.u;
   a.v = L.v;
   a.q = L.q;
@@ -321,10 +356,34 @@ int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t st
   a.kcut = L.kcut >= 0 ? L.kcut : mpdiv_default_kcut(ctx, max_digits);
   a.ntt = ntt_tables(ctx);
   a.ntt_cut = ntt_cutoff(ctx);
-  const int64_t grid = std::min<int64_t>(L.n, 0x7fffffff);
+  a.list = L.list;
+  a.u_off = L.u_off;
+  a.v_off = L.v_off;
+  a.q_off = L.q_off;
+  a.r_off = L.r_off;
+  a.u_len = L.u_len;
+  a.v_len = L.v_len;
+  a.q_len = L.q_len;
+  a.r_len = L.r_len;
+  P->kernel = k;
+  P->grid = std::min<int64_t>(L.n, 0x7fffffff);
+  P->threads = 32 * warps;
+  P->smem = smem;
+  return MPDIV_OK;
+}
+
+int mpdiv_launch_prepared(mpdiv_ctx* ctx, const PreparedLaunch& P, cudaStream_t stream) {
+  UniformArgs a = P.args;
   void* args[] = {&a};
-  cudaError_t e = cudaLaunchKernel(k, dim3((unsigned)grid), dim3(32 * warps), args, smem, stream);
+  cudaError_t e = cudaLaunchKernel(P.kernel, dim3((unsigned)P.grid), dim3(P.threads), args, P.smem, stream);
   return mpdiv_cuda_check(ctx, e, "launch of the division kernel");
+}
+
+int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t stream) {
+  PreparedLaunch P;
+  int rc = mpdiv_prepare_uniform(ctx, L, &P);
+  if (rc) return rc;
+  return mpdiv_launch_prepared(ctx, P, stream);
 }
 
 extern "C" int mpdiv_batch(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* u, int32_t u_limbs, int64_t u_stride,
@@ -416,54 +475,46 @@ static void persistent_shape(mpdiv_ctx* ctx, int max_u, RaggedArgs& a, int* warp
   *smem_words = (words + 3) & ~3;
 }
 
-int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stream) {
-  int max_u = 1;
-  for (int64_t i = 0; i < L.n; i++) max_u = std::max(max_u, (int)L.u_len_host[i]);
-  RaggedArgs a;
-  std::memset(&a, 0, sizeof a);  // the graph cache compares argument blocks bytewise
-  int warps = 0, smem = 0;
-  // the self-splitting kernel is built without the transform
-  const bool split = L.split && ntt_tables(ctx) == nullptr;
-  if (split) {
-    int words = 0;
-    persistent_shape(ctx, max_u, a, &warps, &words);
-    smem = words * 4;
-  } else {
-    smem = launch_smem_bytes(ctx, max_u, T_MAX);  // any strip width per item
-    warps = 16;  // the one-block-per-item queue kernel is built for 16-warp blocks
+// The order of a ragged batch's items on the device (and its host copy):
+// the caller's (L.order, L.order_host), else built here and cached with a
+// copy of the shape list and the form it was made for, reused only when both
+// length arrays are equal to the cached ones entry for entry. Called with
+// ctx->ragged_mu held. The class form orders by size class, largest first,
+// then by cost; the queue forms by dividend length (the shared memory a
+// self-splitting group must hold), then by cost.
+static int ragged_order(mpdiv_ctx* ctx, const RaggedLaunch& L, int form, const int32_t** d_order,
+                        const int32_t** h_order, bool* same_shapes) {
+  if (L.order != nullptr) {
+    *d_order = L.order;
+    *h_order = L.order_host;
+    *same_shapes = true;
+    return MPDIV_OK;
   }
-  if (smem > ctx->max_smem)
-    return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory", smem);
-  void* k = split ? kernel_for(KK_PERSIST, warps)
-                  : (ntt_tables(ctx) ? ntt_kernel_for(KK_RAGGED, warps) : kernel_for(KK_RAGGED, warps));
-  int rc = prepare_kernel(ctx, k, smem);
-  if (rc) return rc;
-  // size-sorted order, cached with a copy of the shape list it was made for:
-  // reused only when both length arrays are equal to the cached ones entry for
-  // entry
-  std::lock_guard<std::mutex> g(ctx->ragged_mu);
-  const bool same_shapes =
-      L.order != nullptr ||
-      (L.n == ctx->order_n && (size_t)L.n == ctx->order_u_len.size() &&
-       std::memcmp(ctx->order_u_len.data(), L.u_len_host, sizeof(int32_t) * L.n) == 0 &&
-       std::memcmp(ctx->order_v_len.data(), L.v_len_host, sizeof(int32_t) * L.n) == 0);
-  // launches with the context's queue head and order array are ordered on the
-  // GPU one after another, whatever their streams (ragged_ev marks the last one)
-  const bool ctx_queue = L.head == nullptr;
-  if (!same_shapes) {
+  *same_shapes = L.n == ctx->order_n && ctx->order_form == form && (size_t)L.n == ctx->order_u_len.size() &&
+                 std::memcmp(ctx->order_u_len.data(), L.u_len_host, sizeof(int32_t) * L.n) == 0 &&
+                 std::memcmp(ctx->order_v_len.data(), L.v_len_host, sizeof(int32_t) * L.n) == 0;
+  if (!*same_shapes) {
+    int rc;
     // the previous launch may still read the order array on another stream
     if ((rc = mpdiv_cuda_check(ctx, cudaEventSynchronize(ctx->ragged_ev), "wait for the previous queue launch")))
       return rc;
-    std::vector<int32_t> order(L.n);
+    std::vector<int32_t>& order = ctx->order_host;
+    order.resize(L.n);
     std::iota(order.begin(), order.end(), 0);
     std::vector<double> cost(L.n);
     for (int64_t i = 0; i < L.n; i++) cost[i] = item_cost(L.u_len_host[i], L.v_len_host[i]);
-    // largest dividend first (shared-memory need, which decides when a block
-    // splits), then the most expensive division first
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-      if (L.u_len_host[a] != L.u_len_host[b]) return L.u_len_host[a] > L.u_len_host[b];
-      return cost[a] > cost[b];
-    });
+    if (form == RF_CLASSES) {
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const int ca = class_of(L.u_len_host[a]), cb = class_of(L.u_len_host[b]);
+        if (ca != cb) return ca > cb;
+        return cost[a] > cost[b];
+      });
+    } else {
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (L.u_len_host[a] != L.u_len_host[b]) return L.u_len_host[a] > L.u_len_host[b];
+        return cost[a] > cost[b];
+      });
+    }
     if ((size_t)L.n > ctx->order_cap) {
       if (ctx->d_order) cudaFree(ctx->d_order);
       ctx->d_order = nullptr;
@@ -479,7 +530,149 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
     ctx->order_u_len.assign(L.u_len_host, L.u_len_host + L.n);
     ctx->order_v_len.assign(L.v_len_host, L.v_len_host + L.n);
     ctx->order_n = L.n;
+    ctx->order_form = form;
   }
+  *d_order = ctx->d_order;
+  *h_order = ctx->order_host.data();
+  return MPDIV_OK;
+}
+
+// The class form: the ordered items fall into runs of one size class; each
+// run is one plain launch (the class's tuned warps, strip width and register
+// budget, shared memory for its largest dividend) over its item list. With
+// several runs the launches are independent branches forked from `stream`
+// and joined back to it, so that the blocks of one class fill the last wave
+// of another; with use_graph they are captured and replayed as one CUDA graph.
+static int launch_ragged_classes(mpdiv_ctx* ctx, const RaggedLaunch& L, const int32_t* d_order,
+                                 const int32_t* h_order, bool same_shapes, cudaStream_t stream) {
+  std::vector<PreparedLaunch> runs;
+  int64_t start = 0;
+  while (start < L.n) {
+    const int cls = class_of(L.u_len_host[h_order[start]]);
+    int64_t end = start;
+    int max_u = 1;
+    while (end < L.n && class_of(L.u_len_host[h_order[end]]) == cls) max_u = std::max(max_u, L.u_len_host[h_order[end++]]);
+    UniformLaunch U{};
+    U.u = L.u;
+    U.v = L.v;
+    U.q = L.q;
+    U.r = L.r;
+    U.status = L.status;
+    U.iters = L.iters;
+    U.products = L.products;
+    U.n = end - start;
+    U.un = max_u;
+    U.vn = U.qn = U.rn = 1;
+    U.kcut = -1;
+    U.list = d_order + start;
+    U.u_off = L.u_off;
+    U.v_off = L.v_off;
+    U.q_off = L.q_off;
+    U.r_off = L.r_off;
+    U.u_len = L.u_len;
+    U.v_len = L.v_len;
+    U.q_len = L.q_len;
+    U.r_len = L.r_len;
+    runs.emplace_back();
+    int rc = mpdiv_prepare_uniform(ctx, U, &runs.back());
+    if (rc) return rc;
+    start = end;
+  }
+  if ((int)runs.size() > kMaxRuns) return mpdiv_set_error(ctx, MPDIV_EINVAL, "more size classes than expected");
+  auto fork_join = [&](cudaStream_t s) -> int {
+    if (runs.size() == 1) return mpdiv_launch_prepared(ctx, runs[0], s);
+    int rc = mpdiv_cuda_check(ctx, cudaEventRecord(ctx->fork_ev, s), "fork");
+    for (size_t i = 0; i < runs.size() && rc == MPDIV_OK; i++) {
+      rc = mpdiv_cuda_check(ctx, cudaStreamWaitEvent(ctx->side[i], ctx->fork_ev, 0), "fork");
+      if (rc == MPDIV_OK) rc = mpdiv_launch_prepared(ctx, runs[i], ctx->side[i]);
+      if (rc == MPDIV_OK) rc = mpdiv_cuda_check(ctx, cudaEventRecord(ctx->join_ev[i], ctx->side[i]), "join");
+      if (rc == MPDIV_OK) rc = mpdiv_cuda_check(ctx, cudaStreamWaitEvent(s, ctx->join_ev[i], 0), "join");
+    }
+    return rc;
+  };
+  if (!L.use_graph) return fork_join(stream);
+  // the graph is replayed while the launches are unchanged
+  std::vector<char> desc(sizeof(PreparedLaunch) * runs.size());
+  for (size_t i = 0; i < runs.size(); i++) {
+    PreparedLaunch P{};
+    std::memset(&P, 0, sizeof P);
+    P.kernel = runs[i].kernel;
+    P.args = runs[i].args;
+    P.grid = runs[i].grid;
+    P.threads = runs[i].threads;
+    P.smem = runs[i].smem;
+    std::memcpy(desc.data() + i * sizeof P, &P, sizeof P);
+  }
+  int rc;
+  if (!(ctx->cgexec && same_shapes && desc == ctx->c_desc)) {
+    if (ctx->cgexec) {
+      cudaGraphExecDestroy(ctx->cgexec);
+      ctx->cgexec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    if ((rc = mpdiv_cuda_check(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal),
+                               "begin graph capture")))
+      return rc;
+    const int le = fork_join(ctx->cap_stream);
+    cudaError_t ee = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (le != MPDIV_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return le;
+    }
+    if ((rc = mpdiv_cuda_check(ctx, ee, "end graph capture"))) return rc;
+    cudaError_t ie = cudaGraphInstantiate(&ctx->cgexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if ((rc = mpdiv_cuda_check(ctx, ie, "graph instantiate"))) {
+      ctx->cgexec = nullptr;
+      return rc;
+    }
+    ctx->c_desc = desc;
+    ctx->graph_captures++;
+  } else {
+    ctx->graph_replays++;
+  }
+  return mpdiv_cuda_check(ctx, cudaGraphLaunch(ctx->cgexec, stream), "graph launch");
+}
+
+int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stream) {
+  int max_u = 1;
+  for (int64_t i = 0; i < L.n; i++) max_u = std::max(max_u, (int)L.u_len_host[i]);
+  // the self-splitting kernel is built without the transform
+  const int form = (L.form == RF_SPLIT && ntt_tables(ctx) != nullptr) ? RF_QUEUE : L.form;
+  std::lock_guard<std::mutex> g(ctx->ragged_mu);
+  // launches with the context's queue head and order array are ordered on the
+  // GPU one after another, whatever their streams (ragged_ev marks the last one)
+  const bool ctx_queue = L.order == nullptr;
+  const int32_t* d_order = nullptr;
+  const int32_t* h_order = nullptr;
+  bool same_shapes = false;
+  int rc = ragged_order(ctx, L, form, &d_order, &h_order, &same_shapes);
+  if (rc) return rc;
+  if (ctx_queue &&
+      (rc = mpdiv_cuda_check(ctx, cudaStreamWaitEvent(stream, ctx->ragged_ev, 0), "order after the previous launch")))
+    return rc;
+  if (form == RF_CLASSES) {
+    rc = launch_ragged_classes(ctx, L, d_order, h_order, same_shapes, stream);
+    if (rc == MPDIV_OK && ctx_queue) rc = mpdiv_cuda_check(ctx, cudaEventRecord(ctx->ragged_ev, stream), "event");
+    return rc;
+  }
+  RaggedArgs a;
+  std::memset(&a, 0, sizeof a);  // the graph cache compares argument blocks bytewise
+  int warps = 0, smem = 0;
+  const bool split = form == RF_SPLIT;
+  if (split) {
+    int words = 0;
+    persistent_shape(ctx, max_u, a, &warps, &words);
+    smem = words * 4;
+  } else {
+    smem = launch_smem_bytes(ctx, max_u, T_MAX);  // any strip width per item
+    warps = 16;  // the one-block-per-item queue kernel is built for 16-warp blocks
+  }
+  if (smem > ctx->max_smem)
+    return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "needs %d bytes of shared memory", smem);
+  void* k = split ? kernel_for(KK_PERSIST, warps)
+                  : (ntt_tables(ctx) ? ntt_kernel_for(KK_RAGGED, warps) : kernel_for(KK_RAGGED, warps));
+  if ((rc = prepare_kernel(ctx, k, smem))) return rc;
   int occ = kernel_occupancy(ctx, k, 32 * warps, smem);
   if (occ < 1) return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "kernel does not fit on an SM");
   if (ctx->cfg.blocks_per_sm > 0) occ = std::min(occ, ctx->cfg.blocks_per_sm);
@@ -501,7 +694,7 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
   a.status = L.status;
   a.iters = L.iters;
   a.products = L.products;
-  a.order = L.order ? L.order : ctx->d_order;
+  a.order = d_order;
   a.head = L.head ? L.head : ctx->d_head;
   a.n = L.n;
   a.smem_words = smem / 4;
@@ -510,9 +703,6 @@ int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stre
   a.kcut = split ? -1 : mpdiv_default_kcut(ctx, max_u);
   a.ntt = ntt_tables(ctx);
   a.ntt_cut = ntt_cutoff(ctx);
-  if (ctx_queue &&
-      (rc = mpdiv_cuda_check(ctx, cudaStreamWaitEvent(stream, ctx->ragged_ev, 0), "order after the previous launch")))
-    return rc;
   if (!L.use_graph) {
     if ((rc = mpdiv_cuda_check(ctx, cudaMemsetAsync(a.head, 0, sizeof(int32_t), stream), "queue reset"))) return rc;
     void* args[] = {&a};
@@ -603,7 +793,7 @@ extern "C" int mpdiv_batch_ragged(mpdiv_ctx* ctx, int64_t n_items, const uint32_
   L.v_len_host = v_len_host;
   L.n = n_items;
   L.use_graph = true;
-  L.split = true;
+  L.form = mpdiv_ragged_form(ctx);
   return mpdiv_launch_ragged(ctx, L, (cudaStream_t)stream);
 }
 

@@ -1,8 +1,7 @@
 // The plain division kernel for 4-warp blocks with the register budget of
-// 4 resident block(s) per SM, 128 registers per thread: where shared memory
-// already limits residency to 4 block(s) per SM, the wider budget costs no
-// occupancy and avoids the spills of the 64-register build (a separate
-// translation unit, so that the block sizes build in parallel).
+// 4 resident block(s) per SM, 128 registers per thread, without the spills of the
+// 64-register build: a candidate of the tuner (a separate translation unit,
+// so that the block sizes build in parallel).
 #include "mp_kernels.cuh"
 #include "mpdiv_kernels.h"
 

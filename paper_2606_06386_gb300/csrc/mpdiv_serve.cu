@@ -1,23 +1,37 @@
 // Continuous-batching server for divisions of mixed precision.
 //
-// Operands travel through two pinned host rings mirrored on the device: an
-// input ring (u and v of every request, in arrival order) and an output ring
-// (q and r of every launched request). mpdiv_serve_submit reserves the
-// request's digits at the tail of the input ring and copies its operands there
-// itself, outside the server lock. A scheduler thread turns the oldest ready
-// requests into a batch: a contiguous run of the input ring (one host-to-device
-// copy), per-item offsets and a largest-first order (one more copy), one launch
-// of the self-splitting persistent kernel over the batch's queue, and one
-// device-to-host copy of the batch's results, all on the batch's own stream.
-// Up to max_inflight batches run at once. While fewer than low_water requests
-// are on the GPU, queued requests launch as soon as there are at least
-// kBatchStep of them for every batch already in flight (so an idle server
-// launches each request at once, and a busy one launches fewer, larger
-// batches instead of being bound by the launch path); otherwise they gather
-// into larger batches (up to max_batch, or until the oldest has waited
+// Requests are admitted by footprint: each belongs to the footprint class of
+// its dividend (at most 1024, 2048, 4096, 8192 digits, or more: the size
+// classes whose shared-memory plan and block shape the launches are tuned
+// for), and a batch holds requests of one class only, so that a large request
+// never sets the block shape and shared memory of a batch of small ones.
+// Operands travel through pinned host rings mirrored on the device, one input
+// ring per footprint class (u and v of every request of the class, in arrival
+// order) and one output ring (q and r of every launched request): the input
+// rings share the pool's input half, the output ring is its other half.
+// mpdiv_serve_submit reserves the request's digits at the tail of its class's
+// input ring and copies its operands there itself, outside the server lock. A
+// scheduler thread turns the oldest ready requests of a class into a batch: a
+// contiguous run of that class's ring (one host-to-device copy), per-item
+// offsets and a most-expensive-first order (one more copy), one plain launch
+// over the batch with the class's tuned shape (or, with
+// MPDIV_FLAG_PERSISTENT_QUEUE, one launch of the self-splitting persistent
+// kernel), and one device-to-host copy of the batch's results, all on the
+// batch's own stream; batches of different classes overlap on the GPU.
+// Up to max_inflight batches run at once. The class whose oldest ready request
+// is oldest goes first. While fewer than low_water requests are on the GPU,
+// the queued requests of a class launch as soon as there are at least
+// kBatchStep of them for every batch of that class already in flight (so an
+// idle class launches each request at once, and a busy one launches fewer,
+// larger batches instead of being bound by the launch path); otherwise they
+// gather into larger batches (up to max_batch, or until the oldest has waited
 // max_wait_us).
 // The kernel is the division path of the plain launch, so a result does not
 // depend on the batch a request lands in.
+//
+// A batch whose launch fails fails its requests and every queued one (status
+// MPDIV_ST_INTERNAL, and poll returns MPDIV_ECUDA for them), and the server
+// refuses further work until it is stopped.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -38,6 +52,9 @@ namespace {
 // its low-water mark (see the header comment).
 constexpr int kBatchStep = 8;
 
+// Footprint classes: the dividend's size class (mp::class_of).
+constexpr int kClasses = MPDIV_SERVE_CLASSES;
+
 using Clock = std::chrono::steady_clock;
 
 int64_t now_ns() {
@@ -56,8 +73,10 @@ struct OutBatch {
 struct Request {
   uint64_t ticket = 0;
   int32_t u_len = 0, v_len = 0, q_len = 0, r_len = 0;
-  int64_t in_off = -1;            // u at in_off, v at in_off + u_len (input ring digits)
-  int64_t in_seq = -1;            // its input-ring allocation
+  int cls = 0;                    // footprint class
+  bool failed = false;            // its batch could not be launched
+  int64_t in_off = -1;            // u at in_off, v at in_off + u_len (digits of the input half)
+  int64_t in_seq = -1;            // its allocation in its class's input ring
   int64_t out_off = -1;           // q at out_off, r at out_off + q_len (output ring digits)
   std::shared_ptr<OutBatch> out;  // the batch's output allocation
   std::atomic<int> ready{0};      // operands copied into the ring
@@ -72,10 +91,12 @@ struct MpServer {
   mpdiv_ctx* ctx = nullptr;
   mpdiv_serve_config cfg{};
   uint32_t *d_in = nullptr, *h_in = nullptr, *d_out = nullptr, *h_out = nullptr;
-  mp_serve::Ring in_ring, out_ring;
+  mp_serve::Ring in_ring[kClasses], out_ring;
+  int64_t in_base[kClasses] = {};  // start of each class's ring in the input half
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
-  std::deque<Request*> queue;
+  std::deque<Request*> queue[kClasses];
+  int64_t queued = 0;  // requests in all queues
   // request of ticket t at by_ticket[t & ticket_mask], owned there until it is
   // polled (a poller claims it by swapping the slot to null, without the lock)
   std::unique_ptr<std::atomic<Request*>[]> by_ticket;
@@ -85,12 +106,15 @@ struct MpServer {
   bool stopping = false, quit = false;
   int sched_error = 0;
   int64_t completed = 0, launches = 0, batched_items = 0;
+  int64_t class_launches[kClasses] = {}, class_items[kClasses] = {};  // by the batch's largest dividend
+  int64_t fail_launch = -1;  // test hook: the launch with this index fails on the host (-1: none)
   std::thread th;
   struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     uint32_t *h_meta = nullptr, *d_meta = nullptr;  // offsets, lengths, order, heads, status
     bool busy = false;
+    int cls = 0;  // footprint class of the batch in flight
     int64_t out_off = -1, out_seq = -1;
     std::vector<Request*> reqs;
   };
@@ -99,7 +123,20 @@ struct MpServer {
 
   void run();
   bool launch(Slot& s);
+  void fail(Request* r, int64_t t);
 };
+
+// Mark a request failed (no results; status MPDIV_ST_INTERNAL) and release its
+// input-ring space. Called with the lock held.
+void MpServer::fail(Request* r, int64_t t) {
+  r->out.reset();
+  r->out_off = -1;
+  r->failed = true;
+  r->status = MPDIV_ST_INTERNAL;
+  r->t_done = t;
+  r->state.store(RQ_DONE, std::memory_order_release);
+  in_ring[r->cls].release(r->in_seq);
+}
 
 // metadata layout of a slot for n items: int64 offsets (u, v, q, r) as digit
 // pairs, int32 lengths (u, v, q, r), order, queue heads, status
@@ -135,9 +172,13 @@ bool MpServer::launch(Slot& s) {
     const double a = std::max(1, r->u_len - r->v_len + 1);
     cost[i] = a * (r->u_len + r->v_len) + 2.0 * a * std::min<double>(a, r->v_len);
   }
+  // the order of the context's ragged form: most expensive first (a batch is
+  // one footprint class), or, for the self-splitting kernel, largest dividend
+  // first (the shared memory a group must hold), then most expensive
+  const int form = mpdiv_ragged_form(ctx);
   std::iota(order, order + n, 0);
   std::stable_sort(order, order + n, [&](int32_t a, int32_t b) {
-    if (s.reqs[a]->u_len != s.reqs[b]->u_len) return s.reqs[a]->u_len > s.reqs[b]->u_len;
+    if (form == RF_SPLIT && s.reqs[a]->u_len != s.reqs[b]->u_len) return s.reqs[a]->u_len > s.reqs[b]->u_len;
     return cost[a] > cost[b];
   });
   std::memset(heads, 0, 8 * sizeof(int32_t));
@@ -152,7 +193,7 @@ bool MpServer::launch(Slot& s) {
   int32_t* d_status = reinterpret_cast<int32_t*>(s.d_meta + status_w);
   int rc = (e == cudaSuccess) ? MPDIV_OK : MPDIV_ECUDA;
   if (rc == MPDIV_OK) {
-    // one self-splitting persistent launch over the batch, largest first
+    // one launch over the batch in the context's ragged form
     std::vector<int32_t> ulh(n);
     for (int64_t i = 0; i < n; i++) ulh[i] = s.reqs[i]->u_len;
     RaggedLaunch L{};
@@ -172,10 +213,11 @@ bool MpServer::launch(Slot& s) {
     L.u_len_host = ulh.data();
     L.v_len_host = ulh.data();
     L.order = d_len + 4 * n;
+    L.order_host = order;
     L.head = const_cast<int32_t*>(d_len + 5 * n);
     L.n = n;
     L.use_graph = false;
-    L.split = true;
+    L.form = form;
     rc = mpdiv_launch_ragged(ctx, L, s.stream);
   }
   if (rc == MPDIV_OK)
@@ -205,7 +247,7 @@ void MpServer::run() {
         r->status = st[i];
         r->t_done = t;
         r->state.store(RQ_DONE, std::memory_order_release);
-        in_ring.release(r->in_seq);
+        in_ring[r->cls].release(r->in_seq);
       }
       completed += n;
       pending -= n;
@@ -214,77 +256,99 @@ void MpServer::run() {
       s->busy = false;
     }
     if (!finished.empty()) cv_done.notify_all();
-    int busy = 0;
+    int busy = 0, busy_c[kClasses] = {};
     Slot* free_slot = nullptr;
     for (auto& s : slots) {
-      if (s.busy)
+      if (s.busy) {
         busy++;
-      else if (!free_slot)
+        busy_c[s.cls]++;
+      } else if (!free_slot) {
         free_slot = &s;
+      }
     }
-    // ---- admission
-    bool admit = false;
-    if (free_slot && !queue.empty() && queue.front()->ready.load(std::memory_order_acquire) && sched_error == 0) {
-      const int64_t waited_us = (t - queue.front()->t_submit) / 1000;
-      admit = (inflight_items < cfg.low_water && (int64_t)queue.size() >= (int64_t)kBatchStep * busy) ||
-              (int64_t)queue.size() >= cfg.max_batch || waited_us >= cfg.max_wait_us || quit;
+    // ---- admission: the class whose oldest ready request is oldest among
+    // those whose admission condition holds
+    int adm = -1;
+    if (free_slot && sched_error == 0) {
+      int64_t oldest = INT64_MAX;
+      for (int c = 0; c < kClasses; c++) {
+        if (queue[c].empty() || !queue[c].front()->ready.load(std::memory_order_acquire)) continue;
+        const Request* f = queue[c].front();
+        const int64_t waited_us = (t - f->t_submit) / 1000;
+        const bool go = (inflight_items < cfg.low_water && (int64_t)queue[c].size() >= (int64_t)kBatchStep * busy_c[c]) ||
+                        (int64_t)queue[c].size() >= cfg.max_batch || waited_us >= cfg.max_wait_us || quit;
+        if (go && f->t_submit < oldest) {
+          oldest = f->t_submit;
+          adm = c;
+        }
+      }
     }
-    if (admit) {
-      // the oldest ready requests, contiguous in the input ring, within the output ring
+    if (adm >= 0) {
+      // the oldest ready requests of the class, contiguous in its ring, within the output ring
+      std::deque<Request*>& qc = queue[adm];
       std::vector<Request*>& b = free_slot->reqs;
       int64_t out_need = 0;
       const int64_t out_room = out_ring.cap - out_ring.used - 4;
-      while (!queue.empty() && (int64_t)b.size() < cfg.max_batch) {
-        Request* r = queue.front();
+      while (!qc.empty() && (int64_t)b.size() < cfg.max_batch) {
+        Request* r = qc.front();
         if (!r->ready.load(std::memory_order_acquire)) break;
         if (!b.empty() && r->in_off != b.back()->in_off + ((b.back()->u_len + b.back()->v_len + 3) & ~3)) break;
         const int64_t need = r->q_len + r->r_len;
         if (out_need + need > out_room) break;
         out_need += need;
         b.push_back(r);
-        queue.pop_front();
+        qc.pop_front();
       }
+      queued -= (int64_t)b.size();
       int64_t oseq = -1;
       const int64_t off = b.empty() ? -1 : out_ring.alloc(out_need, &oseq);
       if (off < 0) {
-        for (auto it = b.rbegin(); it != b.rend(); ++it) queue.push_front(*it);
+        for (auto it = b.rbegin(); it != b.rend(); ++it) qc.push_front(*it);
+        queued += (int64_t)b.size();
         b.clear();
       } else {
         free_slot->out_off = off;
         free_slot->out_seq = oseq;
         free_slot->busy = true;
-        for (Request* r : b) r->state.store(RQ_RUNNING, std::memory_order_relaxed);
+        free_slot->cls = adm;
+        int bcls = 0;
+        for (Request* r : b) {
+          r->state.store(RQ_RUNNING, std::memory_order_relaxed);
+          bcls = std::max(bcls, mp::class_of(r->u_len));
+        }
         const int64_t nb = (int64_t)b.size();
+        const bool inject = launches == fail_launch;
         inflight_items += nb;
         launches++;
         batched_items += nb;
+        class_launches[bcls]++;
+        class_items[bcls] += nb;
         lk.unlock();
-        const bool ok = launch(*free_slot);
+        const bool ok = !inject && launch(*free_slot);
         lk.lock();
-        if (!ok) {  // fail these requests and refuse further work
+        if (!ok) {  // fail these requests and every queued one, and refuse further work
           sched_error = MPDIV_ECUDA;
           const int64_t tf = now_ns();
-          for (Request* r : b) {
-            r->out.reset();  // no results: the output allocation is released below
-            r->out_off = -1;
-            r->status = MPDIV_ST_INTERNAL;
-            r->t_done = tf;
-            r->state.store(RQ_DONE, std::memory_order_release);
-            in_ring.release(r->in_seq);
-          }
+          for (Request* r : b) fail(r, tf);
           out_ring.release(oseq);
           pending -= nb;
           inflight_items -= nb;
           b.clear();
           free_slot->busy = false;
+          for (auto& qq : queue) {
+            for (Request* r : qq) fail(r, tf);
+            pending -= (int64_t)qq.size();
+            qq.clear();
+          }
+          queued = 0;
           cv_done.notify_all();
         }
         continue;
       }
     }
-    if (quit && busy == 0 && (queue.empty() || sched_error)) break;
-    cv_sched.wait_for(lk, (busy > 0 || !queue.empty()) ? std::chrono::microseconds(20)
-                                                       : std::chrono::microseconds(5000));
+    if (quit && busy == 0 && (queued == 0 || sched_error)) break;
+    cv_sched.wait_for(lk, (busy > 0 || queued > 0) ? std::chrono::microseconds(20)
+                                                  : std::chrono::microseconds(5000));
   }
 }
 
@@ -311,7 +375,11 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
   if (S->cfg.low_water <= 0) S->cfg.low_water = 2048;
   if (S->cfg.max_wait_us <= 0) S->cfg.max_wait_us = 2000;
   const int64_t half = (S->cfg.pool_digits / 2) & ~int64_t(3);
-  S->in_ring.cap = half;
+  const int64_t per_class = (half / kClasses) & ~int64_t(3);
+  for (int c = 0; c < kClasses; c++) {
+    S->in_ring[c].cap = per_class;
+    S->in_base[c] = c * per_class;
+  }
   S->out_ring.cap = half;
   S->meta_words = meta_words_for(S->cfg.max_batch);
   {
@@ -350,33 +418,37 @@ extern "C" int mpdiv_serve_submit(mpdiv_ctx* ctx, const uint32_t* u_host, int32_
   if (u_len < 1 || v_len < 1) return mpdiv_set_error(ctx, MPDIV_EINVAL, "digit counts must be positive");
   if (u_len > MPDIV_MAX_LIMBS || v_len > MPDIV_MAX_LIMBS)
     return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "at most %d digits", MPDIV_MAX_LIMBS);
-  if (2 * (int64_t)(u_len + v_len) + 8 > S->in_ring.cap)
+  const int cls = mp::class_of(u_len);
+  if (2 * (int64_t)(u_len + v_len) + 8 > S->in_ring[cls].cap)
     return mpdiv_set_error(ctx, MPDIV_EBUSY, "request larger than the server's rings");
   auto r = std::make_unique<Request>();
   r->u_len = u_len;
   r->v_len = v_len;
   r->q_len = u_len;  // enough for any quotient
   r->r_len = v_len;
+  r->cls = cls;
   Request* rp = r.get();
   bool wake = false;
   {
     std::lock_guard<std::mutex> g(S->mu);
     if (S->stopping) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server stopping");
+    if (S->sched_error) return mpdiv_set_error(ctx, S->sched_error, "the server stopped after a failed launch");
     if (S->pending >= S->cfg.max_pending) return MPDIV_EBUSY;
     // the ticket's slot still holds an unpolled result from ticket - capacity
     if (S->by_ticket[S->next_ticket & S->ticket_mask].load(std::memory_order_acquire) != nullptr) return MPDIV_EBUSY;
     int64_t seq = -1;
-    const int64_t off = S->in_ring.alloc(u_len + v_len, &seq);
-    if (off < 0) return MPDIV_EBUSY;  // input ring full: retry later
-    r->in_off = off;
+    const int64_t off = S->in_ring[cls].alloc(u_len + v_len, &seq);
+    if (off < 0) return MPDIV_EBUSY;  // the class's input ring is full: retry later
+    r->in_off = S->in_base[cls] + off;
     r->in_seq = seq;
     r->ticket = S->next_ticket++;
     r->t_submit = now_ns();
     *ticket = r->ticket;
     // the scheduler re-checks a non-empty queue every few microseconds by
     // itself; only a request into an empty queue needs to wake it
-    wake = S->queue.empty();
-    S->queue.push_back(rp);
+    wake = S->queued == 0;
+    S->queue[cls].push_back(rp);
+    S->queued++;
     S->by_ticket[rp->ticket & S->ticket_mask].store(r.release(), std::memory_order_release);
     S->pending++;
   }
@@ -407,7 +479,7 @@ static int poll_impl(mpdiv_ctx* ctx, uint64_t ticket, uint32_t* q_host, int32_t 
         return MPDIV_ETIMEDOUT;
     }
   }
-  const uint32_t* qd = r->out_off >= 0 ? S->h_out + r->out_off : nullptr;
+  const uint32_t* qd = (r->out_off >= 0 && !r->failed) ? S->h_out + r->out_off : nullptr;
   if (qd && ((q_host && q_cap < r->q_len) || (r_host && r_cap < r->r_len))) {
     // a short buffer is fine when the digits it drops are zero
     int qs = r->q_len, rs = r->r_len;
@@ -438,6 +510,8 @@ static int poll_impl(mpdiv_ctx* ctx, uint64_t ticket, uint32_t* q_host, int32_t 
     std::lock_guard<std::mutex> g(S->mu);
     S->out_ring.release(r->out->seq);
   }
+  if (r->failed) return mpdiv_set_error(ctx, MPDIV_ECUDA, "ticket %llu failed: its batch could not be launched",
+                                        (unsigned long long)ticket);
   return MPDIV_OK;
 }
 
@@ -465,13 +539,27 @@ extern "C" int mpdiv_serve_stop(mpdiv_ctx* ctx) {
   return S->sched_error ? mpdiv_set_error(ctx, S->sched_error, "a batch failed to launch") : MPDIV_OK;
 }
 
-extern "C" int mpdiv_serve_stats(mpdiv_ctx* ctx, int64_t* completed, int64_t* launches, int64_t* batched_items) {
+extern "C" int mpdiv_serve_stats(mpdiv_ctx* ctx, int64_t* completed, int64_t* launches, int64_t* batched_items,
+                                 int64_t* class_launches, int64_t* class_items) {
   if (!ctx || !ctx->server) return MPDIV_EINVAL;
   MpServer* S = ctx->server;
   std::lock_guard<std::mutex> g(S->mu);
   if (completed) *completed = S->completed;
   if (launches) *launches = S->launches;
   if (batched_items) *batched_items = S->batched_items;
+  for (int c = 0; c < kClasses; c++) {
+    if (class_launches) class_launches[c] = S->class_launches[c];
+    if (class_items) class_items[c] = S->class_items[c];
+  }
+  return MPDIV_OK;
+}
+
+extern "C" int mpdiv_debug_serve_fail_launch(mpdiv_ctx* ctx, int64_t launch_index) {
+  if (!ctx || launch_index < -1) return MPDIV_EINVAL;
+  MpServer* S = ctx->server;
+  if (!S) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server not running");
+  std::lock_guard<std::mutex> g(S->mu);
+  S->fail_launch = launch_index;
   return MPDIV_OK;
 }
 

@@ -1,7 +1,7 @@
 """Run a few plain division launches of one size, for profilers.
 
     python -m paper_2606_06386_gb300.profile_case --digits 8192 --vdigits 4096 --items 152 --launches 2 \
-        [--warps W] [--cols T] [--products clipped|full|ntt] [--tcut D] [--mul]
+        [--warps W] [--cols T] [--regs 64|128] [--products clipped|full|ntt] [--tcut D] [--mul]
 
 The operands are the seeded uniform sweep inputs; the launches go through the
 C ABI (mpdiv_batch, or mpdiv_mul_batch for the multiplication cost unit of
@@ -24,6 +24,7 @@ def main():
     ap.add_argument("--launches", type=int, default=2)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--cols", type=int, default=0, help="strip width (columns per lane): 3, 5 or 7")
+    ap.add_argument("--regs", type=int, default=0, help="registers per thread of the plain kernel: 64 or 128")
     ap.add_argument("--products", default="clipped", choices=["clipped", "full", "ntt"])
     ap.add_argument("--tcut", type=int, default=0, help="transform cutoff in digits (0: the library's)")
     ap.add_argument("--mul", action="store_true", help="the multiplication cost unit instead of the division")
@@ -43,7 +44,8 @@ def main():
     r = torch.zeros((a.items, kl), dtype=torch.int32, device="cuda")
     st = torch.zeros(a.items, dtype=torch.int32, device="cuda")
     flags = {"clipped": 0, "full": mp.MPDIV_FLAG_FULL_PRODUCTS, "ntt": mp.MPDIV_FLAG_NTT_PRODUCTS}[a.products]
-    ctx = mp.mpdiv_init(0, warps_per_block=a.warps, mul_columns=a.cols, flags=flags, transform_cutoff=a.tcut)
+    ctx = mp.mpdiv_init(0, warps_per_block=a.warps, mul_columns=a.cols, flags=flags, transform_cutoff=a.tcut,
+                        registers=a.regs)
     if a.mul:
         v = d(I.uniform_batch(a.items, a.digits, seed=6, stream=a.digits))
         out = torch.zeros_like(u)

@@ -57,28 +57,50 @@ def _ragged(u_len, v_len, seed, c=None, edge=False):
     return IT
 
 
+PERSIST = 8  # MPDIV_FLAG_PERSISTENT_QUEUE
+
+
 @pytest.mark.parametrize("warps", [0, 2, 4, 16])
 def test_mixed_precision_persistent_launch(warps):
     # block shapes of the self-splitting kernel: untuned defaults (16-warp
     # blocks splitting to 8 and 4), and configured block sizes 2 and 4 (8-warp
     # blocks splitting to 4 and 2 warps) and 16 (16-warp blocks, no split)
     u_len, v_len = I.mixed_sizes(192, seed=I.SEED_BASE + 20)
-    _ragged(u_len, v_len, seed=5, c=ctx(warps=warps))
+    _ragged(u_len, v_len, seed=5, c=ctx(warps=warps, flags=PERSIST))
 
 
+@pytest.mark.parametrize("warps", [0, 1, 4, 8])
+def test_mixed_precision_by_size_class(warps):
+    # the default ragged form: one plain launch per size class over its item
+    # list, the launches forked as branches of one graph (configured block
+    # sizes, or the untuned defaults per class)
+    u_len, v_len = I.mixed_sizes(192, seed=I.SEED_BASE + 21)
+    _ragged(u_len, v_len, seed=7, c=ctx(warps=warps))
+
+
+@pytest.mark.parametrize("flags", [0, PERSIST])
 @pytest.mark.parametrize("warps", [0, 2])
-def test_mixed_small_shapes_and_edges(warps):
+def test_mixed_small_shapes_and_edges(warps, flags):
     rnd = np.random.default_rng(3)
     u_len = rnd.integers(1, 300, size=200).astype(np.int32)
     v_len = np.maximum(1, (u_len * rnd.uniform(0.05, 1.3, size=200)).astype(np.int32))
-    _ragged(u_len, v_len, seed=6, edge=True, c=ctx(warps=warps))
+    _ragged(u_len, v_len, seed=6, edge=True, c=ctx(warps=warps, flags=flags))
 
 
-def test_mixed_with_2e19_bit_items():
-    # the persistent launch with dividends up to 2^19 bits in the queue
+@pytest.mark.parametrize("flags", [0, PERSIST])
+def test_mixed_with_2e19_bit_items(flags):
+    # dividends up to 2^19 bits in the batch (five size classes)
     u_len = np.array([16384, 9000, 4096, 2048, 1000, 16384, 300, 8192], np.int32)
     v_len = np.array([8192, 100, 4000, 1024, 999, 16000, 150, 8192], np.int32)
-    _ragged(u_len, v_len, seed=8)
+    _ragged(u_len, v_len, seed=8, c=ctx(flags=flags))
+
+
+def test_one_class_and_single_item_batches():
+    # a batch of one size class (one launch, no fork) and a batch of one item
+    u_len = np.full(40, 3000, np.int32)
+    v_len = np.arange(1, 41, dtype=np.int32) * 70
+    _ragged(u_len, v_len, seed=9)
+    _ragged(np.array([5000], np.int32), np.array([77], np.int32), seed=10)
 
 
 @pytest.mark.parametrize("variant", I.STRESS_VARIANTS)
@@ -194,13 +216,14 @@ def test_configured_block_size_rounds_to_a_built_kernel(warps):
     assert mp.mpdiv_tuning(ctx(warps=warps), 700)[0] == min(32, 1 << (warps - 1).bit_length())
 
 
-def test_bench_mixed_configuration_every_item():
+@pytest.mark.parametrize("flags", [0, PERSIST])
+def test_bench_mixed_configuration_every_item(flags):
     # the mixed workload exactly as the benchmark runs it: 8192 divisions,
-    # 2^15..2^18-bit dividends, shapes tuned per size class first, one
-    # persistent launch (replayed as a graph); every item against the oracle
+    # 2^15..2^18-bit dividends, shapes tuned per size class first, one call
+    # (replayed as a graph) in either ragged form; every item against the oracle
     import paper_2606_06386_gb300 as mp
 
-    c = mp.mpdiv_init(0)
+    c = mp.mpdiv_init(0, flags=flags)
     try:
         for n in (1024, 2048, 4096, 8192):
             mp.mpdiv_autotune(c, n, n // 2, 1024)

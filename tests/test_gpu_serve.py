@@ -183,10 +183,13 @@ def test_concurrent_polls_of_one_ticket():
         mp.mpdiv_destroy(c)
 
 
-def test_serving_full_size_mix():
+@pytest.mark.parametrize("flags", [0, 8])
+def test_serving_full_size_mix(flags):
     # the full size range of the serving workload (2^15..2^18-bit dividends,
     # divisors of 0.25..1.0 of their length) plus a few 2^19-bit requests and
-    # degenerate ones (u < v, v = 1): every result equals the oracle's
+    # degenerate ones (u < v, v = 1), in both launch forms of a batch (plain
+    # launch with the class's shape; flag 8, MPDIV_FLAG_PERSISTENT_QUEUE: the
+    # self-splitting persistent kernel): every result equals the oracle's
     import paper_2606_06386_gb300 as mp
 
     n = 96
@@ -201,7 +204,7 @@ def test_serving_full_size_mix():
     v_flat[v_off[4]] = 1  # v = 1
     items = [(u_flat[u_off[i] : u_off[i] + u_len[i]].copy(), v_flat[v_off[i] : v_off[i] + v_len[i]].copy())
              for i in range(n)]
-    c = mp.mpdiv_init(0)
+    c = mp.mpdiv_init(0, flags=flags)
     try:
         mp.mpdiv_serve_start(c, pool_digits=1 << 23, max_batch=32, max_inflight=3)
         tickets = [_submit_retry(mp, c, u, v) for u, v in items]
@@ -216,3 +219,91 @@ def test_serving_full_size_mix():
     for (u, v), (q, r) in zip(items, got):
         qo, ro, _ = oracle.divmod_u32(u, v, len(u), len(v))
         assert (q == qo).all() and (r == ro).all()
+
+
+def test_admission_by_footprint_keeps_classes_apart():
+    # requests of every footprint class (dividends of at most 1024, 2048, 4096,
+    # 8192 digits and a 2^19-bit one) submitted at once: every launch holds
+    # requests of one class, so the requests counted per launch class (the
+    # class of the launch's largest dividend) equal the requests per class, a
+    # 2^19-bit request never shares the launch of smaller ones, and every
+    # result equals the oracle's
+    import paper_2606_06386_gb300 as mp
+
+    rnd = np.random.default_rng(77)
+    u_len = np.concatenate([rnd.integers(64, 1025, 24), rnd.integers(1025, 2049, 24), rnd.integers(2049, 4097, 12),
+                            rnd.integers(4097, 8193, 6), [16384]]).astype(np.int32)
+    rnd.shuffle(u_len)
+    v_len = np.maximum(1, (u_len * rnd.uniform(0.25, 1.0, len(u_len))).astype(np.int32)).astype(np.int32)
+    u_flat, u_off, v_flat, v_off = I.ragged_operands(u_len, v_len, seed=77)
+    items = [(u_flat[u_off[i]:u_off[i] + u_len[i]].copy(), v_flat[v_off[i]:v_off[i] + v_len[i]].copy())
+             for i in range(len(u_len))]
+    cls = [0 if n <= 1024 else 1 if n <= 2048 else 2 if n <= 4096 else 3 if n <= 8192 else 4 for n in u_len]
+    c = mp.mpdiv_init(0)
+    try:
+        mp.mpdiv_serve_start(c, pool_digits=1 << 24, max_batch=64, max_inflight=4, max_wait_us=20000)
+        tickets = [_submit_retry(mp, c, u, v) for u, v in items]
+        got = []
+        for t, (u, v) in zip(tickets, items):
+            rc, q, r, st = mp.mpdiv_serve_poll(c, t, len(u), len(v), timeout_us=60_000_000)
+            assert rc == mp.MPDIV_OK and st == 0
+            got.append((q, r))
+        completed, launches, batched, cl, ci = mp.mpdiv_serve_stats(c, by_class=True)
+        mp.mpdiv_serve_stop(c)
+    finally:
+        mp.mpdiv_destroy(c)
+    assert completed == len(items) and sum(cl) == launches and sum(ci) == batched == len(items)
+    assert ci == [cls.count(k) for k in range(mp.MPDIV_SERVE_CLASSES)]
+    assert cl[4] == 1 and all(cl[k] >= 1 for k in range(4))
+    for (u, v), (q, r) in zip(items, got):
+        qo, ro, _ = oracle.divmod_u32(u, v, len(u), len(v))
+        assert (q == qo).all() and (r == ro).all()
+
+
+def test_a_failed_launch_fails_its_requests_and_the_server_refuses_work():
+    # the host-side hook fails the server's second launch before any of its
+    # work reaches the GPU: the first request's result is exact; the failed
+    # batch's requests and those still queued finish with status 4 and poll
+    # returns MPDIV_ECUDA for them; submit then returns MPDIV_ECUDA, stop
+    # reports the failure, and a new server on the same context works
+    import paper_2606_06386_gb300 as mp
+
+    items = _mix(24, seed=I.SEED_BASE + 33)
+    c = mp.mpdiv_init(0)
+    try:
+        mp.mpdiv_serve_start(c, pool_digits=1 << 22, max_batch=4, max_inflight=2)
+        mp.mpdiv_debug_serve_fail_launch(c, 1)
+        u, v = items[0]
+        t0 = _submit_retry(mp, c, u, v)
+        rc, q, r, st = mp.mpdiv_serve_poll(c, t0, len(u), len(v), timeout_us=30_000_000)
+        qo, ro, _ = oracle.divmod_u32(u, v, len(u), len(v))
+        assert rc == mp.MPDIV_OK and st == 0 and (q == qo).all() and (r == ro).all()
+        tickets = []
+        for u, v in items[1:]:
+            try:
+                tickets.append(mp.mpdiv_serve_submit(c, u, v))
+            except mp.MpdivError as e:  # the failure may come before every request is in
+                assert e.code == mp.MPDIV_ECUDA
+                break
+        assert tickets
+        for t, (u, v) in zip(tickets, items[1:]):
+            with pytest.raises(mp.MpdivError) as e:
+                mp.mpdiv_serve_poll(c, t, len(u), len(v), timeout_us=30_000_000)
+            assert e.value.code == mp.MPDIV_ECUDA and e.value.status == mp.MPDIV_ST_INTERNAL
+        with pytest.raises(mp.MpdivError) as e:
+            mp.mpdiv_serve_submit(c, *items[1])
+        assert e.value.code == mp.MPDIV_ECUDA
+        completed, launches, batched = mp.mpdiv_serve_stats(c)
+        assert completed == 1 and launches == 2
+        with pytest.raises(mp.MpdivError) as e:
+            mp.mpdiv_serve_stop(c)
+        assert e.value.code == mp.MPDIV_ECUDA
+        mp.mpdiv_serve_start(c, pool_digits=1 << 22)  # a new server starts clean
+        u, v = items[2]
+        t = _submit_retry(mp, c, u, v)
+        rc, q, r, st = mp.mpdiv_serve_poll(c, t, len(u), len(v), timeout_us=30_000_000)
+        qo, ro, _ = oracle.divmod_u32(u, v, len(u), len(v))
+        assert rc == mp.MPDIV_OK and st == 0 and (q == qo).all() and (r == ro).all()
+        mp.mpdiv_serve_stop(c)
+    finally:
+        mp.mpdiv_destroy(c)
