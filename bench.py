@@ -471,7 +471,7 @@ def other_configs_summary(mp, ctx, dev, stream, args):
     mixed = {"div_s": _sig(m["div_per_s"]), "plain_class_div_s": _sig(m["plain_per_size_class"]["div_per_s"]),
              "over_plain": _sig(m["batched_over_plain_class"]), "n": m["n"], "clk": _clk(m["clocks"])}
     cap, sv = measure_serve(mp, ctx, dev, stream, args.requests, args.max_batch, args.max_inflight, args.low_water,
-                            repeat_top=3)
+                            repeat_top=3, batch_step=args.batch_step, max_wait_us=args.max_wait_us)
     loads = {}
     for k, x in sv.items():
         d = {"div_s": _sig(x["sustained_div_per_s"]), "p50_ms": _sig(x["p50_ms"], 3), "p99_ms": _sig(x["p99_ms"], 3),
@@ -590,7 +590,7 @@ def measure_mixed(mp, ctx, dev, stream, steps, warmup, per_n=True):
 
 
 def measure_serve(mp, ctx, dev, stream, n_req, max_batch, max_inflight, low_water, loads=(0.5, 0.8, 0.95),
-                  repeat_top=1):
+                  repeat_top=1, batch_step=0, max_wait_us=0):
     """Config 4: Poisson arrivals of mixed-precision requests through the
     serving loop at fractions of the plain path's measured capacity (one plain
     launch per size class); the last load is run repeat_top times."""
@@ -623,7 +623,7 @@ def measure_serve(mp, ctx, dev, stream, n_req, max_batch, max_inflight, low_wate
             st = np.full(n_req, -9, np.int32)
             lat = np.zeros(n_req, np.int64)
             mp.mpdiv_serve_start(ctx, pool_digits=256 << 20, max_batch=max_batch, max_inflight=max_inflight,
-                                 low_water=low_water)
+                                 low_water=low_water, batch_step=batch_step, max_wait_us=max_wait_us)
             with ClockSampler(dev.index or 0) as clk:
                 t0 = time.perf_counter()
                 rej = mp.mpdiv_serve_replay(ctx, arr, R["u_flat"], uo, ul, R["v_flat"], vo, vl, q, qo, ul.copy(), r,
@@ -692,7 +692,7 @@ def run_mixed(args, dev, dist, rank, ws):
     import paper_2606_06386_gb300 as mp
 
     mp.build()
-    ctx = mp.mpdiv_init(dev.index or 0)
+    ctx = mp.mpdiv_init(dev.index or 0, flags=PERSISTENT_QUEUE if args.persistent_queue else 0)
     _tune_classes(mp, ctx)
     stream = torch.cuda.current_stream(dev)
     _barrier(dist, dev)
@@ -728,11 +728,11 @@ def run_serve(args, dev, dist, rank, ws):
     import paper_2606_06386_gb300 as mp
 
     mp.build()
-    ctx = mp.mpdiv_init(dev.index or 0)
+    ctx = mp.mpdiv_init(dev.index or 0, flags=PERSISTENT_QUEUE if args.persistent_queue else 0)
     _tune_classes(mp, ctx)
     stream = torch.cuda.current_stream(dev)
     cap, res = measure_serve(mp, ctx, dev, stream, args.requests, args.max_batch, args.max_inflight, args.low_water,
-                             repeat_top=3)
+                             repeat_top=3, batch_step=args.batch_step, max_wait_us=args.max_wait_us)
     n_req = args.requests
     out = {
         "metric": METRIC, "value": res["95%"]["sustained_div_per_s"], "unit": UNIT, "n_gpus": ws,
@@ -896,6 +896,13 @@ def main():
     ap.add_argument("--max-inflight", type=int, default=32, help="serve workload: batches in flight")
     ap.add_argument("--low-water", type=int, default=2048, help="serve workload: requests on the GPU below "
                     "which queued requests launch at once")
+    ap.add_argument("--batch-step", type=int, default=0, help="serve workload: queued requests of a class per "
+                    "batch of that class in flight before a launch, below the low-water mark (0: 8)")
+    ap.add_argument("--max-wait-us", type=int, default=0, help="serve workload: longest wait of a queued request "
+                    "for its batch to grow (0: 2000)")
+    ap.add_argument("--persistent-queue", action="store_true", help="mixed and serve workloads: ragged batches by "
+                    "the self-splitting persistent kernel (MPDIV_FLAG_PERSISTENT_QUEUE) instead of one plain launch "
+                    "per size class")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

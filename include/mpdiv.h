@@ -244,9 +244,9 @@ int mpdiv_mul_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, const ui
  * launch. Admission is by footprint: a request's footprint class is the size
  * class of its dividend (class 0: at most 1024 digits, 1: 2048, 2: 4096,
  * 3: 8192, 4: more), which sets the shared memory and block shape its
- * division needs; each class has its own share of the operand pool, and a
- * batch holds requests of one class only, so that a large request never sets
- * the launch shape of small ones. Batches of different classes run at once. */
+ * division needs; each class has its own queue, and a batch holds requests of
+ * one class only, so that a large request never sets the launch shape of small
+ * ones. Batches of different classes run at once. */
 #define MPDIV_SERVE_CLASSES 5
 typedef struct mpdiv_serve_config {
   int64_t pool_digits;  /* digits of device operand/result pool (0: 64 Mi digits) */
@@ -254,9 +254,11 @@ typedef struct mpdiv_serve_config {
   int32_t max_inflight; /* batches in flight at once, each on its own stream (0: 32) */
   int32_t max_pending;  /* submitted-but-unfinished requests before EBUSY (0: 1<<20) */
   int32_t low_water;    /* below this many requests on the GPU, queued requests launch as
-                           soon as there are 8 of them per batch in flight; above it they
-                           gather into larger batches (0: 2048) */
+                           soon as there are batch_step of them per batch in flight; above it
+                           they gather into larger batches (0: 2048) */
   int32_t max_wait_us;  /* longest a queued request waits for its batch to grow (0: 2000) */
+  int32_t batch_step;   /* below low_water, a class's queued requests launch once there are this
+                           many per batch of that class in flight (0: 8) */
 } mpdiv_serve_config;
 
 /* Start the server on ctx (cfg may be NULL). MPDIV_ESTATE if one is running.
@@ -266,9 +268,9 @@ int mpdiv_serve_start(mpdiv_ctx *ctx, const mpdiv_serve_config *cfg);
 
 /* Submit one division from host memory; the operands are copied before the
  * call returns. *ticket identifies the request. MPDIV_EBUSY when the request
- * would exceed max_pending, finds its class's share of the pool full (retry
- * later) or can never fit it, or when the ticket 2*max_pending (rounded up to
- * a power of two) before it has not been polled yet; MPDIV_EUNSUPPORTED for
+ * would exceed max_pending, finds the pool full (retry later) or can never
+ * fit it, or when the ticket 2*max_pending (rounded up to a power of two)
+ * before it has not been polled yet; MPDIV_EUNSUPPORTED for
  * sizes beyond MPDIV_MAX_LIMBS; MPDIV_ECUDA once a batch has failed to launch
  * (the server then refuses work until it is stopped). Thread-safe. */
 int mpdiv_serve_submit(mpdiv_ctx *ctx, const uint32_t *u_host, int32_t u_len, const uint32_t *v_host,

@@ -24,6 +24,7 @@ SO_PATH = os.path.join(_BUILD, "libmpdiv.so")
 HEADER = os.path.join(_ROOT, "include", "mpdiv.h")
 SOURCES = ["mpdiv_p.cu", "mpdiv_p16.cu", "mpdiv_q.cu", "mpdiv_t.cu", "mpdiv_k1.cu", "mpdiv_k2.cu", "mpdiv_k4.cu", "mpdiv_k8.cu", "mpdiv_k16.cu",
            "mpdiv_k4r.cu", "mpdiv_k8r.cu", "mpdiv_k16r.cu",
+           "mpdiv_l1.cu", "mpdiv_l2.cu", "mpdiv_l4.cu", "mpdiv_l8.cu", "mpdiv_l16.cu", "mpdiv_l32.cu",
            "mpdiv_k32.cu", "mpdiv_n.cu", "mpdiv_n8.cu", "mpdiv_n16.cu", "mpdiv_n32.cu",
            "mpdiv_n2.cu", "mpdiv_n3.cu", "mpdiv_noalloc.cu", "mpdiv.cu", "mpdiv_tune.cu", "mpdiv_serve.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
@@ -96,6 +97,7 @@ class mpdiv_serve_config(ctypes.Structure):
         ("max_pending", ctypes.c_int32),
         ("low_water", ctypes.c_int32),
         ("max_wait_us", ctypes.c_int32),
+        ("batch_step", ctypes.c_int32),
     ]
 
 
@@ -323,8 +325,8 @@ def mpdiv_tuning(ctx, u_limbs: int):
 
 # ---------------------------------------------------------------- serving
 def mpdiv_serve_start(ctx, pool_digits: int = 0, max_batch: int = 0, max_inflight: int = 0, max_pending: int = 0,
-                      low_water: int = 0, max_wait_us: int = 0):
-    cfg = mpdiv_serve_config(pool_digits, max_batch, max_inflight, max_pending, low_water, max_wait_us)
+                      low_water: int = 0, max_wait_us: int = 0, batch_step: int = 0):
+    cfg = mpdiv_serve_config(pool_digits, max_batch, max_inflight, max_pending, low_water, max_wait_us, batch_step)
     _check(ctx, lib().mpdiv_serve_start(ctx, ctypes.byref(cfg)))
 
 

@@ -27,6 +27,11 @@ struct UniformArgs {
   const int32_t* list;
   const int64_t *u_off, *v_off, *q_off, *r_off;
   const int32_t *u_len, *v_len, *q_len, *r_len;
+  // 0: one pass. 1: the fit pass, whose shared memory covers the items whose
+  // operands' effective lengths are their buffers' (an item whose plan is
+  // larger gets the internal retry status); 2: the retry pass, which divides
+  // only the items with that status, in shared memory for any item.
+  int pass;
 };
 
 struct RaggedArgs {

@@ -41,7 +41,6 @@ constexpr int RED_WORDS = 100;           // block scratch: 3 x 32 per-warp slots
 // block scratch layout
 constexpr int RED_CNT = 96;     // multiply work counter
 constexpr int RED_AUX = 97;     // misc broadcast
-constexpr int RED_RIPPLE = 98;  // multiply: a strip fold carried past its two columns
 
 // A group of whole warps that cooperates on one division: the whole thread
 // block, or a slice of it synchronised by its own named barrier.
@@ -599,30 +598,37 @@ __device__ MP_MUL_ATTR void mul_t(const Blk& b, uint32_t* C, int npos, uint32_t*
     mul_strip<T>(b, Cw, npos, A, na, Bv, nb, OV, plo + ws * WSPAN, ws);
   }
   group_sync<WHOLE>(b);
-  // fold each strip's two overflow digits into the next strip's first two
-  // columns, one thread per strip boundary; a carry out of those two columns
+  if (nws == 1) return;  // one strip: its overflow digits lie beyond the product
+  // warp 0 folds each strip's two overflow digits into the next strip's first
+  // two columns, a lane per strip boundary; a carry out of those two columns
   // (rare: it needs the high overflow digit plus the column to reach B) is
   // recorded in the consumed overflow word and added afterwards, boundary by
-  // boundary, with a full carry ripple
-  for (int s = 1 + b.tid; s < nws; s += b.nt) {
-    const int c = plo + s * WSPAN;  // < npos
-    uint64_t t = (uint64_t)Cw[c] + OV[2 * (s - 1)];
-    Cw[c] = (uint32_t)t;
-    uint32_t k = 0u;
-    if (c + 1 < npos) {
-      t = (uint64_t)Cw[c + 1] + OV[2 * (s - 1) + 1] + (t >> 32);
-      Cw[c + 1] = (uint32_t)t;
-      k = (c + 2 < npos) ? (uint32_t)(t >> 32) : 0u;
+  // boundary, with a full carry ripple by the same warp
+  if (b.warp == 0) {
+    uint32_t any = 0u;
+    for (int s0 = 1; s0 < nws; s0 += 32) {
+      const int s = s0 + b.lane;
+      uint32_t kc = 0u;
+      if (s < nws) {
+        const int c = plo + s * WSPAN;  // < npos
+        uint64_t t = (uint64_t)Cw[c] + OV[2 * (s - 1)];
+        Cw[c] = (uint32_t)t;
+        if (c + 1 < npos) {
+          t = (uint64_t)Cw[c + 1] + OV[2 * (s - 1) + 1] + (t >> 32);
+          Cw[c + 1] = (uint32_t)t;
+          kc = (c + 2 < npos) ? (uint32_t)(t >> 32) : 0u;
+        }
+        OV[2 * (s - 1)] = kc;
+      }
+      any |= __ballot_sync(FULL, kc != 0u);
     }
-    OV[2 * (s - 1)] = k;
-    if (k) b.red[RED_RIPPLE] = 1;
+    if (any != 0u) {
+      __syncwarp();
+      for (int s = 1; s < nws; s++)
+        if (OV[2 * (s - 1)] != 0u) ripple_add_one(b, Cw, plo + s * WSPAN + 2, npos);
+    }
   }
   group_sync<WHOLE>(b);
-  if (b.red[RED_RIPPLE] != 0 && b.warp == 0) {
-    for (int s = 1; s < nws; s++)
-      if (OV[2 * (s - 1)] != 0u) ripple_add_one(b, Cw, plo + s * WSPAN + 2, npos);
-  }
-  group_sync<WHOLE>(b);  // also orders every read of RED_RIPPLE before the next multiply resets it
 }
 
 // Zero digits a multiply operand needs on each side for T columns per lane.
@@ -675,10 +681,7 @@ __device__ inline int mul(const Blk& b, uint32_t* C, int npos, uint32_t* X, int 
     A[na + i] = 0u;
     if (i < T_MAX) Bv[nb + i] = 0u;
   }
-  if (b.tid == 0) {
-    b.red[RED_CNT] = 0;
-    b.red[RED_RIPPLE] = 0;
-  }
+  if (b.tid == 0) b.red[RED_CNT] = 0;
   b.sync();
   constexpr bool kWhole = !MP_NAMED_GROUPS;
   // in groups of several warps, a product with fewer strips than the group

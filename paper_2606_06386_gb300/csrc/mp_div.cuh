@@ -26,11 +26,12 @@
 //   W  [h-kl+9]        shifted inverse; later the quotient q
 //   X  [kl+32]         divisor prefix v' and PowDiff result x      } u overlays
 //   R  [h-kl+16]       Step result before its shift                } X..R later
-//   P  products: clipped, max(h-kl+240, kl+32) (the clipped products keep
+//   P  products: clipped, max(h-kl+17, kl+32) (the clipped products keep
 //      only their top columns, stored from the lowest kept column up);
 //      full, max(h+41, 2h-kl+9)
 //   OV [two words per 96-column strip of P] multiply overflow digits
-// The total is largest at kl = 1: about 3 h digits clipped, 4 h full.
+// The total is largest at kl = 1 or kl = h: about 3 h digits clipped, 4 h
+// full; at kl = h/2 it is about 2.5 h clipped.
 // With full products and the number-theoretic transform enabled, the shared
 // memory left after OV is the transform's scratch: products of up to 2^s_log
 // digits with 4 * 2^s_log <= the words left use the transform.
@@ -41,7 +42,13 @@
 namespace mp {
 
 enum : int { ST_OK = 0, ST_DIV_BY_ZERO = 1, ST_CORR = 2, ST_QOVF = 3, ST_INTERNAL = 4 };
+// Internal status of a launch's fit pass: the item's plan exceeds the
+// launch's shared memory, and the retry pass divides it (never returned).
+constexpr int ST_RETRY = 5;
 enum : int { FLAG_INJECT_LAMBDA = 1, FLAG_FULL_PRODUCTS = 2 };
+// Internal flag (above the library's flags): an item whose plan exceeds the
+// shared memory gets ST_RETRY instead of ST_INTERNAL.
+constexpr int FLAG_FIT_OR_RETRY = 1 << 20;
 
 // Guard digits of the clipped products: skipping the digit products below
 // position c - QGUARD of a product whose digits below c are shifted away drops
@@ -65,12 +72,14 @@ struct Layout {
 };
 
 // Product buffer. Clipped: the Newton step keeps at most |R| - 1 digits above
-// its dropped ones plus QGUARD guard digits, i.e. at most h-kl+17 digits; the
-// quotient at most |W| + QGUARD; PowDiff's products and the remainder fit in
-// |X| = kl+32 digits (the bound below keeps 224 digits of room). Full: the Newton step's and the quotient's full products.
+// its dropped ones plus QGUARD guard digits, i.e. at most h-kl+17 digits (its
+// result's length is checked against |R| first); the quotient at most
+// |W| + QGUARD = h-kl+11; PowDiff's products and the remainder fit in
+// |X| = kl+32 digits (checked against |X|). Full: the Newton step's and the
+// quotient's full products.
 __host__ __device__ __forceinline__ int cap_p(int h, int kl, bool clip) {
   if (clip) {
-    const int a = h - kl + 240, c = kl + 32;
+    const int a = h - kl + 17, c = kl + 32;
     return a > c ? a : c;
   }
   const int a = h + 41, c = 2 * h - kl + 9;
@@ -93,10 +102,12 @@ __host__ __device__ __forceinline__ int layout_words(int h, int kl, bool clip, i
   return 5 * pad + kl + (h - kl + 9) + (kl + 32) + (h - kl + 16) + capP + capOV + 5 * 3;
 }
 
-// Words of dynamic shared memory that cover every item with at most h digits
-// (the plan is largest for a one-digit divisor).
+// Words of dynamic shared memory that cover every item with at most h
+// dividend digits (the plan is largest for a one-digit divisor or one as long
+// as the dividend; only divisors of at most h digits get a plan).
 __host__ __device__ __forceinline__ int smem_words_for(int h, bool clip, int pad) {
-  return layout_words(h, 1, clip, pad);
+  const int a = layout_words(h, 1, clip, pad), b = layout_words(h, h, clip, pad);
+  return a > b ? a : b;
 }
 
 __device__ __forceinline__ Layout make_layout(uint32_t* sm, int h, int kl, bool clip, int pad) {
@@ -445,7 +456,7 @@ __device__ __forceinline__ int div_item(const Blk& b, uint32_t* sm, int smem_wor
   }
   const bool clip = (flags & FLAG_FULL_PRODUCTS) == 0;
   Layout L = make_layout(sm, h, kl, clip, layout_pad(clip, b.tcols));
-  if (L.total > smem_words) return ST_INTERNAL;
+  if (L.total > smem_words) return (flags & FLAG_FIT_OR_RETRY) ? ST_RETRY : ST_INTERNAL;
   if (NTT && ntt_tab != nullptr && !clip) layout_ntt_scratch(L, sm, smem_words, ntt_tab, ntt_cut);
   for (int i = b.tid; i < L.total; i += b.nt) sm[i] = 0u;
   b.sync();

@@ -8,20 +8,26 @@
 namespace mp {
 
 // Plain launch: block b handles items b, b + gridDim.x, ... of a uniform
-// batch, or of a ragged batch's item list (a.list: one size class of a
-// ragged batch, largest first). NTT: full products may use the transform,
-// with its scratch after the item's layout.
-template <int NW, int MINB, bool NTT = false>
+// batch, or (LIST) of a ragged batch's item list (a.list: one size class of a
+// ragged batch, most expensive first); a compile-time choice, since the list's
+// indirection measured 1-2 % slower in the strided launch. NTT: full products
+// may use the transform, with its scratch after the item's layout. a.pass
+// selects the fit pass or the retry pass (UniformArgs).
+template <int NW, int MINB, bool NTT = false, bool LIST = false>
 __global__ void __launch_bounds__(NW * 32, MINB) k_div_uniform(UniformArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int red[RED_WORDS];
   Blk b = make_block<NW>(red);
   b.tcols = a.tcols;
   b.kcut = a.kcut;
+  const int flags = a.pass == 1 ? (a.flags | FLAG_FIT_OR_RETRY) : a.flags;
   for (int64_t slot = blockIdx.x; slot < a.n; slot += gridDim.x) {
+    const int64_t item = LIST ? (int64_t)a.list[slot] : slot;
+    // retry pass: only the items the fit pass left (every thread reads the
+    // status before the item's first barrier, so the branch is uniform)
+    if (a.pass == 2 && a.status[item] != ST_RETRY) continue;
     ItemIO io;
-    int64_t item = slot;
-    if (a.list == nullptr) {
+    if (!LIST) {
       io.u = a.u + item * a.us;
       io.un = a.un;
       io.v = a.v + item * a.vs;
@@ -31,7 +37,6 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_uniform(UniformArgs a) {
       io.r = a.r + item * a.rs;
       io.rn = a.rn;
     } else {
-      item = a.list[slot];
       io.u = a.u + a.u_off[item];
       io.un = a.u_len[item];
       io.v = a.v + a.v_off[item];
@@ -45,7 +50,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_div_uniform(UniformArgs a) {
     unsigned long long work = 0ull;
     Blk bw = b;
     bw.work = a.products ? &work : nullptr;
-    const int st = div_item<NTT>(bw, sm, a.smem_words, io, a.flags, &it, nullptr, 0, 0, a.ntt, a.ntt_cut);
+    const int st = div_item<NTT>(bw, sm, a.smem_words, io, flags, &it, nullptr, 0, 0, a.ntt, a.ntt_cut);
     if (b.tid == 0) {
       a.status[item] = st;
       if (a.iters) a.iters[item] = it;

@@ -188,6 +188,17 @@ static int prepare_kernel(mpdiv_ctx* ctx, void* k, int smem) {
   return mpdiv_cuda_check(ctx, mpdiv_open_kernel_smem(k, smem), "cudaFuncSetAttribute(max dynamic shared memory)");
 }
 
+void* mp_kernel_list(int warps) {
+  switch (warps) {
+    case 1: return mp_kernel_list1();
+    case 2: return mp_kernel_list2();
+    case 4: return mp_kernel_list4();
+    case 8: return mp_kernel_list8();
+    case 16: return mp_kernel_list16();
+    default: return mp_kernel_list32();
+  }
+}
+
 // The 128-register build of the plain kernel for a block of w warps (4, 8
 // or 16), or null.
 static void* wide_uniform_kernel(int w) {
@@ -207,11 +218,18 @@ static int kernel_occupancy(mpdiv_ctx* ctx, void* k, int threads, int smem) {
 }
 
 // ------------------------------------------------------------------ init / destroy
-// Streams and events of the class form's forked launches.
+// Streams and events of the class form's forked launches. The class runs are
+// ordered largest first, and side stream i has the i-th highest priority, so
+// that the block scheduler starts the largest divisions first and the smaller
+// classes' blocks fill the SMs that free up (largest-first across the classes).
 static int mpdiv_create_side_streams(mpdiv_ctx* ctx) {
   int rc = mpdiv_cuda_check(ctx, cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming), "cudaEventCreate");
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) least = greatest = 0;
   for (int i = 0; i < kMaxRuns && rc == MPDIV_OK; i++) {
-    rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking), "cudaStreamCreate");
+    const int prio = std::min(least, greatest + i);  // numerically lower is higher priority
+    rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithPriority(&ctx->side[i], cudaStreamNonBlocking, prio),
+                          "cudaStreamCreate");
     if (rc == MPDIV_OK)
       rc = mpdiv_cuda_check(ctx, cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming), "cudaEventCreate");
   }
@@ -317,15 +335,20 @@ int mpdiv_prepare_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, PreparedLaunch
                            ctx->max_smem);
   int warps = L.warps > 0 ? kernel_warps(L.warps) : mpdiv_default_warps(ctx, max_digits);
   if (ntt_tables(ctx)) warps = ntt_kernel_warps(warps);
-  void* k = ntt_tables(ctx) ? ntt_kernel_for(KK_UNIFORM, warps) : kernel_for(KK_UNIFORM, warps);
+  if (L.list != nullptr && ntt_tables(ctx) != nullptr)
+    return mpdiv_set_error(ctx, MPDIV_EINVAL, "item lists are not built with the transform");
+  void* k = L.list != nullptr ? mp_kernel_list(warps)
+            : ntt_tables(ctx)  ? ntt_kernel_for(KK_UNIFORM, warps)
+                               : kernel_for(KK_UNIFORM, warps);
   int rc = prepare_kernel(ctx, k, smem);
   if (rc) return rc;
   // 128 registers per thread where the block size has such a build and the
-  // tuner or the configuration asks for it. Not by default: on GB300 the
-  // 128-register builds ran 0.5-6 % slower than the 64-register ones at every
-  // sweep size, although shared memory held the SM to as few blocks as 128
-  // registers allow and the 64-register builds spill a few hundred bytes
-  if (void* kw = ntt_tables(ctx) ? nullptr : wide_uniform_kernel(warps)) {
+  // tuner or the configuration asks for it (strided launches only). Not by
+  // default: on GB300 the 128-register builds ran 0.5-6 % slower than the
+  // 64-register ones at every sweep size, although shared memory held the SM
+  // to as few blocks as 128 registers allow and the 64-register builds spill a
+  // few hundred bytes
+  if (void* kw = (ntt_tables(ctx) || L.list) ? nullptr : wide_uniform_kernel(warps)) {
     const int regs = L.regs > 0 ? L.regs : mpdiv_default_regs(ctx, max_digits);
     if (regs == 128) {
       if ((rc = prepare_kernel(ctx, kw, smem))) return rc;
@@ -369,6 +392,40 @@ int mpdiv_prepare_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, PreparedLaunch
   P->grid = std::min<int64_t>(L.n, 0x7fffffff);
   P->threads = 32 * warps;
   P->smem = smem;
+  P->retry_grid = 0;
+  P->retry_smem = 0;
+  // clipped products without the transform: a fit pass with shared memory for
+  // the batch's own operand lengths (the largest plan of the listed items, or
+  // of a uniform batch's digit counts) when it lets more blocks share an SM,
+  // then a retry pass for the items whose effective lengths need more
+  const bool clip = (ctx->cfg.flags & MPDIV_FLAG_FULL_PRODUCTS) == 0;
+  if (clip && ntt_tables(ctx) == nullptr) {
+    const int pad = layout_pad(true, tcols);
+    int fit_words = 0;
+    if (L.list == nullptr) {
+      fit_words = layout_words(L.un, std::min(L.vn, L.un), true, pad);
+    } else if (L.list_host != nullptr) {
+      for (int64_t i = 0; i < L.n; i++) {
+        const int it = L.list_host[i];
+        const int h = L.u_len_host[it], kl = std::min(L.v_len_host[it], h);
+        fit_words = std::max(fit_words, layout_words(h, kl, true, pad));
+      }
+    }
+    const int fit = (fit_words * 4 + 15) & ~15;
+    if (fit > 0 && fit < smem) {
+      const int occ_fit = kernel_occupancy(ctx, k, 32 * warps, fit);
+      const int occ_full = kernel_occupancy(ctx, k, 32 * warps, smem);
+      // only a batch of more than one wave of full-size blocks gains from
+      // more blocks per SM; a smaller one keeps one launch
+      if (occ_full >= 1 && occ_fit > occ_full && L.n > (int64_t)ctx->num_sms * occ_full) {
+        a.pass = 1;
+        a.smem_words = fit / 4;
+        P->smem = fit;
+        P->retry_smem = smem;
+        P->retry_grid = std::min<int64_t>(std::min<int64_t>(L.n, (int64_t)ctx->num_sms * occ_full), 0x7fffffff);
+      }
+    }
+  }
   return MPDIV_OK;
 }
 
@@ -376,7 +433,13 @@ int mpdiv_launch_prepared(mpdiv_ctx* ctx, const PreparedLaunch& P, cudaStream_t 
   UniformArgs a = P.args;
   void* args[] = {&a};
   cudaError_t e = cudaLaunchKernel(P.kernel, dim3((unsigned)P.grid), dim3(P.threads), args, P.smem, stream);
-  return mpdiv_cuda_check(ctx, e, "launch of the division kernel");
+  int rc = mpdiv_cuda_check(ctx, e, "launch of the division kernel");
+  if (rc != MPDIV_OK || P.retry_grid == 0) return rc;
+  // the retry pass: the items the fit pass left, in shared memory for any item
+  a.pass = 2;
+  a.smem_words = P.retry_smem / 4;
+  e = cudaLaunchKernel(P.kernel, dim3((unsigned)P.retry_grid), dim3(P.threads), args, P.retry_smem, stream);
+  return mpdiv_cuda_check(ctx, e, "launch of the division kernel's retry pass");
 }
 
 int mpdiv_launch_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, cudaStream_t stream) {
@@ -573,6 +636,9 @@ static int launch_ragged_classes(mpdiv_ctx* ctx, const RaggedLaunch& L, const in
     U.v_len = L.v_len;
     U.q_len = L.q_len;
     U.r_len = L.r_len;
+    U.list_host = h_order + start;
+    U.u_len_host = L.u_len_host;
+    U.v_len_host = L.v_len_host;
     runs.emplace_back();
     int rc = mpdiv_prepare_uniform(ctx, U, &runs.back());
     if (rc) return rc;
@@ -601,6 +667,8 @@ static int launch_ragged_classes(mpdiv_ctx* ctx, const RaggedLaunch& L, const in
     P.grid = runs[i].grid;
     P.threads = runs[i].threads;
     P.smem = runs[i].smem;
+    P.retry_grid = runs[i].retry_grid;
+    P.retry_smem = runs[i].retry_smem;
     std::memcpy(desc.data() + i * sizeof P, &P, sizeof P);
   }
   int rc;
@@ -637,8 +705,8 @@ static int launch_ragged_classes(mpdiv_ctx* ctx, const RaggedLaunch& L, const in
 int mpdiv_launch_ragged(mpdiv_ctx* ctx, const RaggedLaunch& L, cudaStream_t stream) {
   int max_u = 1;
   for (int64_t i = 0; i < L.n; i++) max_u = std::max(max_u, (int)L.u_len_host[i]);
-  // the self-splitting kernel is built without the transform
-  const int form = (L.form == RF_SPLIT && ntt_tables(ctx) != nullptr) ? RF_QUEUE : L.form;
+  // the self-splitting kernel and the item-list kernels are built without the transform
+  const int form = (L.form != RF_QUEUE && ntt_tables(ctx) != nullptr) ? RF_QUEUE : L.form;
   std::lock_guard<std::mutex> g(ctx->ragged_mu);
   // launches with the context's queue head and order array are ordered on the
   // GPU one after another, whatever their streams (ragged_ev marks the last one)

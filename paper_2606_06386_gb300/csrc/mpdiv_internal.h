@@ -83,14 +83,23 @@ struct UniformLaunch {
   const int32_t* list;
   const int64_t *u_off, *v_off, *q_off, *r_off;
   const int32_t *u_len, *v_len, *q_len, *r_len;
+  // host copies of the list and of the items' digit counts (with list): the
+  // fit pass's shared memory covers the largest plan of the listed items
+  const int32_t *list_host, *u_len_host, *v_len_host;
 };
 
-// A plain launch ready to go: kernel, arguments, grid, threads, shared memory.
+// A plain launch ready to go: kernel, arguments, grid, threads, shared memory;
+// with retry_grid > 0 a fit pass (args.pass = 1, shared memory for the batch's
+// own operand lengths, so more blocks fit on an SM) followed by a retry pass
+// (grid retry_grid, shared memory retry_smem) for the items whose effective
+// lengths need a larger plan.
 struct PreparedLaunch {
   void* kernel = nullptr;
   mp::UniformArgs args{};
   int64_t grid = 0;
   int threads = 0, smem = 0;
+  int64_t retry_grid = 0;
+  int retry_smem = 0;
 };
 
 struct RaggedLaunch {

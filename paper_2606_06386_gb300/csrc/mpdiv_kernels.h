@@ -17,6 +17,15 @@ void* mp_kernel_w32(int kind);
 void* mp_kernel_w4_wide();
 void* mp_kernel_w8_wide();
 void* mp_kernel_w16_wide();
+// the plain division kernel over a ragged batch's item list (64 registers),
+// mpdiv_l{1,2,4,8,16,32}.cu: the class form of mpdiv_batch_ragged
+void* mp_kernel_list(int warps);
+void* mp_kernel_list1();
+void* mp_kernel_list2();
+void* mp_kernel_list4();
+void* mp_kernel_list8();
+void* mp_kernel_list16();
+void* mp_kernel_list32();
 void* mp_kernel_persistent(int warps);  // 8 (warps <= 8) or 16 warps per block
 void* mp_kernel_persistent8();          // mpdiv_p.cu
 void* mp_kernel_persistent16();         // mpdiv_p16.cu

@@ -5,14 +5,15 @@
 // classes whose shared-memory plan and block shape the launches are tuned
 // for), and a batch holds requests of one class only, so that a large request
 // never sets the block shape and shared memory of a batch of small ones.
-// Operands travel through pinned host rings mirrored on the device, one input
-// ring per footprint class (u and v of every request of the class, in arrival
-// order) and one output ring (q and r of every launched request): the input
-// rings share the pool's input half, the output ring is its other half.
-// mpdiv_serve_submit reserves the request's digits at the tail of its class's
-// input ring and copies its operands there itself, outside the server lock. A
-// scheduler thread turns the oldest ready requests of a class into a batch: a
-// contiguous run of that class's ring (one host-to-device copy), per-item
+// Operands travel through two pinned host rings mirrored on the device: an
+// input ring (u and v of every request, in arrival order) and an output ring
+// (q and r of every launched request). mpdiv_serve_submit reserves the
+// request's digits at the tail of the input ring and copies its operands there
+// itself, outside the server lock. A scheduler thread turns the oldest ready
+// requests of a class into a batch: the run of the input ring from its first
+// request to its last (one host-to-device copy on the server's copy stream; the
+// run may hold requests of other classes and requests still being copied in,
+// see copy_stream), per-item
 // offsets and a most-expensive-first order (one more copy), one plain launch
 // over the batch with the class's tuned shape (or, with
 // MPDIV_FLAG_PERSISTENT_QUEUE, one launch of the self-splitting persistent
@@ -21,7 +22,7 @@
 // Up to max_inflight batches run at once. The class whose oldest ready request
 // is oldest goes first. While fewer than low_water requests are on the GPU,
 // the queued requests of a class launch as soon as there are at least
-// kBatchStep of them for every batch of that class already in flight (so an
+// batch_step of them for every batch of that class already in flight (so an
 // idle class launches each request at once, and a busy one launches fewer,
 // larger batches instead of being bound by the launch path); otherwise they
 // gather into larger batches (up to max_batch, or until the oldest has waited
@@ -49,7 +50,7 @@
 namespace {
 
 // Requests a launch needs per batch already in flight while the GPU is below
-// its low-water mark (see the header comment).
+// its low-water mark (see the header comment), unless configured.
 constexpr int kBatchStep = 8;
 
 // Footprint classes: the dividend's size class (mp::class_of).
@@ -75,8 +76,8 @@ struct Request {
   int32_t u_len = 0, v_len = 0, q_len = 0, r_len = 0;
   int cls = 0;                    // footprint class
   bool failed = false;            // its batch could not be launched
-  int64_t in_off = -1;            // u at in_off, v at in_off + u_len (digits of the input half)
-  int64_t in_seq = -1;            // its allocation in its class's input ring
+  int64_t in_off = -1;            // u at in_off, v at in_off + u_len (input ring digits)
+  int64_t in_seq = -1;            // its input-ring allocation
   int64_t out_off = -1;           // q at out_off, r at out_off + q_len (output ring digits)
   std::shared_ptr<OutBatch> out;  // the batch's output allocation
   std::atomic<int> ready{0};      // operands copied into the ring
@@ -91,8 +92,7 @@ struct MpServer {
   mpdiv_ctx* ctx = nullptr;
   mpdiv_serve_config cfg{};
   uint32_t *d_in = nullptr, *h_in = nullptr, *d_out = nullptr, *h_out = nullptr;
-  mp_serve::Ring in_ring[kClasses], out_ring;
-  int64_t in_base[kClasses] = {};  // start of each class's ring in the input half
+  mp_serve::Ring in_ring, out_ring;
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
   std::deque<Request*> queue[kClasses];
@@ -109,9 +109,20 @@ struct MpServer {
   int64_t class_launches[kClasses] = {}, class_items[kClasses] = {};  // by the batch's largest dividend
   int64_t fail_launch = -1;  // test hook: the launch with this index fails on the host (-1: none)
   std::thread th;
+  // operand copies of every batch, in admission order: a batch's copy may
+  // span ring space of requests still being written by their submitters
+  // (skipped, to be taken by a later batch), and the later batch's own copy of
+  // that space must land after this stale one
+  cudaStream_t copy_stream = nullptr;
   struct Slot {
+    MpServer* server = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t copied = nullptr;  // the batch's operand copy is done
+    // set by a host function the slot's stream runs after the batch's results
+    // are on the host, so that the scheduler reads a flag per slot instead of
+    // querying an event
+    std::atomic<int> done{0};
     uint32_t *h_meta = nullptr, *d_meta = nullptr;  // offsets, lengths, order, heads, status
     bool busy = false;
     int cls = 0;  // footprint class of the batch in flight
@@ -121,8 +132,11 @@ struct MpServer {
   std::vector<Slot> slots;
   int64_t meta_words = 0;
 
+  std::vector<Request*> skipped;  // scheduler scratch: requests a batch passed over
+
   void run();
   bool launch(Slot& s);
+  static void CUDART_CB slot_done(void* p);
   void fail(Request* r, int64_t t);
 };
 
@@ -135,7 +149,7 @@ void MpServer::fail(Request* r, int64_t t) {
   r->status = MPDIV_ST_INTERNAL;
   r->t_done = t;
   r->state.store(RQ_DONE, std::memory_order_release);
-  in_ring[r->cls].release(r->in_seq);
+  in_ring.release(r->in_seq);
 }
 
 // metadata layout of a slot for n items: int64 offsets (u, v, q, r) as digit
@@ -183,10 +197,15 @@ bool MpServer::launch(Slot& s) {
   });
   std::memset(heads, 0, 8 * sizeof(int32_t));
   // operands: one contiguous run of the input ring
+  // operands: one run of the input ring, from the first request of the batch
+  // to the end of its last (a class's requests are in ring order), on the copy
+  // stream
   const int64_t in_lo = s.reqs.front()->in_off;
   const int64_t in_hi = s.reqs.back()->in_off + s.reqs.back()->u_len + s.reqs.back()->v_len;
   cudaError_t e = cudaMemcpyAsync(d_in + in_lo, h_in + in_lo, 4 * (size_t)(in_hi - in_lo), cudaMemcpyHostToDevice,
-                                  s.stream);
+                                  copy_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(s.copied, copy_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s.stream, s.copied, 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_meta, H, 4 * (size_t)status_w, cudaMemcpyHostToDevice, s.stream);
   const int64_t* d_off = reinterpret_cast<const int64_t*>(s.d_meta);
   const int32_t* d_len = reinterpret_cast<const int32_t*>(s.d_meta + 8 * n);
@@ -194,8 +213,11 @@ bool MpServer::launch(Slot& s) {
   int rc = (e == cudaSuccess) ? MPDIV_OK : MPDIV_ECUDA;
   if (rc == MPDIV_OK) {
     // one launch over the batch in the context's ragged form
-    std::vector<int32_t> ulh(n);
-    for (int64_t i = 0; i < n; i++) ulh[i] = s.reqs[i]->u_len;
+    std::vector<int32_t> ulh(n), vlh(n);
+    for (int64_t i = 0; i < n; i++) {
+      ulh[i] = s.reqs[i]->u_len;
+      vlh[i] = s.reqs[i]->v_len;
+    }
     RaggedLaunch L{};
     L.u = d_in;
     L.u_off = d_off;
@@ -211,7 +233,7 @@ bool MpServer::launch(Slot& s) {
     L.r_len = d_len + 3 * n;
     L.status = d_status;
     L.u_len_host = ulh.data();
-    L.v_len_host = ulh.data();
+    L.v_len_host = vlh.data();
     L.order = d_len + 4 * n;
     L.order_host = order;
     L.head = const_cast<int32_t*>(d_len + 5 * n);
@@ -225,8 +247,16 @@ bool MpServer::launch(Slot& s) {
                         s.stream);
   if (rc == MPDIV_OK && e == cudaSuccess)
     e = cudaMemcpyAsync(H + status_w, d_status, 4 * (size_t)n, cudaMemcpyDeviceToHost, s.stream);
-  if (rc == MPDIV_OK && e == cudaSuccess) e = cudaEventRecord(s.ev, s.stream);
+  if (rc == MPDIV_OK && e == cudaSuccess) e = cudaLaunchHostFunc(s.stream, slot_done, &s);
   return rc == MPDIV_OK && e == cudaSuccess;
+}
+
+// Host function run by a slot's stream once its batch's results and statuses
+// are on the host: flags the slot and wakes the scheduler (no CUDA call).
+void CUDART_CB MpServer::slot_done(void* p) {
+  Slot* s = static_cast<Slot*>(p);
+  s->done.store(1, std::memory_order_release);
+  s->server->cv_sched.notify_one();
 }
 
 void MpServer::run() {
@@ -236,7 +266,7 @@ void MpServer::run() {
     // ---- completions: results stay in the pinned output ring until polled
     finished.clear();
     for (auto& s : slots)
-      if (s.busy && cudaEventQuery(s.ev) == cudaSuccess) finished.push_back(&s);
+      if (s.busy && s.done.load(std::memory_order_acquire)) finished.push_back(&s);
     std::unique_lock<std::mutex> lk(mu);
     const int64_t t = now_ns();
     for (Slot* s : finished) {
@@ -247,12 +277,13 @@ void MpServer::run() {
         r->status = st[i];
         r->t_done = t;
         r->state.store(RQ_DONE, std::memory_order_release);
-        in_ring[r->cls].release(r->in_seq);
+        in_ring.release(r->in_seq);
       }
       completed += n;
       pending -= n;
       inflight_items -= n;
       s->reqs.clear();
+      s->done.store(0, std::memory_order_relaxed);
       s->busy = false;
     }
     if (!finished.empty()) cv_done.notify_all();
@@ -275,7 +306,7 @@ void MpServer::run() {
         if (queue[c].empty() || !queue[c].front()->ready.load(std::memory_order_acquire)) continue;
         const Request* f = queue[c].front();
         const int64_t waited_us = (t - f->t_submit) / 1000;
-        const bool go = (inflight_items < cfg.low_water && (int64_t)queue[c].size() >= (int64_t)kBatchStep * busy_c[c]) ||
+        const bool go = (inflight_items < cfg.low_water && (int64_t)queue[c].size() >= (int64_t)cfg.batch_step * busy_c[c]) ||
                         (int64_t)queue[c].size() >= cfg.max_batch || waited_us >= cfg.max_wait_us || quit;
         if (go && f->t_submit < oldest) {
           oldest = f->t_submit;
@@ -284,26 +315,37 @@ void MpServer::run() {
       }
     }
     if (adm >= 0) {
-      // the oldest ready requests of the class, contiguous in its ring, within the output ring
+      // the oldest ready requests of the class, in ring order and short of the
+      // ring's wrap, within the output ring; requests whose submitters are
+      // still copying their operands are skipped and stay queued in order
       std::deque<Request*>& qc = queue[adm];
       std::vector<Request*>& b = free_slot->reqs;
       int64_t out_need = 0;
       const int64_t out_room = out_ring.cap - out_ring.used - 4;
+      skipped.clear();
       while (!qc.empty() && (int64_t)b.size() < cfg.max_batch) {
         Request* r = qc.front();
-        if (!r->ready.load(std::memory_order_acquire)) break;
-        if (!b.empty() && r->in_off != b.back()->in_off + ((b.back()->u_len + b.back()->v_len + 3) & ~3)) break;
+        if (!b.empty() && r->in_off < b.back()->in_off) break;  // the ring wrapped
+        if (!r->ready.load(std::memory_order_acquire)) {
+          skipped.push_back(r);
+          qc.pop_front();
+          continue;
+        }
         const int64_t need = r->q_len + r->r_len;
         if (out_need + need > out_room) break;
         out_need += need;
         b.push_back(r);
         qc.pop_front();
       }
+      for (auto it = skipped.rbegin(); it != skipped.rend(); ++it) qc.push_front(*it);
       queued -= (int64_t)b.size();
       int64_t oseq = -1;
       const int64_t off = b.empty() ? -1 : out_ring.alloc(out_need, &oseq);
       if (off < 0) {
+        // put the batch back in ring order among the skipped requests
         for (auto it = b.rbegin(); it != b.rend(); ++it) qc.push_front(*it);
+        std::stable_sort(qc.begin(), qc.begin() + (ptrdiff_t)(b.size() + skipped.size()),
+                         [](const Request* x, const Request* y) { return x->in_off < y->in_off; });
         queued += (int64_t)b.size();
         b.clear();
       } else {
@@ -374,12 +416,9 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
   if (S->cfg.max_pending <= 0) S->cfg.max_pending = 1 << 20;
   if (S->cfg.low_water <= 0) S->cfg.low_water = 2048;
   if (S->cfg.max_wait_us <= 0) S->cfg.max_wait_us = 2000;
+  if (S->cfg.batch_step <= 0) S->cfg.batch_step = kBatchStep;
   const int64_t half = (S->cfg.pool_digits / 2) & ~int64_t(3);
-  const int64_t per_class = (half / kClasses) & ~int64_t(3);
-  for (int c = 0; c < kClasses; c++) {
-    S->in_ring[c].cap = per_class;
-    S->in_base[c] = c * per_class;
-  }
+  S->in_ring.cap = half;
   S->out_ring.cap = half;
   S->meta_words = meta_words_for(S->cfg.max_batch);
   {
@@ -393,11 +432,15 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
   if (!rc) rc = mpdiv_cuda_check(ctx, cudaMalloc(&S->d_out, 4 * (size_t)half), "server output ring");
   if (!rc) rc = mpdiv_cuda_check(ctx, cudaMallocHost(&S->h_in, 4 * (size_t)half), "server pinned input ring");
   if (!rc) rc = mpdiv_cuda_check(ctx, cudaMallocHost(&S->h_out, 4 * (size_t)half), "server pinned output ring");
-  S->slots.resize(S->cfg.max_inflight);
+  if (!rc)
+    rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking), "server copy stream");
+  S->slots = std::vector<MpServer::Slot>(S->cfg.max_inflight);
   for (auto& s : S->slots) {
+    s.server = S;
     if (rc) break;
     rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking), "server stream");
     if (!rc) rc = mpdiv_cuda_check(ctx, cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming), "server event");
+    if (!rc) rc = mpdiv_cuda_check(ctx, cudaEventCreateWithFlags(&s.copied, cudaEventDisableTiming), "server event");
     if (!rc) rc = mpdiv_cuda_check(ctx, cudaMallocHost(&s.h_meta, 4 * (size_t)S->meta_words), "server metadata");
     if (!rc) rc = mpdiv_cuda_check(ctx, cudaMalloc(&s.d_meta, 4 * (size_t)S->meta_words), "server metadata");
   }
@@ -419,7 +462,7 @@ extern "C" int mpdiv_serve_submit(mpdiv_ctx* ctx, const uint32_t* u_host, int32_
   if (u_len > MPDIV_MAX_LIMBS || v_len > MPDIV_MAX_LIMBS)
     return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "at most %d digits", MPDIV_MAX_LIMBS);
   const int cls = mp::class_of(u_len);
-  if (2 * (int64_t)(u_len + v_len) + 8 > S->in_ring[cls].cap)
+  if (2 * (int64_t)(u_len + v_len) + 8 > S->in_ring.cap)
     return mpdiv_set_error(ctx, MPDIV_EBUSY, "request larger than the server's rings");
   auto r = std::make_unique<Request>();
   r->u_len = u_len;
@@ -437,9 +480,9 @@ extern "C" int mpdiv_serve_submit(mpdiv_ctx* ctx, const uint32_t* u_host, int32_
     // the ticket's slot still holds an unpolled result from ticket - capacity
     if (S->by_ticket[S->next_ticket & S->ticket_mask].load(std::memory_order_acquire) != nullptr) return MPDIV_EBUSY;
     int64_t seq = -1;
-    const int64_t off = S->in_ring[cls].alloc(u_len + v_len, &seq);
-    if (off < 0) return MPDIV_EBUSY;  // the class's input ring is full: retry later
-    r->in_off = S->in_base[cls] + off;
+    const int64_t off = S->in_ring.alloc(u_len + v_len, &seq);
+    if (off < 0) return MPDIV_EBUSY;  // input ring full: retry later
+    r->in_off = off;
     r->in_seq = seq;
     r->ticket = S->next_ticket++;
     r->t_submit = now_ns();
@@ -571,12 +614,17 @@ void mpdiv_serve_shutdown(mpdiv_ctx* ctx) {
   for (auto& s : S->slots) {
     if (s.stream) cudaStreamSynchronize(s.stream);
     if (s.ev) cudaEventDestroy(s.ev);
+    if (s.copied) cudaEventDestroy(s.copied);
     if (s.stream) cudaStreamDestroy(s.stream);
     if (s.h_meta) cudaFreeHost(s.h_meta);
     if (s.d_meta) cudaFree(s.d_meta);
   }
   if (S->by_ticket)
     for (uint64_t i = 0; i <= S->ticket_mask; i++) delete S->by_ticket[i].exchange(nullptr);
+  if (S->copy_stream) {
+    cudaStreamSynchronize(S->copy_stream);
+    cudaStreamDestroy(S->copy_stream);
+  }
   cudaFree(S->d_in);
   cudaFree(S->d_out);
   if (S->h_in) cudaFreeHost(S->h_in);

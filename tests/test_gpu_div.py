@@ -343,3 +343,27 @@ def test_register_budgets_of_the_plain_kernel(tmp_path, monkeypatch, n, warps, c
         assert_same(host_u32(q), host_u32(r), st.cpu().numpy(), Qo, Ro, So)
     finally:
         mp.mpdiv_destroy(c)
+
+
+@pytest.mark.parametrize("n,kl", [(1024, 512), (2048, 1024), (4096, 2048), (3000, 1100)])
+def test_fit_pass_and_retry_pass(n, kl):
+    # the plain launch sizes its shared memory for the batch's digit counts
+    # (more blocks per SM); items whose effective divisor (or dividend) is
+    # shorter than its buffer need a larger plan and are divided by the retry
+    # pass: here a quarter of the divisors and some dividends have leading
+    # zero digits. Every status is 0 (no item is left behind) and every digit
+    # the oracle's, with the default shapes and with every strip width.
+    U = I.uniform_batch(64, n, seed=90 + n, stream=kl)
+    V = I.uniform_batch(64, kl, seed=91 + n, stream=kl)
+    rnd = np.random.default_rng(n + kl)
+    for i in range(0, 64, 4):
+        V[i, rnd.integers(1, kl):] = 0  # prec(v) < kl
+        if V[i].max() == 0:
+            V[i, 0] = 3
+    for i in range(1, 64, 8):
+        U[i, rnd.integers(kl, n):] = 0  # prec(u) < n
+    Qo, Ro, So = oracle_uniform(U, V)
+    for cols in (0, 3, 5, 7):
+        Q, R, S, _ = run_uniform(U, V, cols=cols)
+        assert (S == 0).all()
+        assert_same(Q, R, S, Qo, Ro, So)
