@@ -159,6 +159,13 @@ int mpdiv_batch_ragged(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, const
                        const int32_t *r_len, int32_t *status, int32_t *iters, int64_t *products,
                        const int32_t *u_len_host, const int32_t *v_len_host, void *stream);
 
+/* Kernel launches mpdiv_batch makes for n_items items of u_limbs and v_limbs
+ * digits on this context: 1, or 2 when the launch is split into a fit pass
+ * (shared memory for the batch's own digit counts, so that more blocks share
+ * an SM) and a retry pass (the items whose effective lengths need more). A
+ * negative error code for shapes mpdiv_batch would refuse. */
+int mpdiv_batch_launches(mpdiv_ctx *ctx, int64_t n_items, int32_t u_limbs, int32_t v_limbs);
+
 /* Test entry: the shifted inverse of Algorithm 1 for each item, as the
  * division path computes it (16-warp blocks; the context's strip width, 5 if
  * unset, and its MPDIV_FLAG_FULL_PRODUCTS flag): out + i*out_stride gets

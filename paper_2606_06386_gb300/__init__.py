@@ -111,6 +111,7 @@ _SIGS = {
     "mpdiv_batch_ragged": (ctypes.c_int, [_P, _I64] + [_P] * 18),
     "mpdiv_debug_shinv": (ctypes.c_int, [_P, _I64, _P, _I32, _I64, _P, _P, _I32, _I64, _P, _P, _P]),
     "mpdiv_autotune": (ctypes.c_int, [_P, _I32, _I32, _I32]),
+    "mpdiv_batch_launches": (ctypes.c_int, [_P, _I64, _I32, _I32]),
     "mpdiv_debug_primitive": (ctypes.c_int, [_P, _I32, _I64, _P, _I32, _P, _I32, _I32, _P, _I32, _P, _I32, _P]),
     "mpdiv_mul_batch": (ctypes.c_int, [_P, _I64, _P, _P, _I32, _I64, _P, _I64, _P]),
     "mpdiv_measure_peak": (ctypes.c_int, [_P, _I32, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -309,6 +310,11 @@ def mpdiv_measure_peak(ctx, kind: int = 0, iters: int = 0):
     rate, ms = ctypes.c_double(), ctypes.c_double()
     _check(ctx, lib().mpdiv_measure_peak(ctx, kind, iters, ctypes.byref(rate), ctypes.byref(ms)))
     return rate.value, ms.value
+
+
+def mpdiv_batch_launches(ctx, n_items: int, u_limbs: int, v_limbs: int) -> int:
+    """Kernel launches mpdiv_batch makes for that shape on this context (1 or 2)."""
+    return _check(ctx, lib().mpdiv_batch_launches(ctx, n_items, u_limbs, v_limbs))
 
 
 def mpdiv_autotune(ctx, u_limbs: int, v_limbs: int, n_items: int) -> int:

@@ -490,6 +490,23 @@ extern "C" int mpdiv_batch(mpdiv_ctx* ctx, int64_t n_items, const uint32_t* u, i
   return mpdiv_launch_uniform(ctx, L, (cudaStream_t)stream);
 }
 
+extern "C" int mpdiv_batch_launches(mpdiv_ctx* ctx, int64_t n_items, int32_t u_limbs, int32_t v_limbs) {
+  if (!ctx) return MPDIV_EINVAL;
+  if (n_items < 1 || u_limbs < 1 || v_limbs < 1) return mpdiv_set_error(ctx, MPDIV_EINVAL, "bad shape");
+  if (u_limbs > MPDIV_MAX_LIMBS || v_limbs > MPDIV_MAX_LIMBS)
+    return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "at most %d digits per operand", MPDIV_MAX_LIMBS);
+  cudaSetDevice(ctx->device);
+  UniformLaunch L{};
+  L.n = n_items;
+  L.un = u_limbs;
+  L.vn = v_limbs;
+  L.kcut = -1;
+  PreparedLaunch P;
+  const int rc = mpdiv_prepare_uniform(ctx, L, &P);
+  if (rc) return rc;
+  return P.retry_grid > 0 ? 2 : 1;
+}
+
 // ------------------------------------------------------------------ ragged (persistent) batch
 // Cost estimate used to order the queue (largest first): limb products of the
 // quotient and remainder products plus the Newton refinement, from the
