@@ -478,7 +478,8 @@ def other_configs_summary(mp, ctx, dev, stream, args):
     loads = {}
     for k, x in sv.items():
         d = {"div_s": _sig(x["sustained_div_per_s"]), "p50_ms": _sig(x["p50_ms"], 3), "p99_ms": _sig(x["p99_ms"], 3),
-             "ok": x["ok"], "batch": _sig(x["mean_batch"], 3), "clk": _clk(x["clocks"])}
+             "ok": x["ok"], "batch": _sig(x["mean_batch"], 3),
+             "p99_phase_ms": {k2: _sig(v2, 3) for k2, v2 in x["p99_phase_ms"].items()}, "clk": _clk(x["clocks"])}
         if "runs" in x:
             d["p99_ms_runs"] = [_sig(r["p99_ms"], 3) for r in x["runs"]]
             d["ok"] = min(r["ok"] for r in x["runs"])
@@ -625,12 +626,13 @@ def measure_serve(mp, ctx, dev, stream, n_req, max_batch, max_inflight, low_wate
             r = np.zeros(int(R["r_len"].sum()), np.uint32)
             st = np.full(n_req, -9, np.int32)
             lat = np.zeros(n_req, np.int64)
+            ph = np.zeros(3 * n_req, np.int64)
             mp.mpdiv_serve_start(ctx, pool_digits=256 << 20, max_batch=max_batch, max_inflight=max_inflight,
                                  low_water=low_water, batch_step=batch_step, max_wait_us=max_wait_us)
             with ClockSampler(dev.index or 0) as clk:
                 t0 = time.perf_counter()
                 rej = mp.mpdiv_serve_replay(ctx, arr, R["u_flat"], uo, ul, R["v_flat"], vo, vl, q, qo, ul.copy(), r,
-                                            ro, vl.copy(), st, lat)
+                                            ro, vl.copy(), st, lat, ph)
                 wall = time.perf_counter() - t0
             completed, launches, batched = mp.mpdiv_serve_stats(ctx)
             mp.mpdiv_serve_stop(ctx)
@@ -640,6 +642,8 @@ def measure_serve(mp, ctx, dev, stream, n_req, max_batch, max_inflight, low_wate
                 "p50_ms": float(np.percentile(lat, 50)) / 1e6, "p99_ms": float(np.percentile(lat, 99)) / 1e6,
                 "max_ms": float(lat.max()) / 1e6, "ok": int((st == 0).sum()), "launches": launches,
                 "mean_batch": batched / max(1, launches), "busy_retries": rej, "wall_s": wall,
+                "p99_phase_ms": {k: float(np.percentile(ph[j::3], 99)) / 1e6
+                                 for j, k in enumerate(("submit", "queue", "run"))},
                 "clocks": clk.summary()})
         out = dict(runs[0])
         if len(runs) > 1:

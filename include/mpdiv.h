@@ -244,11 +244,12 @@ int mpdiv_mul_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, const ui
                     int64_t stride, uint32_t *out, int64_t out_stride, void *stream);
 
 /* ---------------------------------------------------------------- serving
- * Continuous batching: a host scheduler thread admits submitted requests into
- * device-resident operand pools, launches batches of admitted requests as
- * slots free up, with several batches in flight on separate streams, and
- * publishes results. Requests that arrive while batches run join the next
- * launch. Admission is by footprint: a request's footprint class is the size
+ * Continuous batching: submitted requests are copied into a pinned input ring
+ * that the GPU reads directly (device-mapped host memory); a host scheduler
+ * thread launches batches of them as slots free up, with several batches in
+ * flight on separate streams; the kernels write the results into a pinned,
+ * device-mapped output ring, and each batch's completion publishes them.
+ * Requests that arrive while batches run join the next launch. Admission is by footprint: a request's footprint class is the size
  * class of its dividend (class 0: at most 1024 digits, 1: 2048, 2: 4096,
  * 3: 8192, 4: more), which sets the shared memory and block shape its
  * division needs; each class has its own queue, and a batch holds requests of
@@ -256,7 +257,8 @@ int mpdiv_mul_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, const ui
  * ones. Batches of different classes run at once. */
 #define MPDIV_SERVE_CLASSES 5
 typedef struct mpdiv_serve_config {
-  int64_t pool_digits;  /* digits of device operand/result pool (0: 64 Mi digits) */
+  int64_t pool_digits;  /* digits of the pinned, device-mapped operand and result rings, half each
+                           (0: 64 Mi digits) */
   int32_t max_batch;    /* most requests per batch (0: 4096) */
   int32_t max_inflight; /* batches in flight at once, each on its own stream (0: 32) */
   int32_t max_pending;  /* submitted-but-unfinished requests before EBUSY (0: 1<<20) */
@@ -265,7 +267,7 @@ typedef struct mpdiv_serve_config {
                            they gather into larger batches (0: 2048) */
   int32_t max_wait_us;  /* longest a queued request waits for its batch to grow (0: 2000) */
   int32_t batch_step;   /* below low_water, a class's queued requests launch once there are this
-                           many per batch of that class in flight (0: 8) */
+                           many per batch of that class in flight (0: 16) */
 } mpdiv_serve_config;
 
 /* Start the server on ctx (cfg may be NULL). MPDIV_ESTATE if one is running.
@@ -320,12 +322,16 @@ int mpdiv_debug_serve_fail_launch(mpdiv_ctx *ctx, int64_t launch_index);
  * latency_ns[i] is the time from that scheduled arrival until its result was
  * pollable. Results go to host arrays q + q_off[i] (q_len[i] digits) and
  * r + r_off[i] (r_len[i] digits); status[i] per item (-1 if never admitted).
- * *rejected (may be NULL) counts MPDIV_EBUSY retries. Synchronous. */
+ * *rejected (may be NULL) counts MPDIV_EBUSY retries. phase_ns (may be NULL;
+ * 3 n entries) splits each latency into the submitter's delay past the
+ * scheduled arrival, the wait in the queue until its batch launched, and the
+ * time from launch until the result was pollable (-1 for a request that never
+ * completed). Synchronous. */
 int mpdiv_serve_replay(mpdiv_ctx *ctx, int64_t n, const int64_t *arrival_ns, const uint32_t *u,
                        const int64_t *u_off, const int32_t *u_len, const uint32_t *v, const int64_t *v_off,
                        const int32_t *v_len, uint32_t *q, const int64_t *q_off, const int32_t *q_len, uint32_t *r,
                        const int64_t *r_off, const int32_t *r_len, int32_t *status, int64_t *latency_ns,
-                       int64_t *rejected);
+                       int64_t *rejected, int64_t *phase_ns);
 
 /* ---------------------------------------------------------------- allocation-free form
  * The paper has no counterpart to this entry point; it exists for callers that

@@ -125,7 +125,7 @@ _SIGS = {
     "mpdiv_batch_ragged_noalloc": (ctypes.c_int, [_I64] + [_P] * 15),
     "mpdiv_serve_replay": (
         ctypes.c_int,
-        [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_I64)],
+        [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_I64), _P],
     ),
 }
 
@@ -388,14 +388,18 @@ def mpdiv_debug_serve_fail_launch(ctx, launch_index: int) -> None:
 
 
 def mpdiv_serve_replay(ctx, arrival_ns, u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r, r_off, r_len,
-                       status, latency_ns) -> int:
-    """Open-loop replay with host numpy arrays (see include/mpdiv.h). Returns EBUSY retries."""
+                       status, latency_ns, phase_ns=None) -> int:
+    """Open-loop replay with host numpy arrays (see include/mpdiv.h). Returns EBUSY retries.
+    phase_ns, if given, is an int64 array of 3 entries per request (submit delay, queue wait, run)."""
     import numpy as np
 
     arrs = [arrival_ns, u, u_off, u_len, v, v_off, v_len, q, q_off, q_len, r, r_off, r_len, status, latency_ns]
-    for a in arrs:
+    for a in arrs + ([] if phase_ns is None else [phase_ns]):
         if not (isinstance(a, np.ndarray) and a.flags.c_contiguous):
             raise ValueError("replay arrays must be contiguous numpy arrays")
+    if phase_ns is not None and (phase_ns.dtype != np.int64 or phase_ns.size < 3 * len(arrival_ns)):
+        raise ValueError("phase_ns must be an int64 array of 3 entries per request")
     rej = _I64()
-    _check(ctx, lib().mpdiv_serve_replay(ctx, len(arrival_ns), *[a.ctypes.data for a in arrs], ctypes.byref(rej)))
+    _check(ctx, lib().mpdiv_serve_replay(ctx, len(arrival_ns), *[a.ctypes.data for a in arrs], ctypes.byref(rej),
+                                         None if phase_ns is None else phase_ns.ctypes.data))
     return rej.value

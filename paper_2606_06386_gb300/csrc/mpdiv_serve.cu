@@ -5,20 +5,23 @@
 // classes whose shared-memory plan and block shape the launches are tuned
 // for), and a batch holds requests of one class only, so that a large request
 // never sets the block shape and shared memory of a batch of small ones.
-// Operands travel through two pinned host rings mirrored on the device: an
-// input ring (u and v of every request, in arrival order) and an output ring
-// (q and r of every launched request). mpdiv_serve_submit reserves the
-// request's digits at the tail of the input ring and copies its operands there
-// itself, outside the server lock. A scheduler thread turns the oldest ready
-// requests of a class into a batch: the run of the input ring from its first
-// request to its last (one host-to-device copy on the server's copy stream; the
-// run may hold requests of other classes and requests still being copied in,
-// see copy_stream), per-item
-// offsets and a most-expensive-first order (one more copy), one plain launch
-// over the batch with the class's tuned shape (or, with
+// Operands and results stay in two pinned, device-mapped host rings: an input
+// ring (u and v of every request, in arrival order) and an output ring (q and
+// r of every launched request). The division kernels read the operands from
+// the input ring and write the results to the output ring through the rings'
+// device addresses (host memory reached over the CPU-GPU link), and a batch's
+// offsets, lengths, order and statuses sit in pinned, device-mapped memory of
+// its slot as well: a batch costs one kernel launch (two with the plain
+// kernel's retry pass) and one host function, with no copy calls.
+// mpdiv_serve_submit reserves the request's digits at the tail of the input
+// ring and copies its operands there itself, outside the server lock. A
+// scheduler thread turns the oldest ready requests of a class into a batch
+// (requests whose submitters are still copying are left queued, in order):
+// one plain launch over the batch with the class's tuned shape (or, with
 // MPDIV_FLAG_PERSISTENT_QUEUE, one launch of the self-splitting persistent
-// kernel), and one device-to-host copy of the batch's results, all on the
-// batch's own stream; batches of different classes overlap on the GPU.
+// kernel) on the batch's own stream, followed by a host function that
+// publishes the batch's results to the pollers and frees its slot; batches of
+// different classes overlap on the GPU.
 // Up to max_inflight batches run at once. The class whose oldest ready request
 // is oldest goes first. While fewer than low_water requests are on the GPU,
 // the queued requests of a class launch as soon as there are at least
@@ -51,7 +54,7 @@ namespace {
 
 // Requests a launch needs per batch already in flight while the GPU is below
 // its low-water mark (see the header comment), unless configured.
-constexpr int kBatchStep = 8;
+constexpr int kBatchStep = 16;
 
 // Footprint classes: the dividend's size class (mp::class_of).
 constexpr int kClasses = MPDIV_SERVE_CLASSES;
@@ -61,6 +64,22 @@ using Clock = std::chrono::steady_clock;
 int64_t now_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now().time_since_epoch()).count();
 }
+
+// A test-and-test-and-set lock for the short critical sections that
+// submitters share with the scheduler and the completions (a ring allocation,
+// a list append): under many submitting threads it hands over without the
+// kernel calls of a contended mutex. It yields after a while so that a
+// preempted holder can run.
+struct SpinLock {
+  std::atomic<bool> held{false};
+  void lock() {
+    int spins = 0;
+    while (held.exchange(true, std::memory_order_acquire))
+      while (held.load(std::memory_order_relaxed))
+        if (++spins % 64 == 0) std::this_thread::yield();
+  }
+  void unlock() { held.store(false, std::memory_order_release); }
+};
 
 enum ReqState { RQ_QUEUED = 0, RQ_RUNNING = 1, RQ_DONE = 2 };
 
@@ -83,78 +102,113 @@ struct Request {
   std::atomic<int> ready{0};      // operands copied into the ring
   int32_t status = 0;
   std::atomic<int> state{RQ_QUEUED};  // RQ_DONE is published with release order
-  int64_t t_submit = 0, t_done = 0;
+  int64_t t_submit = 0, t_launch = 0, t_done = 0;
 };
 
 }  // namespace
 
+// Threads and what they own:
+//  - submitters (mpdiv_serve_submit): take a ticket and input-ring space and
+//    append the request to `arrivals`, under sub_mu only;
+//  - the scheduler thread (run): moves arrivals into the per-class queues,
+//    which it alone touches, forms batches, launches them and reclaims the
+//    slots their host functions have marked done;
+//  - host functions (slot_done), one per batch: release the batch's input
+//    space (sub_mu) and publish its requests as done;
+//  - pollers (mpdiv_serve_poll): claim a done request without a lock, wait
+//    for one under mu / cv_done, and release a batch's output space (out_mu).
+// A request is published done (state RQ_DONE, release order) after its last
+// use by the server: from then on it belongs to the poller that claims it.
 struct MpServer {
   mpdiv_ctx* ctx = nullptr;
   mpdiv_serve_config cfg{};
-  uint32_t *d_in = nullptr, *h_in = nullptr, *d_out = nullptr, *h_out = nullptr;
-  mp_serve::Ring in_ring, out_ring;
+  // pinned, device-mapped rings: host addresses and the kernels' device addresses
+  uint32_t *h_in = nullptr, *h_out = nullptr, *dv_in = nullptr, *dv_out = nullptr;
+  SpinLock sub_mu;                 // in_ring, next_ticket, arrivals, ticket slots taken
+  mp_serve::Ring in_ring;
+  std::vector<Request*> arrivals;  // submitted, not yet in a queue
+  uint64_t next_ticket = 1;
+  SpinLock out_mu;  // out_ring
+  mp_serve::Ring out_ring;
+  // waits: pollers on cv_done, the scheduler on cv_sched (both under mu)
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
-  std::deque<Request*> queue[kClasses];
-  int64_t queued = 0;  // requests in all queues
+  // the scheduler waits: sched_sleeping in any wait, sched_idle in the long
+  // wait of an empty server (a submitter wakes it only from that one)
+  std::atomic<bool> sched_sleeping{false}, sched_idle{false};
   // request of ticket t at by_ticket[t & ticket_mask], owned there until it is
-  // polled (a poller claims it by swapping the slot to null, without the lock)
+  // polled (a poller claims it by swapping the slot to null)
   std::unique_ptr<std::atomic<Request*>[]> by_ticket;
   uint64_t ticket_mask = 0;
-  uint64_t next_ticket = 1;
-  int64_t pending = 0, inflight_items = 0;
-  bool stopping = false, quit = false;
-  int sched_error = 0;
-  int64_t completed = 0, launches = 0, batched_items = 0;
-  int64_t class_launches[kClasses] = {}, class_items[kClasses] = {};  // by the batch's largest dividend
-  int64_t fail_launch = -1;  // test hook: the launch with this index fails on the host (-1: none)
+  std::atomic<int64_t> pending{0};  // submitted, not yet done
+  std::atomic<bool> stopping{false}, quit{false};
+  std::atomic<int> sched_error{0};
+  std::atomic<int64_t> completed{0}, launches{0}, batched_items{0};
+  std::atomic<int64_t> class_launches[kClasses] = {}, class_items[kClasses] = {};  // by the batch's largest dividend
+  std::atomic<int64_t> fail_launch{-1};  // test hook: the launch with this index fails on the host (-1: none)
   std::thread th;
-  // operand copies of every batch, in admission order: a batch's copy may
-  // span ring space of requests still being written by their submitters
-  // (skipped, to be taken by a later batch), and the later batch's own copy of
-  // that space must land after this stale one
-  cudaStream_t copy_stream = nullptr;
+  // scheduler-only state
+  std::deque<Request*> queue[kClasses];
+  int64_t queued = 0;          // requests in all queues
+  int64_t inflight_items = 0;  // requests of the batches in flight
+  std::vector<Request*> incoming, skipped;
   struct Slot {
     MpServer* server = nullptr;
     cudaStream_t stream = nullptr;
-    cudaEvent_t ev = nullptr;
-    cudaEvent_t copied = nullptr;  // the batch's operand copy is done
-    // set by a host function the slot's stream runs after the batch's results
-    // are on the host, so that the scheduler reads a flag per slot instead of
-    // querying an event
-    std::atomic<int> done{0};
-    uint32_t *h_meta = nullptr, *d_meta = nullptr;  // offsets, lengths, order, heads, status
-    bool busy = false;
-    int cls = 0;  // footprint class of the batch in flight
-    int64_t out_off = -1, out_seq = -1;
-    std::vector<Request*> reqs;
+    // offsets, lengths, order and statuses of the batch: pinned and
+    // device-mapped (host and device addresses); the queue heads of the queue
+    // forms in device memory
+    uint32_t *h_meta = nullptr, *dv_meta = nullptr;
+    int32_t* d_heads = nullptr;
+    bool busy = false;           // scheduler-only
+    std::atomic<int> done{0};    // set by the batch's host function
+    int cls = 0;                 // footprint class of the batch in flight
+    std::vector<Request*> reqs;  // read by the host function while busy
   };
   std::vector<Slot> slots;
   int64_t meta_words = 0;
 
-  std::vector<Request*> skipped;  // scheduler scratch: requests a batch passed over
-
   void run();
   bool launch(Slot& s);
   static void CUDART_CB slot_done(void* p);
-  void fail(Request* r, int64_t t);
+  void publish(Request* r, int32_t status, bool failed, int64_t t);
+  void wake_pollers();
+  void wake_scheduler(const std::atomic<bool>& waiting);
 };
 
-// Mark a request failed (no results; status MPDIV_ST_INTERNAL) and release its
-// input-ring space. Called with the lock held.
-void MpServer::fail(Request* r, int64_t t) {
-  r->out.reset();
-  r->out_off = -1;
-  r->failed = true;
-  r->status = MPDIV_ST_INTERNAL;
+// Publish a request as done; the server does not touch it afterwards.
+void MpServer::publish(Request* r, int32_t status, bool failed, int64_t t) {
+  if (failed) {
+    r->out.reset();
+    r->out_off = -1;
+    r->failed = true;
+  }
+  r->status = status;
   r->t_done = t;
   r->state.store(RQ_DONE, std::memory_order_release);
-  in_ring.release(r->in_seq);
 }
 
-// metadata layout of a slot for n items: int64 offsets (u, v, q, r) as digit
-// pairs, int32 lengths (u, v, q, r), order, queue heads, status
-static int64_t meta_words_for(int64_t n) { return 8 * n + 5 * n + 8 + n + 8; }
+// Wake every poller waiting on cv_done: taking mu orders this after any
+// poller's check of its request's state, so no wakeup is lost.
+void MpServer::wake_pollers() {
+  { std::lock_guard<std::mutex> g(mu); }
+  cv_done.notify_all();
+}
+
+// Wake the scheduler if it is in the wait that `waiting` flags (completions:
+// any wait; submits: the idle wait only, as a busy scheduler looks at its
+// arrivals every few microseconds by itself and a wakeup per request would
+// cost every submitter a system call).
+void MpServer::wake_scheduler(const std::atomic<bool>& waiting) {
+  if (waiting.load(std::memory_order_acquire)) {
+    std::lock_guard<std::mutex> g(mu);
+    cv_sched.notify_one();
+  }
+}
+
+// metadata layout of a slot for n items (32-bit words): int64 offsets (u, v,
+// q, r) as digit pairs, int32 lengths (u, v, q, r), order, status
+static int64_t meta_words_for(int64_t n) { return 8 * n + 4 * n + n + n; }
 
 bool MpServer::launch(Slot& s) {
   MpdivRange nvtx_range("mpdiv.serve.batch");
@@ -163,24 +217,16 @@ bool MpServer::launch(Slot& s) {
   int64_t* h_off = reinterpret_cast<int64_t*>(H);
   int32_t* h_len = reinterpret_cast<int32_t*>(H + 8 * n);
   int32_t* order = h_len + 4 * n;
-  int32_t* heads = order + n;
-  const int64_t status_w = 13 * n + 8;  // status after the heads
   std::vector<double> cost(n);
-  int64_t pq = s.out_off;
-  auto ob = std::make_shared<OutBatch>();
-  ob->seq = s.out_seq;
-  ob->remaining = (int)n;
+  std::vector<int32_t> ulh(n), vlh(n);
   for (int64_t i = 0; i < n; i++) {
-    Request* r = s.reqs[i];
-    r->out_off = pq;
-    r->out = ob;
+    const Request* r = s.reqs[i];
     h_off[i] = r->in_off;
     h_off[n + i] = r->in_off + r->u_len;
-    h_off[2 * n + i] = pq;
-    h_off[3 * n + i] = pq + r->q_len;
-    pq += r->q_len + r->r_len;
-    h_len[i] = r->u_len;
-    h_len[n + i] = r->v_len;
+    h_off[2 * n + i] = r->out_off;
+    h_off[3 * n + i] = r->out_off + r->q_len;
+    h_len[i] = ulh[i] = r->u_len;
+    h_len[n + i] = vlh[i] = r->v_len;
     h_len[2 * n + i] = r->q_len;
     h_len[3 * n + i] = r->r_len;
     const double a = std::max(1, r->u_len - r->v_len + 1);
@@ -195,101 +241,73 @@ bool MpServer::launch(Slot& s) {
     if (form == RF_SPLIT && s.reqs[a]->u_len != s.reqs[b]->u_len) return s.reqs[a]->u_len > s.reqs[b]->u_len;
     return cost[a] > cost[b];
   });
-  std::memset(heads, 0, 8 * sizeof(int32_t));
-  // operands: one contiguous run of the input ring
-  // operands: one run of the input ring, from the first request of the batch
-  // to the end of its last (a class's requests are in ring order), on the copy
-  // stream
-  const int64_t in_lo = s.reqs.front()->in_off;
-  const int64_t in_hi = s.reqs.back()->in_off + s.reqs.back()->u_len + s.reqs.back()->v_len;
-  cudaError_t e = cudaMemcpyAsync(d_in + in_lo, h_in + in_lo, 4 * (size_t)(in_hi - in_lo), cudaMemcpyHostToDevice,
-                                  copy_stream);
-  if (e == cudaSuccess) e = cudaEventRecord(s.copied, copy_stream);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s.stream, s.copied, 0);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_meta, H, 4 * (size_t)status_w, cudaMemcpyHostToDevice, s.stream);
-  const int64_t* d_off = reinterpret_cast<const int64_t*>(s.d_meta);
-  const int32_t* d_len = reinterpret_cast<const int32_t*>(s.d_meta + 8 * n);
-  int32_t* d_status = reinterpret_cast<int32_t*>(s.d_meta + status_w);
-  int rc = (e == cudaSuccess) ? MPDIV_OK : MPDIV_ECUDA;
-  if (rc == MPDIV_OK) {
-    // one launch over the batch in the context's ragged form
-    std::vector<int32_t> ulh(n), vlh(n);
-    for (int64_t i = 0; i < n; i++) {
-      ulh[i] = s.reqs[i]->u_len;
-      vlh[i] = s.reqs[i]->v_len;
-    }
-    RaggedLaunch L{};
-    L.u = d_in;
-    L.u_off = d_off;
-    L.u_len = d_len;
-    L.v = d_in;
-    L.v_off = d_off + n;
-    L.v_len = d_len + n;
-    L.q = d_out;
-    L.q_off = d_off + 2 * n;
-    L.q_len = d_len + 2 * n;
-    L.r = d_out;
-    L.r_off = d_off + 3 * n;
-    L.r_len = d_len + 3 * n;
-    L.status = d_status;
-    L.u_len_host = ulh.data();
-    L.v_len_host = vlh.data();
-    L.order = d_len + 4 * n;
-    L.order_host = order;
-    L.head = const_cast<int32_t*>(d_len + 5 * n);
-    L.n = n;
-    L.use_graph = false;
-    L.form = form;
-    rc = mpdiv_launch_ragged(ctx, L, s.stream);
-  }
-  if (rc == MPDIV_OK)
-    e = cudaMemcpyAsync(h_out + s.out_off, d_out + s.out_off, 4 * (size_t)(pq - s.out_off), cudaMemcpyDeviceToHost,
-                        s.stream);
-  if (rc == MPDIV_OK && e == cudaSuccess)
-    e = cudaMemcpyAsync(H + status_w, d_status, 4 * (size_t)n, cudaMemcpyDeviceToHost, s.stream);
-  if (rc == MPDIV_OK && e == cudaSuccess) e = cudaLaunchHostFunc(s.stream, slot_done, &s);
-  return rc == MPDIV_OK && e == cudaSuccess;
+  // the kernels read the metadata and the operands, and write the results
+  // and statuses, through the device addresses of the pinned buffers
+  const int64_t* d_off = reinterpret_cast<const int64_t*>(s.dv_meta);
+  const int32_t* d_len = reinterpret_cast<const int32_t*>(s.dv_meta + 8 * n);
+  RaggedLaunch L{};
+  L.u = dv_in;
+  L.u_off = d_off;
+  L.u_len = d_len;
+  L.v = dv_in;
+  L.v_off = d_off + n;
+  L.v_len = d_len + n;
+  L.q = dv_out;
+  L.q_off = d_off + 2 * n;
+  L.q_len = d_len + 2 * n;
+  L.r = dv_out;
+  L.r_off = d_off + 3 * n;
+  L.r_len = d_len + 3 * n;
+  L.status = const_cast<int32_t*>(d_len + 5 * n);
+  L.u_len_host = ulh.data();
+  L.v_len_host = vlh.data();
+  L.order = d_len + 4 * n;
+  L.order_host = order;
+  L.head = s.d_heads;
+  L.n = n;
+  L.use_graph = false;
+  L.form = form;
+  // the CPU's stores to the rings and the metadata come before the launch
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  const int rc = mpdiv_launch_ragged(ctx, L, s.stream);
+  return rc == MPDIV_OK && cudaLaunchHostFunc(s.stream, slot_done, &s) == cudaSuccess;
 }
 
-// Host function run by a slot's stream once its batch's results and statuses
-// are on the host: flags the slot and wakes the scheduler (no CUDA call).
+// Host function run by a slot's stream once its batch's kernels are done (the
+// results and statuses are in the pinned rings): release the batch's input
+// space, publish its requests, and hand the slot back to the scheduler. No
+// CUDA call here.
 void CUDART_CB MpServer::slot_done(void* p) {
   Slot* s = static_cast<Slot*>(p);
+  MpServer* S = s->server;
+  const int64_t t = now_ns();
+  const int64_t n = (int64_t)s->reqs.size();
+  const int32_t* st = reinterpret_cast<const int32_t*>(s->h_meta + 8 * n + 5 * n);
+  {
+    std::lock_guard<SpinLock> g(S->sub_mu);
+    for (Request* r : s->reqs) S->in_ring.release(r->in_seq);
+  }
+  S->completed.fetch_add(n, std::memory_order_relaxed);
+  S->pending.fetch_sub(n, std::memory_order_relaxed);
+  for (int64_t i = 0; i < n; i++) S->publish(s->reqs[i], st[i], false, t);
   s->done.store(1, std::memory_order_release);
-  s->server->cv_sched.notify_one();
+  S->wake_pollers();
+  S->wake_scheduler(S->sched_sleeping);
 }
 
 void MpServer::run() {
   cudaSetDevice(ctx->device);
-  std::vector<Slot*> finished;
   while (true) {
-    // ---- completions: results stay in the pinned output ring until polled
-    finished.clear();
-    for (auto& s : slots)
-      if (s.busy && s.done.load(std::memory_order_acquire)) finished.push_back(&s);
-    std::unique_lock<std::mutex> lk(mu);
-    const int64_t t = now_ns();
-    for (Slot* s : finished) {
-      const int64_t n = (int64_t)s->reqs.size();
-      const int32_t* st = reinterpret_cast<const int32_t*>(s->h_meta + 13 * n + 8);
-      for (int64_t i = 0; i < n; i++) {
-        Request* r = s->reqs[i];
-        r->status = st[i];
-        r->t_done = t;
-        r->state.store(RQ_DONE, std::memory_order_release);
-        in_ring.release(r->in_seq);
-      }
-      completed += n;
-      pending -= n;
-      inflight_items -= n;
-      s->reqs.clear();
-      s->done.store(0, std::memory_order_relaxed);
-      s->busy = false;
-    }
-    if (!finished.empty()) cv_done.notify_all();
+    // ---- finished batches hand their slots back
     int busy = 0, busy_c[kClasses] = {};
     Slot* free_slot = nullptr;
     for (auto& s : slots) {
+      if (s.busy && s.done.load(std::memory_order_acquire)) {
+        inflight_items -= (int64_t)s.reqs.size();
+        s.reqs.clear();
+        s.done.store(0, std::memory_order_relaxed);
+        s.busy = false;
+      }
       if (s.busy) {
         busy++;
         busy_c[s.cls]++;
@@ -297,17 +315,27 @@ void MpServer::run() {
         free_slot = &s;
       }
     }
+    // ---- new requests into their class queues, in ticket order
+    {
+      std::lock_guard<SpinLock> g(sub_mu);
+      incoming.swap(arrivals);
+    }
+    for (Request* r : incoming) queue[r->cls].push_back(r);
+    queued += (int64_t)incoming.size();
+    incoming.clear();
+    const bool stop_now = quit.load(std::memory_order_acquire);
     // ---- admission: the class whose oldest ready request is oldest among
     // those whose admission condition holds
+    const int64_t t = now_ns();
     int adm = -1;
-    if (free_slot && sched_error == 0) {
+    if (free_slot && sched_error.load(std::memory_order_relaxed) == 0) {
       int64_t oldest = INT64_MAX;
       for (int c = 0; c < kClasses; c++) {
         if (queue[c].empty() || !queue[c].front()->ready.load(std::memory_order_acquire)) continue;
         const Request* f = queue[c].front();
         const int64_t waited_us = (t - f->t_submit) / 1000;
         const bool go = (inflight_items < cfg.low_water && (int64_t)queue[c].size() >= (int64_t)cfg.batch_step * busy_c[c]) ||
-                        (int64_t)queue[c].size() >= cfg.max_batch || waited_us >= cfg.max_wait_us || quit;
+                        (int64_t)queue[c].size() >= cfg.max_batch || waited_us >= cfg.max_wait_us || stop_now;
         if (go && f->t_submit < oldest) {
           oldest = f->t_submit;
           adm = c;
@@ -315,17 +343,19 @@ void MpServer::run() {
       }
     }
     if (adm >= 0) {
-      // the oldest ready requests of the class, in ring order and short of the
-      // ring's wrap, within the output ring; requests whose submitters are
-      // still copying their operands are skipped and stay queued in order
+      // the oldest ready requests of the class that fit the output ring;
+      // requests whose submitters are still copying their operands are
+      // skipped and stay queued in order
       std::deque<Request*>& qc = queue[adm];
       std::vector<Request*>& b = free_slot->reqs;
-      int64_t out_need = 0;
-      const int64_t out_room = out_ring.cap - out_ring.used - 4;
+      int64_t out_need = 0, out_room;
+      {
+        std::lock_guard<SpinLock> g(out_mu);
+        out_room = out_ring.cap - out_ring.used - 4;
+      }
       skipped.clear();
       while (!qc.empty() && (int64_t)b.size() < cfg.max_batch) {
         Request* r = qc.front();
-        if (!b.empty() && r->in_off < b.back()->in_off) break;  // the ring wrapped
         if (!r->ready.load(std::memory_order_acquire)) {
           skipped.push_back(r);
           qc.pop_front();
@@ -339,58 +369,95 @@ void MpServer::run() {
       }
       for (auto it = skipped.rbegin(); it != skipped.rend(); ++it) qc.push_front(*it);
       queued -= (int64_t)b.size();
-      int64_t oseq = -1;
-      const int64_t off = b.empty() ? -1 : out_ring.alloc(out_need, &oseq);
+      int64_t oseq = -1, off = -1;
+      if (!b.empty()) {
+        std::lock_guard<SpinLock> g(out_mu);
+        off = out_ring.alloc(out_need, &oseq);
+      }
       if (off < 0) {
-        // put the batch back in ring order among the skipped requests
+        // put the batch back in ticket order among the skipped requests
         for (auto it = b.rbegin(); it != b.rend(); ++it) qc.push_front(*it);
         std::stable_sort(qc.begin(), qc.begin() + (ptrdiff_t)(b.size() + skipped.size()),
-                         [](const Request* x, const Request* y) { return x->in_off < y->in_off; });
+                         [](const Request* x, const Request* y) { return x->ticket < y->ticket; });
         queued += (int64_t)b.size();
         b.clear();
       } else {
-        free_slot->out_off = off;
-        free_slot->out_seq = oseq;
         free_slot->busy = true;
         free_slot->cls = adm;
+        auto ob = std::make_shared<OutBatch>();
+        ob->seq = oseq;
+        ob->remaining = (int)b.size();
+        int64_t pq = off;
         int bcls = 0;
+        const int64_t tl = now_ns();
         for (Request* r : b) {
+          r->out_off = pq;
+          r->out = ob;
+          pq += r->q_len + r->r_len;
+          r->t_launch = tl;
           r->state.store(RQ_RUNNING, std::memory_order_relaxed);
           bcls = std::max(bcls, mp::class_of(r->u_len));
         }
         const int64_t nb = (int64_t)b.size();
-        const bool inject = launches == fail_launch;
+        const int64_t li = launches.fetch_add(1, std::memory_order_relaxed);
         inflight_items += nb;
-        launches++;
-        batched_items += nb;
-        class_launches[bcls]++;
-        class_items[bcls] += nb;
-        lk.unlock();
-        const bool ok = !inject && launch(*free_slot);
-        lk.lock();
-        if (!ok) {  // fail these requests and every queued one, and refuse further work
-          sched_error = MPDIV_ECUDA;
+        batched_items.fetch_add(nb, std::memory_order_relaxed);
+        class_launches[bcls].fetch_add(1, std::memory_order_relaxed);
+        class_items[bcls].fetch_add(nb, std::memory_order_relaxed);
+        // the slot's requests are the host function's to publish once a
+        // launch enqueues it
+        const bool ok = li != fail_launch.load(std::memory_order_relaxed) && launch(*free_slot);
+        if (!ok) {
+          // fail these requests and every queued one, and refuse further work
+          sched_error.store(MPDIV_ECUDA, std::memory_order_release);
+          {
+            std::lock_guard<SpinLock> g(out_mu);
+            out_ring.release(oseq);
+          }
+          for (auto& qq : queue) b.insert(b.end(), qq.begin(), qq.end());
+          {
+            std::lock_guard<SpinLock> g(sub_mu);
+            b.insert(b.end(), arrivals.begin(), arrivals.end());
+            arrivals.clear();
+            for (Request* r : b) in_ring.release(r->in_seq);
+          }
           const int64_t tf = now_ns();
-          for (Request* r : b) fail(r, tf);
-          out_ring.release(oseq);
-          pending -= nb;
+          const int64_t nf = (int64_t)b.size();
+          pending.fetch_sub(nf, std::memory_order_relaxed);
           inflight_items -= nb;
+          for (Request* r : b) publish(r, MPDIV_ST_INTERNAL, true, tf);
           b.clear();
           free_slot->busy = false;
-          for (auto& qq : queue) {
-            for (Request* r : qq) fail(r, tf);
-            pending -= (int64_t)qq.size();
-            qq.clear();
-          }
+          for (auto& qq : queue) qq.clear();
           queued = 0;
-          cv_done.notify_all();
+          wake_pollers();
         }
         continue;
       }
     }
-    if (quit && busy == 0 && (queued == 0 || sched_error)) break;
-    cv_sched.wait_for(lk, (busy > 0 || queued > 0) ? std::chrono::microseconds(20)
-                                                  : std::chrono::microseconds(5000));
+    if (stop_now && busy == 0) {
+      std::lock_guard<SpinLock> g(sub_mu);
+      if ((queued == 0 && arrivals.empty()) || sched_error.load(std::memory_order_relaxed)) break;
+    }
+    // ---- wait: every 20 us while requests are queued or batches run (their
+    // host functions also wake it), else until a submitter wakes it
+    std::unique_lock<std::mutex> lk(mu);
+    const bool long_wait = queued == 0 && busy == 0;
+    sched_sleeping.store(true, std::memory_order_seq_cst);
+    sched_idle.store(long_wait, std::memory_order_seq_cst);
+    bool empty;
+    {
+      std::lock_guard<SpinLock> g(sub_mu);
+      empty = arrivals.empty();
+    }
+    if (empty) {
+      if (long_wait)
+        cv_sched.wait_for(lk, std::chrono::milliseconds(5));
+      else
+        cv_sched.wait_for(lk, std::chrono::microseconds(20));
+    }
+    sched_idle.store(false, std::memory_order_relaxed);
+    sched_sleeping.store(false, std::memory_order_relaxed);
   }
 }
 
@@ -398,12 +465,7 @@ void MpServer::run() {
 extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) {
   if (!ctx) return MPDIV_EINVAL;
   if (ctx->server) {
-    bool stopped;
-    {
-      std::lock_guard<std::mutex> g(ctx->server->mu);
-      stopped = ctx->server->stopping;
-    }
-    if (!stopped) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server already running");
+    if (!ctx->server->stopping.load()) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server already running");
     mpdiv_serve_shutdown(ctx);  // a stopped server is released: its unpolled results are dropped
   }
   cudaSetDevice(ctx->device);
@@ -428,21 +490,30 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
     for (uint64_t i = 0; i < cap; i++) S->by_ticket[i].store(nullptr, std::memory_order_relaxed);
     S->ticket_mask = cap - 1;
   }
-  int rc = mpdiv_cuda_check(ctx, cudaMalloc(&S->d_in, 4 * (size_t)half), "server input ring");
-  if (!rc) rc = mpdiv_cuda_check(ctx, cudaMalloc(&S->d_out, 4 * (size_t)half), "server output ring");
-  if (!rc) rc = mpdiv_cuda_check(ctx, cudaMallocHost(&S->h_in, 4 * (size_t)half), "server pinned input ring");
-  if (!rc) rc = mpdiv_cuda_check(ctx, cudaMallocHost(&S->h_out, 4 * (size_t)half), "server pinned output ring");
+  // pinned rings mapped into the device's address space: the kernels read
+  // operands and write results there directly
+  const unsigned mapped = cudaHostAllocMapped | cudaHostAllocPortable;
+  int rc = mpdiv_cuda_check(ctx, cudaHostAlloc((void**)&S->h_in, 4 * (size_t)half, mapped), "server pinned input ring");
   if (!rc)
-    rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking), "server copy stream");
+    rc = mpdiv_cuda_check(ctx, cudaHostAlloc((void**)&S->h_out, 4 * (size_t)half, mapped), "server pinned output ring");
+  if (!rc)
+    rc = mpdiv_cuda_check(ctx, cudaHostGetDevicePointer((void**)&S->dv_in, S->h_in, 0),
+                          "device address of the input ring");
+  if (!rc)
+    rc = mpdiv_cuda_check(ctx, cudaHostGetDevicePointer((void**)&S->dv_out, S->h_out, 0),
+                          "device address of the output ring");
   S->slots = std::vector<MpServer::Slot>(S->cfg.max_inflight);
   for (auto& s : S->slots) {
     s.server = S;
     if (rc) break;
     rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking), "server stream");
-    if (!rc) rc = mpdiv_cuda_check(ctx, cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming), "server event");
-    if (!rc) rc = mpdiv_cuda_check(ctx, cudaEventCreateWithFlags(&s.copied, cudaEventDisableTiming), "server event");
-    if (!rc) rc = mpdiv_cuda_check(ctx, cudaMallocHost(&s.h_meta, 4 * (size_t)S->meta_words), "server metadata");
-    if (!rc) rc = mpdiv_cuda_check(ctx, cudaMalloc(&s.d_meta, 4 * (size_t)S->meta_words), "server metadata");
+    if (!rc)
+      rc = mpdiv_cuda_check(ctx, cudaHostAlloc((void**)&s.h_meta, 4 * (size_t)S->meta_words, mapped),
+                            "server metadata");
+    if (!rc)
+      rc = mpdiv_cuda_check(ctx, cudaHostGetDevicePointer((void**)&s.dv_meta, s.h_meta, 0),
+                            "device address of metadata");
+    if (!rc) rc = mpdiv_cuda_check(ctx, cudaMalloc(&s.d_heads, 8 * sizeof(int32_t)), "server queue heads");
   }
   ctx->server = S;
   if (rc) {
@@ -461,50 +532,56 @@ extern "C" int mpdiv_serve_submit(mpdiv_ctx* ctx, const uint32_t* u_host, int32_
   if (u_len < 1 || v_len < 1) return mpdiv_set_error(ctx, MPDIV_EINVAL, "digit counts must be positive");
   if (u_len > MPDIV_MAX_LIMBS || v_len > MPDIV_MAX_LIMBS)
     return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "at most %d digits", MPDIV_MAX_LIMBS);
-  const int cls = mp::class_of(u_len);
   if (2 * (int64_t)(u_len + v_len) + 8 > S->in_ring.cap)
     return mpdiv_set_error(ctx, MPDIV_EBUSY, "request larger than the server's rings");
+  if (S->stopping.load(std::memory_order_acquire)) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server stopping");
+  if (const int e = S->sched_error.load(std::memory_order_acquire))
+    return mpdiv_set_error(ctx, e, "the server stopped after a failed launch");
+  if (S->pending.fetch_add(1, std::memory_order_relaxed) >= S->cfg.max_pending) {
+    S->pending.fetch_sub(1, std::memory_order_relaxed);
+    return MPDIV_EBUSY;
+  }
   auto r = std::make_unique<Request>();
   r->u_len = u_len;
   r->v_len = v_len;
   r->q_len = u_len;  // enough for any quotient
   r->r_len = v_len;
-  r->cls = cls;
+  r->cls = mp::class_of(u_len);
   Request* rp = r.get();
-  bool wake = false;
   {
-    std::lock_guard<std::mutex> g(S->mu);
-    if (S->stopping) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server stopping");
-    if (S->sched_error) return mpdiv_set_error(ctx, S->sched_error, "the server stopped after a failed launch");
-    if (S->pending >= S->cfg.max_pending) return MPDIV_EBUSY;
-    // the ticket's slot still holds an unpolled result from ticket - capacity
-    if (S->by_ticket[S->next_ticket & S->ticket_mask].load(std::memory_order_acquire) != nullptr) return MPDIV_EBUSY;
+    std::lock_guard<SpinLock> g(S->sub_mu);
+    // a failed launch drains the arrivals under this lock after setting the error
+    if (const int e = S->sched_error.load(std::memory_order_acquire)) {
+      S->pending.fetch_sub(1, std::memory_order_relaxed);
+      return mpdiv_set_error(ctx, e, "the server stopped after a failed launch");
+    }
     int64_t seq = -1;
-    const int64_t off = S->in_ring.alloc(u_len + v_len, &seq);
-    if (off < 0) return MPDIV_EBUSY;  // input ring full: retry later
+    // the ticket's slot still holds an unpolled result from ticket - capacity,
+    // or the input ring is full: retry later
+    const bool slot_taken = S->by_ticket[S->next_ticket & S->ticket_mask].load(std::memory_order_acquire) != nullptr;
+    const int64_t off = slot_taken ? -1 : S->in_ring.alloc(u_len + v_len, &seq);
+    if (off < 0) {
+      S->pending.fetch_sub(1, std::memory_order_relaxed);
+      return MPDIV_EBUSY;
+    }
     r->in_off = off;
     r->in_seq = seq;
     r->ticket = S->next_ticket++;
     r->t_submit = now_ns();
     *ticket = r->ticket;
-    // the scheduler re-checks a non-empty queue every few microseconds by
-    // itself; only a request into an empty queue needs to wake it
-    wake = S->queued == 0;
-    S->queue[cls].push_back(rp);
-    S->queued++;
+    S->arrivals.push_back(rp);
     S->by_ticket[rp->ticket & S->ticket_mask].store(r.release(), std::memory_order_release);
-    S->pending++;
   }
   // the operands go straight into the pinned ring; the scheduler waits for `ready`
   std::memcpy(S->h_in + rp->in_off, u_host, 4 * (size_t)u_len);
   std::memcpy(S->h_in + rp->in_off + u_len, v_host, 4 * (size_t)v_len);
   rp->ready.store(1, std::memory_order_release);
-  if (wake) S->cv_sched.notify_one();
+  S->wake_scheduler(S->sched_idle);
   return MPDIV_OK;
 }
 
 static int poll_impl(mpdiv_ctx* ctx, uint64_t ticket, uint32_t* q_host, int32_t q_cap, uint32_t* r_host,
-                     int32_t r_cap, int32_t* status, int64_t timeout_us, int64_t* t_done) {
+                     int32_t r_cap, int32_t* status, int64_t timeout_us, int64_t* times) {
   MpServer* S = ctx->server;
   if (!S) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server not running");
   std::atomic<Request*>& slot = S->by_ticket[ticket & S->ticket_mask];
@@ -515,8 +592,6 @@ static int poll_impl(mpdiv_ctx* ctx, uint64_t ticket, uint32_t* q_host, int32_t 
     std::unique_lock<std::mutex> lk(S->mu);
     const auto until = Clock::now() + std::chrono::microseconds(timeout_us);
     while (r->state.load(std::memory_order_acquire) != RQ_DONE) {
-      if (S->sched_error && r->state.load(std::memory_order_relaxed) == RQ_QUEUED)
-        return mpdiv_set_error(ctx, S->sched_error, "the server stopped after a failed launch");
       if (S->cv_done.wait_until(lk, until) == std::cv_status::timeout &&
           r->state.load(std::memory_order_acquire) != RQ_DONE)
         return MPDIV_ETIMEDOUT;
@@ -548,9 +623,13 @@ static int poll_impl(mpdiv_ctx* ctx, uint64_t ticket, uint32_t* q_host, int32_t 
     for (int i = n; i < r_cap; i++) r_host[i] = 0u;
   }
   if (status) *status = r->status;
-  if (t_done) *t_done = r->t_done;
+  if (times) {  // submitted, launched, done
+    times[0] = r->t_submit;
+    times[1] = r->t_launch;
+    times[2] = r->t_done;
+  }
   if (r->out && r->out->remaining.fetch_sub(1, std::memory_order_acq_rel) == 1) {
-    std::lock_guard<std::mutex> g(S->mu);
+    std::lock_guard<SpinLock> g(S->out_mu);
     S->out_ring.release(r->out->seq);
   }
   if (r->failed) return mpdiv_set_error(ctx, MPDIV_ECUDA, "ticket %llu failed: its batch could not be launched",
@@ -565,12 +644,12 @@ extern "C" int mpdiv_serve_poll(mpdiv_ctx* ctx, uint64_t ticket, uint32_t* q_hos
 }
 
 static void stop_impl(MpServer* S) {
+  S->stopping.store(true, std::memory_order_release);
+  S->quit.store(true, std::memory_order_release);
   {
     std::lock_guard<std::mutex> g(S->mu);
-    S->stopping = true;
-    S->quit = true;
+    S->cv_sched.notify_all();
   }
-  S->cv_sched.notify_all();
   if (S->th.joinable()) S->th.join();
 }
 
@@ -579,20 +658,20 @@ extern "C" int mpdiv_serve_stop(mpdiv_ctx* ctx) {
   MpServer* S = ctx->server;
   if (!S) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server not running");
   stop_impl(S);
-  return S->sched_error ? mpdiv_set_error(ctx, S->sched_error, "a batch failed to launch") : MPDIV_OK;
+  const int e = S->sched_error.load();
+  return e ? mpdiv_set_error(ctx, e, "a batch failed to launch") : MPDIV_OK;
 }
 
 extern "C" int mpdiv_serve_stats(mpdiv_ctx* ctx, int64_t* completed, int64_t* launches, int64_t* batched_items,
                                  int64_t* class_launches, int64_t* class_items) {
   if (!ctx || !ctx->server) return MPDIV_EINVAL;
   MpServer* S = ctx->server;
-  std::lock_guard<std::mutex> g(S->mu);
-  if (completed) *completed = S->completed;
-  if (launches) *launches = S->launches;
-  if (batched_items) *batched_items = S->batched_items;
+  if (completed) *completed = S->completed.load();
+  if (launches) *launches = S->launches.load();
+  if (batched_items) *batched_items = S->batched_items.load();
   for (int c = 0; c < kClasses; c++) {
-    if (class_launches) class_launches[c] = S->class_launches[c];
-    if (class_items) class_items[c] = S->class_items[c];
+    if (class_launches) class_launches[c] = S->class_launches[c].load();
+    if (class_items) class_items[c] = S->class_items[c].load();
   }
   return MPDIV_OK;
 }
@@ -601,8 +680,7 @@ extern "C" int mpdiv_debug_serve_fail_launch(mpdiv_ctx* ctx, int64_t launch_inde
   if (!ctx || launch_index < -1) return MPDIV_EINVAL;
   MpServer* S = ctx->server;
   if (!S) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server not running");
-  std::lock_guard<std::mutex> g(S->mu);
-  S->fail_launch = launch_index;
+  S->fail_launch.store(launch_index);
   return MPDIV_OK;
 }
 
@@ -613,20 +691,12 @@ void mpdiv_serve_shutdown(mpdiv_ctx* ctx) {
   cudaSetDevice(ctx->device);
   for (auto& s : S->slots) {
     if (s.stream) cudaStreamSynchronize(s.stream);
-    if (s.ev) cudaEventDestroy(s.ev);
-    if (s.copied) cudaEventDestroy(s.copied);
     if (s.stream) cudaStreamDestroy(s.stream);
     if (s.h_meta) cudaFreeHost(s.h_meta);
-    if (s.d_meta) cudaFree(s.d_meta);
+    if (s.d_heads) cudaFree(s.d_heads);
   }
   if (S->by_ticket)
     for (uint64_t i = 0; i <= S->ticket_mask; i++) delete S->by_ticket[i].exchange(nullptr);
-  if (S->copy_stream) {
-    cudaStreamSynchronize(S->copy_stream);
-    cudaStreamDestroy(S->copy_stream);
-  }
-  cudaFree(S->d_in);
-  cudaFree(S->d_out);
   if (S->h_in) cudaFreeHost(S->h_in);
   if (S->h_out) cudaFreeHost(S->h_out);
   delete S;
@@ -644,7 +714,7 @@ extern "C" int mpdiv_serve_replay(mpdiv_ctx* ctx, int64_t n, const int64_t* arri
                                   const int64_t* u_off, const int32_t* u_len, const uint32_t* v,
                                   const int64_t* v_off, const int32_t* v_len, uint32_t* q, const int64_t* q_off,
                                   const int32_t* q_len, uint32_t* r, const int64_t* r_off, const int32_t* r_len,
-                                  int32_t* status, int64_t* latency_ns, int64_t* rejected) {
+                                  int32_t* status, int64_t* latency_ns, int64_t* rejected, int64_t* phase_ns) {
   if (!ctx || !ctx->server || n < 0) return MPDIV_EINVAL;
   std::vector<uint64_t> tickets((size_t)n);
   std::vector<int64_t> t_arr((size_t)n);
@@ -652,8 +722,12 @@ extern "C" int mpdiv_serve_replay(mpdiv_ctx* ctx, int64_t n, const int64_t* arri
   std::atomic<int> err{MPDIV_OK};
   const int64_t t0 = now_ns();
   // several submitter threads (request i goes to thread i mod kSub) so that
-  // the offered rate is not capped by one thread's operand copies
-  constexpr int kSub = 4;
+  // the offered rate is not capped by one thread's operand copies, and as
+  // many pollers; each side gets about half of the host's cores left after
+  // the scheduler, the CUDA host-function thread and the caller (2 to 8)
+  const int hw = (int)std::thread::hardware_concurrency();
+  const int kSub = std::max(2, std::min(8, (hw - 4) / 2));
+  const int kPoll = kSub;
   std::vector<std::atomic<int64_t>> sub_next(kSub);
   for (auto& x : sub_next) x.store(0);
   auto submitter_fn = [&](int tid) {
@@ -681,9 +755,8 @@ extern "C" int mpdiv_serve_replay(mpdiv_ctx* ctx, int64_t n, const int64_t* arri
   };
   std::vector<std::thread> submitters;
   for (int t = 0; t < kSub; t++) submitters.emplace_back(submitter_fn, t);
-  // several pollers too (request i is polled by thread i mod kPoll); each
-  // copies its results straight from the server's pinned output ring
-  constexpr int kPoll = 4;
+  // the pollers (request i is polled by thread i mod kPoll) copy results
+  // straight from the server's pinned output ring
   auto poller_fn = [&](int tid) {
     for (int64_t i = tid; i < n; i += kPoll) {
       while (sub_next[i % kSub].load(std::memory_order_acquire) <= i)
@@ -691,21 +764,28 @@ extern "C" int mpdiv_serve_replay(mpdiv_ctx* ctx, int64_t n, const int64_t* arri
       if (tickets[i] == 0) {
         status[i] = -1;
         latency_ns[i] = -1;
+        if (phase_ns) phase_ns[3 * i] = phase_ns[3 * i + 1] = phase_ns[3 * i + 2] = -1;
         continue;
       }
-      int64_t td = 0;
+      int64_t tm[3] = {0, 0, 0};
       int rc;
       while ((rc = poll_impl(ctx, tickets[i], q + q_off[i], q_len[i], r + r_off[i], r_len[i], &status[i], 1000000,
-                             &td)) == MPDIV_ETIMEDOUT) {
+                             tm)) == MPDIV_ETIMEDOUT) {
       }
       if (rc != MPDIV_OK) {
         int expect = MPDIV_OK;
         err.compare_exchange_strong(expect, rc);
         status[i] = -1;
         latency_ns[i] = -1;
+        if (phase_ns) phase_ns[3 * i] = phase_ns[3 * i + 1] = phase_ns[3 * i + 2] = -1;
         continue;
       }
-      latency_ns[i] = td - t_arr[i];
+      latency_ns[i] = tm[2] - t_arr[i];
+      if (phase_ns) {
+        phase_ns[3 * i] = tm[0] - t_arr[i];  // submitted after its scheduled arrival
+        phase_ns[3 * i + 1] = tm[1] - tm[0];  // queued until its batch launched
+        phase_ns[3 * i + 2] = tm[2] - tm[1];  // launched until its result was pollable
+      }
     }
   };
   std::vector<std::thread> pollers;

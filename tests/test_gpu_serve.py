@@ -67,15 +67,19 @@ def test_replay_of_a_poisson_stream():
     r = np.zeros(int(r_len.sum()), np.uint32)
     st = np.full(n, -9, np.int32)
     lat = np.zeros(n, np.int64)
+    ph = np.full(3 * n, -5, np.int64)
     c = mp.mpdiv_init(0)
     try:
         mp.mpdiv_serve_start(c, pool_digits=1 << 22, max_batch=64, max_inflight=3)
         mp.mpdiv_serve_replay(c, arr, u_flat, u_off, u_len, v_flat, v_off, v_len, q, q_off, q_len, r, r_off, r_len,
-                              st, lat)
+                              st, lat, ph)
         mp.mpdiv_serve_stop(c)
     finally:
         mp.mpdiv_destroy(c)
     assert (st == 0).all() and (lat > 0).all()
+    # the phases (submit delay, queue wait, run) are ordered and add up to the latency
+    ph = ph.reshape(n, 3)
+    assert (ph >= 0).all() and (ph.sum(axis=1) == lat).all()
     qo, ro, so, _ = oracle.divmod_ragged_u32(u_flat, u_off, u_len, v_flat, v_off, v_len, q_off, q_len, r_off, r_len)
     assert (q == qo).all() and (r == ro).all()
 
