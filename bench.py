@@ -374,6 +374,7 @@ def run_sweep(args, dev, dist, rank, ws):
     # strip multiply's digit-product idiom in registers, and plain multiply-adds
     mac3_rate, _ = mp.mpdiv_measure_peak(ctx, 0)
     imad_rate, _ = mp.mpdiv_measure_peak(ctx, 1)
+    strip_rate, _ = mp.mpdiv_measure_peak(ctx, 2)
     per_size = {}
     for i, d in enumerate(sizes):
         bits = 32 * d["n"]
@@ -415,8 +416,12 @@ def run_sweep(args, dev, dist, rank, ws):
                                    "counted by the kernel",
                      "measured": {"digit_products_Tps": mac3_rate / 1e12, "imad_Tops": imad_rate / 1e12,
                                   "frac_of_measured_idiom": achieved / (mac3_rate / 1e12),
+                                  "strip_loop_Tps": strip_rate / 1e12,
+                                  "frac_of_strip_loop": achieved / (strip_rate / 1e12),
                                   "basis": "mpdiv_measure_peak on this GPU: in-register mad.lo.cc/madc.hi.cc/addc "
-                                           "digit products and mad.lo.u32, 8 blocks x 256 threads per SM"}},
+                                           "digit products and mad.lo.u32, 8 blocks x 256 threads per SM; the strip "
+                                           "multiply's inner loop (5 columns per lane, digits from shared memory), "
+                                           "2 blocks x 256 threads per SM"}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "batched_single_launch": {"div_per_s": items_step * ws / (ms_batched / 1e3), "ms": ms_batched,
                                   "over_plain": (items_step * ws / (ms_batched / 1e3)) / value,

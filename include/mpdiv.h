@@ -221,15 +221,18 @@ int mpdiv_autotune(mpdiv_ctx *ctx, int32_t u_limbs, int32_t v_limbs, int32_t n_i
 int mpdiv_tuning(mpdiv_ctx *ctx, int32_t u_limbs, int32_t *warps, int32_t *mul_columns,
                  int32_t *karatsuba_cutoff, int32_t *regs);
 
-/* Microbenchmark of the integer multiply pipe, the measured ceiling of the
+/* Microbenchmark of the integer multiply pipe, the measured ceilings of the
  * roofline: kind 0 runs the strip multiply's digit product (mad.lo.cc /
- * madc.hi.cc / addc into independent in-register three-word accumulators),
- * kind 1 independent 32-bit multiply-adds, with eight 256-thread blocks per SM
- * for `iters` rounds (0: 4096). *rate gets digit products (kind 0) or
- * multiply-adds (kind 1) per second over all SMs, *ms the kernel time (CUDA
- * events, after one warm-up launch). Synchronous; uses a stream of its own.
- * Errors: MPDIV_EINVAL (kind not 0 or 1, iters < 0, null pointer),
- * MPDIV_ENOMEM, MPDIV_ECUDA. */
+ * madc.hi.cc / addc into independent in-register three-word accumulators)
+ * and kind 1 independent 32-bit multiply-adds, with eight 256-thread blocks
+ * per SM for `iters` rounds (0: 4096); kind 2 runs the strip multiply's inner
+ * loop itself (5 columns per lane, the window digits and the row digits read
+ * from shared memory) with two 256-thread blocks per SM, as the largest
+ * divisions run, for `iters` passes over 4200 rows (0: 8). *rate gets digit
+ * products (kinds 0 and 2) or multiply-adds (kind 1) per second over all SMs,
+ * *ms the kernel time (CUDA events, after one warm-up launch). Synchronous;
+ * uses a stream of its own. Errors: MPDIV_EINVAL (kind not 0, 1 or 2,
+ * iters < 0, null pointer), MPDIV_ENOMEM, MPDIV_ECUDA. */
 int mpdiv_measure_peak(mpdiv_ctx *ctx, int32_t kind, int32_t iters, double *rate, double *ms);
 
 /* The cost unit of the paper's multiplication count (Section 2.3, Fig. 3 and

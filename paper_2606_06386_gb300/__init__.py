@@ -306,7 +306,8 @@ def mpdiv_mul_batch(ctx, u, v, out, stream=None) -> None:
 
 def mpdiv_measure_peak(ctx, kind: int = 0, iters: int = 0):
     """(rate per second, ms) of the multiply-pipe microbenchmark: kind 0 digit
-    products of the strip multiply's idiom, kind 1 32-bit multiply-adds."""
+    products of the strip multiply's idiom, kind 1 32-bit multiply-adds, kind 2
+    digit products of the strip multiply's inner loop on shared-memory operands."""
     rate, ms = ctypes.c_double(), ctypes.c_double()
     _check(ctx, lib().mpdiv_measure_peak(ctx, kind, iters, ctypes.byref(rate), ctypes.byref(ms)))
     return rate.value, ms.value

@@ -984,13 +984,15 @@ extern "C" int mpdiv_tuning(mpdiv_ctx* ctx, int32_t u_limbs, int32_t* warps, int
 // ------------------------------------------------------------------ multiply-pipe microbenchmark
 extern "C" int mpdiv_measure_peak(mpdiv_ctx* ctx, int32_t kind, int32_t iters, double* rate, double* ms) {
   if (!ctx) return MPDIV_EINVAL;
-  if ((kind != 0 && kind != 1) || iters < 0 || !rate || !ms)
+  if (kind < 0 || kind > 2 || iters < 0 || !rate || !ms)
     return mpdiv_set_error(ctx, MPDIV_EINVAL, "bad microbenchmark arguments");
-  if (iters == 0) iters = 4096;
+  if (iters == 0) iters = kind == 2 ? 8 : 4096;
   cudaSetDevice(ctx->device);
-  int per_round = 0;
-  void* k = mp_kernel_peak(kind, &per_round);
-  const int threads = 256, blocks = 8 * ctx->num_sms;
+  int per_round = 0, smem = 0, per_sm = 0;
+  void* k = mp_kernel_peak(kind, &per_round, &smem, &per_sm);
+  if (smem > 0 && mpdiv_open_kernel_smem(k, smem) != cudaSuccess)
+    return mpdiv_set_error(ctx, MPDIV_ECUDA, "microbenchmark shared memory");
+  const int threads = 256, blocks = per_sm * ctx->num_sms;
   uint32_t* out = nullptr;
   cudaStream_t s = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1000,10 +1002,10 @@ extern "C" int mpdiv_measure_peak(mpdiv_ctx* ctx, int32_t kind, int32_t iters, d
   if (rc == MPDIV_OK) rc = mpdiv_cuda_check(ctx, cudaEventCreate(&e1), "cudaEventCreate");
   void* args[] = {&out, &iters};
   if (rc == MPDIV_OK)
-    rc = mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, 0, s), "microbenchmark warm-up");
+    rc = mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, smem, s), "microbenchmark warm-up");
   if (rc == MPDIV_OK) rc = mpdiv_cuda_check(ctx, cudaEventRecord(e0, s), "cudaEventRecord");
   if (rc == MPDIV_OK)
-    rc = mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, 0, s), "microbenchmark launch");
+    rc = mpdiv_cuda_check(ctx, cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, smem, s), "microbenchmark launch");
   if (rc == MPDIV_OK) rc = mpdiv_cuda_check(ctx, cudaEventRecord(e1, s), "cudaEventRecord");
   if (rc == MPDIV_OK) rc = mpdiv_cuda_check(ctx, cudaEventSynchronize(e1), "microbenchmark");
   float t = 0.f;

@@ -33,7 +33,7 @@ void* mp_kernel_w16_queue(int kind);    // mpdiv_q.cu: MP_K_RAGGED and MP_K_SHIN
 void* mp_kernel_prim(int warps);        // mpdiv_t.cu: the primitive test kernel (1, 2, 4, 8, 16, 32 warps)
 // mpdiv_t.cu: the multiply-pipe microbenchmark (kind 0: digit products, 1:
 // 32-bit multiply-adds) for 256-thread blocks; *ops_per_round per thread and round
-void* mp_kernel_peak(int kind, int* ops_per_round);
+void* mp_kernel_peak(int kind, int* ops_per_round, int* smem_bytes, int* blocks_per_sm);
 // kernels whose full products may use the number-theoretic transform
 void* mp_kernel_ntt_uniform(int warps);  // mpdiv_n.cu: 4, 8, 16 or 32 warps (ntt_kernel_warps)
 void* mp_kernel_ntt_mul(int warps);      // mpdiv_n.cu: the multiplication cost unit, 4, 8, 16 or 32 warps

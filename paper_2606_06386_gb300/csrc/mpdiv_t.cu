@@ -57,9 +57,54 @@ __global__ void __launch_bounds__(256) k_peak_imad(uint32_t* out, int iters) {
   for (int k = 0; k < kAcc; k++) s ^= a[k];
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
+// The strip multiply's inner loop as the division kernels run it (mp::mul_strip
+// at 5 columns per lane): each lane keeps a 5-digit window of the longer
+// operand in a register ring refilled from shared memory, and each row digit
+// of the shorter operand is a shared-memory broadcast. Every block holds
+// kStripRows row digits and kStripWin window digits; lane L reads window
+// digits 5 L + 1 up to kStripRows + 5 L + 4 < kStripWin. One round is one
+// pass over the rows.
+constexpr int kStripT = 5, kStripRows = 4200;
+constexpr int kStripWin = kStripRows + 32 * kStripT + 64;
+
+__global__ void __launch_bounds__(256) k_peak_strip(uint32_t* out, int iters) {
+  extern __shared__ uint32_t sm[];
+  uint32_t* A = sm;
+  uint32_t* Bv = sm + kStripWin;
+  for (int i = threadIdx.x; i < kStripWin; i += blockDim.x) A[i] = (uint32_t)(i * 2654435761u) ^ blockIdx.x;
+  for (int i = threadIdx.x; i < kStripRows; i += blockDim.x) Bv[i] = (uint32_t)(i * 40503u + 7u) ^ (blockIdx.x << 8);
+  __syncthreads();
+  const uint32_t* Aw = A + kStripRows + (threadIdx.x & 31) * kStripT;
+  constexpr int T = kStripT;
+  uint32_t a0[T], a1[T], a2[T];
+#pragma unroll
+  for (int c = 0; c < T; c++) a0[c] = a1[c] = a2[c] = 0u;
+  for (int it = 0; it < iters; it++) {
+    uint32_t ring[T];
+#pragma unroll
+    for (int c = 1; c < T; c++) ring[c] = Aw[c];
+    ring[0] = 0u;
+    for (int j = 0; j < kStripRows; j += T) {
+#pragma unroll
+      for (int r = 0; r < T; r++) {
+        ring[(T - r) % T] = Aw[-(j + r)];
+        const uint32_t bj = Bv[j + r];
+#pragma unroll
+        for (int c = 0; c < T; c++) mp::mac3(a0[c], a1[c], a2[c], ring[(c - r + T) % T], bj);
+      }
+    }
+  }
+  uint32_t s = 0u;
+#pragma unroll
+  for (int c = 0; c < T; c++) s ^= a0[c] ^ a1[c] ^ a2[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+static_assert(kStripRows % kStripT == 0, "whole row groups");
 }  // namespace
 
-void* mp_kernel_peak(int kind, int* ops_per_round) {
-  *ops_per_round = kAcc;
-  return kind == 0 ? (void*)k_peak_mac3 : (void*)k_peak_imad;
+void* mp_kernel_peak(int kind, int* ops_per_round, int* smem_bytes, int* blocks_per_sm) {
+  *ops_per_round = kind == 2 ? kStripRows * kStripT : kAcc;
+  *smem_bytes = kind == 2 ? (kStripWin + kStripRows) * 4 : 0;
+  *blocks_per_sm = kind == 2 ? 2 : 8;
+  return kind == 0 ? (void*)k_peak_mac3 : kind == 1 ? (void*)k_peak_imad : (void*)k_peak_strip;
 }

@@ -251,8 +251,11 @@ def test_multiply_pipe_microbenchmark():
     c = ctx()
     prod, ms0 = mp.mpdiv_measure_peak(c, 0, 1024)
     imad, ms1 = mp.mpdiv_measure_peak(c, 1, 1024)
-    assert ms0 > 0 and ms1 > 0
+    strip, ms2 = mp.mpdiv_measure_peak(c, 2, 2)
+    assert ms0 > 0 and ms1 > 0 and ms2 > 0
     assert 0 < prod < imad
+    # the inner loop also loads its digits and rotates its window: below the idiom
+    assert 0 < strip < 1.05 * prod
     assert imad < 2 * 64 * 152 * 2.1e9  # far below nonsense: 64 multiply results/clk/SM at most twice over
 
 
