@@ -489,7 +489,13 @@ def other_configs_summary(mp, ctx, dev, stream, args):
             d["p99_ms_runs"] = [_sig(r["p99_ms"], 3) for r in x["runs"]]
             d["ok"] = min(r["ok"] for r in x["runs"])
         loads[k] = d
-    serve = {"requests": args.requests, "cap_div_s": _sig(cap), **loads}
+    serve = {"requests": args.requests, "cap_div_s": _sig(cap), "pools": "device (HBM)", **loads}
+    # the same with the kernels on the pinned host rings directly (no copies)
+    _, sm_ = measure_serve(mp, ctx, dev, stream, args.requests, args.max_batch, args.max_inflight, args.low_water,
+                           batch_step=args.batch_step, max_wait_us=args.max_wait_us,
+                           serve_flags=mp.MPDIV_SERVE_MAPPED_RINGS)
+    serve["mapped_rings"] = {k: {"div_s": _sig(x["sustained_div_per_s"]), "p50_ms": _sig(x["p50_ms"], 3),
+                                 "p99_ms": _sig(x["p99_ms"], 3), "ok": x["ok"]} for k, x in sm_.items()}
     st, _, _, sclk = measure_stress(mp, ctx, dev, stream, 3)
     stress = {k.split("_")[0]: {"div_s": _sig(x["div_per_s"]), "it": [x["newton_iters_min"], x["newton_iters_max"]],
                                 "st_nz": x["status_nonzero"]} for k, x in st.items()}
@@ -599,7 +605,7 @@ def measure_mixed(mp, ctx, dev, stream, steps, warmup, per_n=True):
 
 
 def measure_serve(mp, ctx, dev, stream, n_req, max_batch, max_inflight, low_water, loads=(0.5, 0.8, 0.95),
-                  repeat_top=1, batch_step=0, max_wait_us=0):
+                  repeat_top=1, batch_step=0, max_wait_us=0, serve_flags=0):
     """Config 4: Poisson arrivals of mixed-precision requests through the
     serving loop at fractions of the plain path's measured capacity (one plain
     launch per size class); the last load is run repeat_top times."""
@@ -633,7 +639,8 @@ def measure_serve(mp, ctx, dev, stream, n_req, max_batch, max_inflight, low_wate
             lat = np.zeros(n_req, np.int64)
             ph = np.zeros(3 * n_req, np.int64)
             mp.mpdiv_serve_start(ctx, pool_digits=256 << 20, max_batch=max_batch, max_inflight=max_inflight,
-                                 low_water=low_water, batch_step=batch_step, max_wait_us=max_wait_us)
+                                 low_water=low_water, batch_step=batch_step, max_wait_us=max_wait_us,
+                                 flags=serve_flags)
             with ClockSampler(dev.index or 0) as clk:
                 t0 = time.perf_counter()
                 rej = mp.mpdiv_serve_replay(ctx, arr, R["u_flat"], uo, ul, R["v_flat"], vo, vl, q, qo, ul.copy(), r,
@@ -744,7 +751,8 @@ def run_serve(args, dev, dist, rank, ws):
     _tune_classes(mp, ctx)
     stream = torch.cuda.current_stream(dev)
     cap, res = measure_serve(mp, ctx, dev, stream, args.requests, args.max_batch, args.max_inflight, args.low_water,
-                             repeat_top=3, batch_step=args.batch_step, max_wait_us=args.max_wait_us)
+                             repeat_top=3, batch_step=args.batch_step, max_wait_us=args.max_wait_us,
+                             serve_flags=mp.MPDIV_SERVE_MAPPED_RINGS if args.mapped_rings else 0)
     n_req = args.requests
     out = {
         "metric": METRIC, "value": res["95%"]["sustained_div_per_s"], "unit": UNIT, "n_gpus": ws,
@@ -912,6 +920,8 @@ def main():
                     "batch of that class in flight before a launch, below the low-water mark (0: 8)")
     ap.add_argument("--max-wait-us", type=int, default=0, help="serve workload: longest wait of a queued request "
                     "for its batch to grow (0: 2000)")
+    ap.add_argument("--mapped-rings", action="store_true", help="serve workload: kernels use the pinned host rings "
+                    "directly (MPDIV_SERVE_MAPPED_RINGS) instead of device-resident pools")
     ap.add_argument("--persistent-queue", action="store_true", help="mixed and serve workloads: ragged batches by "
                     "the self-splitting persistent kernel (MPDIV_FLAG_PERSISTENT_QUEUE) instead of one plain launch "
                     "per size class")

@@ -39,6 +39,7 @@ MPDIV_FLAG_INJECT_LAMBDA = 1
 MPDIV_FLAG_FULL_PRODUCTS = 2
 MPDIV_FLAG_NTT_PRODUCTS = 4
 MPDIV_FLAG_PERSISTENT_QUEUE = 8
+MPDIV_SERVE_MAPPED_RINGS = 1
 MPDIV_MAX_LIMBS = 16384
 MPDIV_NOALLOC_MAX_ITEMS = 65536
 MPDIV_SERVE_CLASSES = 5
@@ -98,6 +99,7 @@ class mpdiv_serve_config(ctypes.Structure):
         ("low_water", ctypes.c_int32),
         ("max_wait_us", ctypes.c_int32),
         ("batch_step", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
     ]
 
 
@@ -332,8 +334,9 @@ def mpdiv_tuning(ctx, u_limbs: int):
 
 # ---------------------------------------------------------------- serving
 def mpdiv_serve_start(ctx, pool_digits: int = 0, max_batch: int = 0, max_inflight: int = 0, max_pending: int = 0,
-                      low_water: int = 0, max_wait_us: int = 0, batch_step: int = 0):
-    cfg = mpdiv_serve_config(pool_digits, max_batch, max_inflight, max_pending, low_water, max_wait_us, batch_step)
+                      low_water: int = 0, max_wait_us: int = 0, batch_step: int = 0, flags: int = 0):
+    cfg = mpdiv_serve_config(pool_digits, max_batch, max_inflight, max_pending, low_water, max_wait_us, batch_step,
+                             flags)
     _check(ctx, lib().mpdiv_serve_start(ctx, ctypes.byref(cfg)))
 
 

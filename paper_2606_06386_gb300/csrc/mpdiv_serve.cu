@@ -5,23 +5,27 @@
 // classes whose shared-memory plan and block shape the launches are tuned
 // for), and a batch holds requests of one class only, so that a large request
 // never sets the block shape and shared memory of a batch of small ones.
-// Operands and results stay in two pinned, device-mapped host rings: an input
-// ring (u and v of every request, in arrival order) and an output ring (q and
-// r of every launched request). The division kernels read the operands from
-// the input ring and write the results to the output ring through the rings'
-// device addresses (host memory reached over the CPU-GPU link), and a batch's
-// offsets, lengths, order and statuses sit in pinned, device-mapped memory of
-// its slot as well: a batch costs one kernel launch (two with the plain
-// kernel's retry pass) and one host function, with no copy calls.
+// Operands and results live in two device-resident pools (HBM): an input
+// ring (u and v of every request, in arrival order) and an output ring (q
+// and r of every launched request), each mirrored by a pinned host ring.
+// A batch copies its run of the input ring to the device (one copy, on one
+// in-order copy stream shared by all batches), runs, and copies its results
+// back (one copy); its offsets, lengths, order and statuses sit in pinned,
+// device-mapped memory of its slot that the kernel reads and writes
+// directly. With MPDIV_SERVE_MAPPED_RINGS the kernels instead read the
+// operands from, and write the results to, the pinned host rings through
+// their device addresses (host memory over the CPU-GPU link), and a batch is
+// one launch and one host function with no copy at all.
 // mpdiv_serve_submit reserves the request's digits at the tail of the input
 // ring and copies its operands there itself, outside the server lock. A
 // scheduler thread turns the oldest ready requests of a class into a batch
 // (requests whose submitters are still copying are left queued, in order):
-// one plain launch over the batch with the class's tuned shape (or, with
-// MPDIV_FLAG_PERSISTENT_QUEUE, one launch of the self-splitting persistent
-// kernel) on the batch's own stream, followed by a host function that
-// publishes the batch's results to the pollers and frees its slot; batches of
-// different classes overlap on the GPU.
+// the operand copy, one plain launch over the batch with the class's tuned
+// shape (or, with MPDIV_FLAG_PERSISTENT_QUEUE, one launch of the
+// self-splitting persistent kernel) and the result copy on the batch's own
+// stream, followed by a host function that publishes the batch's results to
+// the pollers and frees its slot; batches of different classes overlap on the
+// GPU.
 // Up to max_inflight batches run at once. The class whose oldest ready request
 // is oldest goes first. While fewer than low_water requests are on the GPU,
 // the queued requests of a class launch as soon as there are at least
@@ -96,7 +100,7 @@ struct Request {
   int cls = 0;                    // footprint class
   bool failed = false;            // its batch could not be launched
   int64_t in_off = -1;            // u at in_off, v at in_off + u_len (input ring digits)
-  int64_t in_seq = -1;            // its input-ring allocation
+  mp_serve::ChunkedRing::Chunk* in_chunk = nullptr;  // its input-ring chunk
   int64_t out_off = -1;           // q at out_off, r at out_off + q_len (output ring digits)
   std::shared_ptr<OutBatch> out;  // the batch's output allocation
   std::atomic<int> ready{0};      // operands copied into the ring
@@ -122,10 +126,20 @@ struct Request {
 struct MpServer {
   mpdiv_ctx* ctx = nullptr;
   mpdiv_serve_config cfg{};
-  // pinned, device-mapped rings: host addresses and the kernels' device addresses
+  // pinned host rings (their device addresses dv_*), the device pools d_*,
+  // and the rings the kernels use (k_*: the pools, or the mapped host rings)
   uint32_t *h_in = nullptr, *h_out = nullptr, *dv_in = nullptr, *dv_out = nullptr;
+  uint32_t *d_in = nullptr, *d_out = nullptr, *k_in = nullptr, *k_out = nullptr;
+  bool mapped = false;  // MPDIV_SERVE_MAPPED_RINGS
+  // the operand copies of every batch, in admission order: a batch's run of
+  // the input ring may hold requests still being written by their submitters
+  // (skipped, to be taken by a later batch), and the later batch's own copy of
+  // that space must land after this stale one
+  cudaStream_t copy_stream = nullptr;
   SpinLock sub_mu;                 // in_ring, next_ticket, arrivals, ticket slots taken
-  mp_serve::Ring in_ring;
+  // the input ring, allocated by footprint class in chunks, so that a batch's
+  // operands are one contiguous run per chunk with no other class inside
+  mp_serve::ChunkedRing in_ring{kClasses};
   std::vector<Request*> arrivals;  // submitted, not yet in a queue
   uint64_t next_ticket = 1;
   SpinLock out_mu;  // out_ring
@@ -160,6 +174,8 @@ struct MpServer {
     // forms in device memory
     uint32_t *h_meta = nullptr, *dv_meta = nullptr;
     int32_t* d_heads = nullptr;
+    cudaEvent_t copied = nullptr;         // the batch's operand copy is done (device pools)
+    int64_t out_off = 0, out_len = 0;     // the batch's output-ring digits
     bool busy = false;           // scheduler-only
     std::atomic<int> done{0};    // set by the batch's host function
     int cls = 0;                 // footprint class of the batch in flight
@@ -245,17 +261,40 @@ bool MpServer::launch(Slot& s) {
   // and statuses, through the device addresses of the pinned buffers
   const int64_t* d_off = reinterpret_cast<const int64_t*>(s.dv_meta);
   const int32_t* d_len = reinterpret_cast<const int32_t*>(s.dv_meta + 8 * n);
+  int rc = MPDIV_OK;
+  if (!mapped) {
+    // the batch's operands: one copy per input-ring chunk the batch reaches
+    // into, from its first request there to the end of its last (the requests
+    // of a class are consecutive in its chunk, in ticket order; the run may
+    // hold requests of the class still being copied in by their submitters,
+    // which a later batch copies again), on the in-order copy stream
+    // the CPU's stores to the ring come before the copies read them
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    cudaError_t e = cudaSuccess;
+    for (int64_t i = 0; i < n && e == cudaSuccess;) {
+      const mp_serve::ChunkedRing::Chunk* c = s.reqs[i]->in_chunk;
+      const int64_t lo = s.reqs[i]->in_off;
+      int64_t k = i;
+      while (k + 1 < n && s.reqs[k + 1]->in_chunk == c) k++;
+      const int64_t hi = s.reqs[k]->in_off + s.reqs[k]->u_len + s.reqs[k]->v_len;
+      e = cudaMemcpyAsync(d_in + lo, h_in + lo, 4 * (size_t)(hi - lo), cudaMemcpyHostToDevice, copy_stream);
+      i = k + 1;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(s.copied, copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s.stream, s.copied, 0);
+    if (e != cudaSuccess) return false;
+  }
   RaggedLaunch L{};
-  L.u = dv_in;
+  L.u = k_in;
   L.u_off = d_off;
   L.u_len = d_len;
-  L.v = dv_in;
+  L.v = k_in;
   L.v_off = d_off + n;
   L.v_len = d_len + n;
-  L.q = dv_out;
+  L.q = k_out;
   L.q_off = d_off + 2 * n;
   L.q_len = d_len + 2 * n;
-  L.r = dv_out;
+  L.r = k_out;
   L.r_off = d_off + 3 * n;
   L.r_len = d_len + 3 * n;
   L.status = const_cast<int32_t*>(d_len + 5 * n);
@@ -269,7 +308,11 @@ bool MpServer::launch(Slot& s) {
   L.form = form;
   // the CPU's stores to the rings and the metadata come before the launch
   std::atomic_thread_fence(std::memory_order_seq_cst);
-  const int rc = mpdiv_launch_ragged(ctx, L, s.stream);
+  rc = mpdiv_launch_ragged(ctx, L, s.stream);
+  if (rc == MPDIV_OK && !mapped &&
+      cudaMemcpyAsync(h_out + s.out_off, d_out + s.out_off, 4 * (size_t)s.out_len, cudaMemcpyDeviceToHost,
+                      s.stream) != cudaSuccess)
+    rc = MPDIV_ECUDA;
   return rc == MPDIV_OK && cudaLaunchHostFunc(s.stream, slot_done, &s) == cudaSuccess;
 }
 
@@ -285,7 +328,7 @@ void CUDART_CB MpServer::slot_done(void* p) {
   const int32_t* st = reinterpret_cast<const int32_t*>(s->h_meta + 8 * n + 5 * n);
   {
     std::lock_guard<SpinLock> g(S->sub_mu);
-    for (Request* r : s->reqs) S->in_ring.release(r->in_seq);
+    for (Request* r : s->reqs) S->in_ring.release(r->in_chunk);
   }
   S->completed.fetch_add(n, std::memory_order_relaxed);
   S->pending.fetch_sub(n, std::memory_order_relaxed);
@@ -384,6 +427,8 @@ void MpServer::run() {
       } else {
         free_slot->busy = true;
         free_slot->cls = adm;
+        free_slot->out_off = off;
+        free_slot->out_len = out_need;
         auto ob = std::make_shared<OutBatch>();
         ob->seq = oseq;
         ob->remaining = (int)b.size();
@@ -419,7 +464,7 @@ void MpServer::run() {
             std::lock_guard<SpinLock> g(sub_mu);
             b.insert(b.end(), arrivals.begin(), arrivals.end());
             arrivals.clear();
-            for (Request* r : b) in_ring.release(r->in_seq);
+            for (Request* r : b) in_ring.release(r->in_chunk);
           }
           const int64_t tf = now_ns();
           const int64_t nf = (int64_t)b.size();
@@ -480,7 +525,7 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
   if (S->cfg.max_wait_us <= 0) S->cfg.max_wait_us = 2000;
   if (S->cfg.batch_step <= 0) S->cfg.batch_step = kBatchStep;
   const int64_t half = (S->cfg.pool_digits / 2) & ~int64_t(3);
-  S->in_ring.cap = half;
+  S->in_ring.ring.cap = half;
   S->out_ring.cap = half;
   S->meta_words = meta_words_for(S->cfg.max_batch);
   {
@@ -490,8 +535,9 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
     for (uint64_t i = 0; i < cap; i++) S->by_ticket[i].store(nullptr, std::memory_order_relaxed);
     S->ticket_mask = cap - 1;
   }
-  // pinned rings mapped into the device's address space: the kernels read
-  // operands and write results there directly
+  S->mapped = (S->cfg.flags & MPDIV_SERVE_MAPPED_RINGS) != 0;
+  // pinned host rings, mapped into the device's address space (the kernels
+  // use them directly with MPDIV_SERVE_MAPPED_RINGS), and the device pools
   const unsigned mapped = cudaHostAllocMapped | cudaHostAllocPortable;
   int rc = mpdiv_cuda_check(ctx, cudaHostAlloc((void**)&S->h_in, 4 * (size_t)half, mapped), "server pinned input ring");
   if (!rc)
@@ -502,11 +548,22 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
   if (!rc)
     rc = mpdiv_cuda_check(ctx, cudaHostGetDevicePointer((void**)&S->dv_out, S->h_out, 0),
                           "device address of the output ring");
+  if (!rc && !S->mapped) {
+    rc = mpdiv_cuda_check(ctx, cudaMalloc(&S->d_in, 4 * (size_t)half), "server input pool");
+    if (!rc) rc = mpdiv_cuda_check(ctx, cudaMalloc(&S->d_out, 4 * (size_t)half), "server output pool");
+    if (!rc)
+      rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking),
+                            "server copy stream");
+  }
+  S->k_in = S->mapped ? S->dv_in : S->d_in;
+  S->k_out = S->mapped ? S->dv_out : S->d_out;
   S->slots = std::vector<MpServer::Slot>(S->cfg.max_inflight);
   for (auto& s : S->slots) {
     s.server = S;
     if (rc) break;
     rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking), "server stream");
+    if (!rc && !S->mapped)
+      rc = mpdiv_cuda_check(ctx, cudaEventCreateWithFlags(&s.copied, cudaEventDisableTiming), "server event");
     if (!rc)
       rc = mpdiv_cuda_check(ctx, cudaHostAlloc((void**)&s.h_meta, 4 * (size_t)S->meta_words, mapped),
                             "server metadata");
@@ -532,7 +589,7 @@ extern "C" int mpdiv_serve_submit(mpdiv_ctx* ctx, const uint32_t* u_host, int32_
   if (u_len < 1 || v_len < 1) return mpdiv_set_error(ctx, MPDIV_EINVAL, "digit counts must be positive");
   if (u_len > MPDIV_MAX_LIMBS || v_len > MPDIV_MAX_LIMBS)
     return mpdiv_set_error(ctx, MPDIV_EUNSUPPORTED, "at most %d digits", MPDIV_MAX_LIMBS);
-  if (2 * (int64_t)(u_len + v_len) + 8 > S->in_ring.cap)
+  if (2 * (int64_t)(u_len + v_len) + 8 > S->in_ring.ring.cap)
     return mpdiv_set_error(ctx, MPDIV_EBUSY, "request larger than the server's rings");
   if (S->stopping.load(std::memory_order_acquire)) return mpdiv_set_error(ctx, MPDIV_ESTATE, "server stopping");
   if (const int e = S->sched_error.load(std::memory_order_acquire))
@@ -555,17 +612,17 @@ extern "C" int mpdiv_serve_submit(mpdiv_ctx* ctx, const uint32_t* u_host, int32_
       S->pending.fetch_sub(1, std::memory_order_relaxed);
       return mpdiv_set_error(ctx, e, "the server stopped after a failed launch");
     }
-    int64_t seq = -1;
+    mp_serve::ChunkedRing::Chunk* chunk = nullptr;
     // the ticket's slot still holds an unpolled result from ticket - capacity,
     // or the input ring is full: retry later
     const bool slot_taken = S->by_ticket[S->next_ticket & S->ticket_mask].load(std::memory_order_acquire) != nullptr;
-    const int64_t off = slot_taken ? -1 : S->in_ring.alloc(u_len + v_len, &seq);
+    const int64_t off = slot_taken ? -1 : S->in_ring.alloc(r->cls, u_len + v_len, &chunk);
     if (off < 0) {
       S->pending.fetch_sub(1, std::memory_order_relaxed);
       return MPDIV_EBUSY;
     }
     r->in_off = off;
-    r->in_seq = seq;
+    r->in_chunk = chunk;
     r->ticket = S->next_ticket++;
     r->t_submit = now_ns();
     *ticket = r->ticket;
@@ -692,9 +749,16 @@ void mpdiv_serve_shutdown(mpdiv_ctx* ctx) {
   for (auto& s : S->slots) {
     if (s.stream) cudaStreamSynchronize(s.stream);
     if (s.stream) cudaStreamDestroy(s.stream);
+    if (s.copied) cudaEventDestroy(s.copied);
     if (s.h_meta) cudaFreeHost(s.h_meta);
     if (s.d_heads) cudaFree(s.d_heads);
   }
+  if (S->copy_stream) {
+    cudaStreamSynchronize(S->copy_stream);
+    cudaStreamDestroy(S->copy_stream);
+  }
+  if (S->d_in) cudaFree(S->d_in);
+  if (S->d_out) cudaFree(S->d_out);
   if (S->by_ticket)
     for (uint64_t i = 0; i <= S->ticket_mask; i++) delete S->by_ticket[i].exchange(nullptr);
   if (S->h_in) cudaFreeHost(S->h_in);

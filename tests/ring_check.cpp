@@ -75,6 +75,75 @@ int main() {
       return 1;
     }
   }
+  // the chunked allocation by class on top of the ring: live requests never
+  // overlap, a class's requests in one chunk are consecutive, an empty ring
+  // never refuses, and everything returns to the ring once released
+  for (int trial = 0; trial < 200; trial++) {
+    const int classes = 1 + (int)(rng() % 5);
+    mp_serve::ChunkedRing cr(classes);
+    cr.ring.cap = 256 + (int64_t)(rng() % 8000) * 4;
+    cr.chunk_digits = 16 + (int64_t)(rng() % 600);
+    struct Req {
+      int64_t off, len;
+      mp_serve::ChunkedRing::Chunk* chunk;
+    };
+    std::vector<Req> live;
+    std::vector<Req> last(classes, Req{-1, 0, nullptr});  // each class's latest allocation
+    for (int step = 0; step < 4000; step++) {
+      const bool do_alloc = live.empty() || (rng() % 100) < 55;
+      if (do_alloc) {
+        const int cls = (int)(rng() % classes);
+        const int64_t n = 1 + (int64_t)(rng() % (cr.ring.cap / 16 + 1));
+        mp_serve::ChunkedRing::Chunk* c = nullptr;
+        const int64_t off = cr.alloc(cls, n, &c);
+        const int64_t len = (n + 3) & ~int64_t(3);
+        if (off < 0) {
+          if (live.empty()) {
+            std::printf("chunked: refused %lld digits with nothing live\n", (long long)len);
+            return 1;
+          }
+          continue;
+        }
+        if (off + len > cr.ring.cap || (off & 3) || c == nullptr || off < c->off || off + len > c->off + c->len) {
+          std::printf("chunked: allocation [%lld, %lld) outside its chunk or the ring\n", (long long)off,
+                      (long long)(off + len));
+          return 1;
+        }
+        for (const Req& l : live)
+          if (off < l.off + l.len && l.off < off + len) {
+            std::printf("chunked: allocation [%lld, %lld) overlaps live [%lld, %lld)\n", (long long)off,
+                        (long long)(off + len), (long long)l.off, (long long)(l.off + l.len));
+            return 1;
+          }
+        const Req& p = last[cls];
+        if (p.chunk == c && p.off + p.len != off) {
+          std::printf("chunked: a class's requests in one chunk are not consecutive\n");
+          return 1;
+        }
+        live.push_back({off, len, c});
+        last[cls] = {off, len, c};
+      } else {
+        const size_t k = rng() % live.size();
+        mp_serve::ChunkedRing::Chunk* c = live[k].chunk;
+        live.erase(live.begin() + (long)k);
+        bool still = false;  // the chunk stays allocated while one of its requests is live
+        for (const Req& l : live) still = still || l.chunk == c;
+        for (Req& l : last)
+          if (l.chunk == c && !still) l = Req{-1, 0, nullptr};
+        cr.release(c);
+      }
+    }
+    for (const Req& l : live) cr.release(l.chunk);
+    if (cr.ring.used != 0 || !cr.ring.live.empty()) {
+      std::printf("chunked: ring not whole after releasing everything\n");
+      return 1;
+    }
+    for (auto* c : cr.cur)
+      if (c != nullptr) {
+        std::printf("chunked: a current chunk outlived its requests\n");
+        return 1;
+      }
+  }
   std::printf("ok\n");
   return 0;
 }

@@ -58,3 +58,31 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(mp, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         mp.lib()
+
+
+def test_config_structs_match_the_header(tmp_path):
+    # the binding's ctypes structures against the C compiler's layout of the
+    # header's structs (size and every field offset)
+    import ctypes
+    import subprocess
+
+    import paper_2606_06386_gb300 as mp
+
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    structs = {"mpdiv_config": mp.mpdiv_config, "mpdiv_serve_config": mp.mpdiv_serve_config}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mpdiv.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "layout")
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", exe], check=True)
+    got = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    want = []
+    for name, cls in structs.items():
+        want.append(f"{name} size {ctypes.sizeof(cls)}")
+        want += [f"{name} {f} {getattr(cls, f).offset}" for f, _ in cls._fields_]
+    assert [g for g in got if g] == want
