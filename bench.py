@@ -489,12 +489,13 @@ def other_configs_summary(mp, ctx, dev, stream, args):
             d["p99_ms_runs"] = [_sig(r["p99_ms"], 3) for r in x["runs"]]
             d["ok"] = min(r["ok"] for r in x["runs"])
         loads[k] = d
-    serve = {"requests": args.requests, "cap_div_s": _sig(cap), "pools": "device (HBM)", **loads}
-    # the same with the kernels on the pinned host rings directly (no copies)
+    serve = {"requests": args.requests, "cap_div_s": _sig(cap), "pools": "pinned host rings mapped into the GPU",
+             **loads}
+    # the same with operands and results in device pools (HBM), copied per batch
     _, sm_ = measure_serve(mp, ctx, dev, stream, args.requests, args.max_batch, args.max_inflight, args.low_water,
                            batch_step=args.batch_step, max_wait_us=args.max_wait_us,
-                           serve_flags=mp.MPDIV_SERVE_MAPPED_RINGS)
-    serve["mapped_rings"] = {k: {"div_s": _sig(x["sustained_div_per_s"]), "p50_ms": _sig(x["p50_ms"], 3),
+                           serve_flags=mp.MPDIV_SERVE_DEVICE_POOLS)
+    serve["device_pools"] = {k: {"div_s": _sig(x["sustained_div_per_s"]), "p50_ms": _sig(x["p50_ms"], 3),
                                  "p99_ms": _sig(x["p99_ms"], 3), "ok": x["ok"]} for k, x in sm_.items()}
     st, _, _, sclk = measure_stress(mp, ctx, dev, stream, 3)
     stress = {k.split("_")[0]: {"div_s": _sig(x["div_per_s"]), "it": [x["newton_iters_min"], x["newton_iters_max"]],
@@ -752,7 +753,7 @@ def run_serve(args, dev, dist, rank, ws):
     stream = torch.cuda.current_stream(dev)
     cap, res = measure_serve(mp, ctx, dev, stream, args.requests, args.max_batch, args.max_inflight, args.low_water,
                              repeat_top=3, batch_step=args.batch_step, max_wait_us=args.max_wait_us,
-                             serve_flags=mp.MPDIV_SERVE_MAPPED_RINGS if args.mapped_rings else 0)
+                             serve_flags=mp.MPDIV_SERVE_DEVICE_POOLS if args.device_pools else 0)
     n_req = args.requests
     out = {
         "metric": METRIC, "value": res["95%"]["sustained_div_per_s"], "unit": UNIT, "n_gpus": ws,
@@ -920,8 +921,8 @@ def main():
                     "batch of that class in flight before a launch, below the low-water mark (0: 8)")
     ap.add_argument("--max-wait-us", type=int, default=0, help="serve workload: longest wait of a queued request "
                     "for its batch to grow (0: 2000)")
-    ap.add_argument("--mapped-rings", action="store_true", help="serve workload: kernels use the pinned host rings "
-                    "directly (MPDIV_SERVE_MAPPED_RINGS) instead of device-resident pools")
+    ap.add_argument("--device-pools", action="store_true", help="serve workload: operands and results in device "
+                    "pools copied per batch (MPDIV_SERVE_DEVICE_POOLS) instead of the mapped host rings")
     ap.add_argument("--persistent-queue", action="store_true", help="mixed and serve workloads: ragged batches by "
                     "the self-splitting persistent kernel (MPDIV_FLAG_PERSISTENT_QUEUE) instead of one plain launch "
                     "per size class")

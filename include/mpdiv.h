@@ -248,24 +248,25 @@ int mpdiv_mul_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, const ui
 
 /* ---------------------------------------------------------------- serving
  * Continuous batching: submitted requests are copied into a pinned input ring
- * mirrored by a device-resident operand pool; a host scheduler thread launches
- * batches of them as slots free up (each batch copies its operands into the
- * pool, divides, and copies its results back from the device-resident result
- * pool), with several batches in flight on separate streams, and each batch's
- * completion publishes its results. With MPDIV_SERVE_MAPPED_RINGS the kernels
- * read the operands from, and write the results to, the pinned host rings
- * directly (device-mapped host memory) and a batch makes no copy. Requests
- * that arrive while batches run join the next launch. Admission is by footprint: a request's footprint class is the size
- * class of its dividend (class 0: at most 1024 digits, 1: 2048, 2: 4096,
- * 3: 8192, 4: more), which sets the shared memory and block shape its
- * division needs; each class has its own queue, and a batch holds requests of
- * one class only, so that a large request never sets the launch shape of small
- * ones. Batches of different classes run at once. */
+ * that is mapped into the GPU's address space; a host scheduler thread
+ * launches batches of them as slots free up, with several batches in flight
+ * on separate streams; the kernels read the operands from the input ring and
+ * write the results into a pinned, mapped output ring directly (host memory
+ * over the CPU-GPU link: a batch makes no copy), and each batch's completion
+ * publishes its results. With MPDIV_SERVE_DEVICE_POOLS the operands and
+ * results live in device-resident pools (HBM) instead, and each batch copies
+ * its operands in and its results out. Requests that arrive while batches run
+ * join the next launch. Admission is by footprint: a request's footprint
+ * class is the size class of its dividend (class 0: at most 1024 digits,
+ * 1: 2048, 2: 4096, 3: 8192, 4: more), which sets the shared memory and block
+ * shape its division needs; each class has its own queue, and a batch holds
+ * requests of one class only, so that a large request never sets the launch
+ * shape of small ones. Batches of different classes run at once. */
 #define MPDIV_SERVE_CLASSES 5
-#define MPDIV_SERVE_MAPPED_RINGS 1 /* serve_config.flags: kernels use the pinned host rings directly */
+#define MPDIV_SERVE_DEVICE_POOLS 1 /* serve_config.flags: operands and results in device pools (HBM) */
 typedef struct mpdiv_serve_config {
-  int64_t pool_digits;  /* digits of the operand and result rings, half each, both on the host
-                           (pinned) and, unless MPDIV_SERVE_MAPPED_RINGS, on the device
+  int64_t pool_digits;  /* digits of the operand and result rings, half each, on the host
+                           (pinned) and, with MPDIV_SERVE_DEVICE_POOLS, on the device too
                            (0: 64 Mi digits) */
   int32_t max_batch;    /* most requests per batch (0: 4096) */
   int32_t max_inflight; /* batches in flight at once, each on its own stream (0: 32) */

@@ -39,7 +39,7 @@ MPDIV_FLAG_INJECT_LAMBDA = 1
 MPDIV_FLAG_FULL_PRODUCTS = 2
 MPDIV_FLAG_NTT_PRODUCTS = 4
 MPDIV_FLAG_PERSISTENT_QUEUE = 8
-MPDIV_SERVE_MAPPED_RINGS = 1
+MPDIV_SERVE_DEVICE_POOLS = 1
 MPDIV_MAX_LIMBS = 16384
 MPDIV_NOALLOC_MAX_ITEMS = 65536
 MPDIV_SERVE_CLASSES = 5

@@ -76,6 +76,17 @@ __device__ __forceinline__ Blk make_group(int* red, int w0, int nw, int bar) {
   return b;
 }
 
+// The first warp of group b as a one-warp group of its own (the same
+// scratch, strip width, Karatsuba cutoff and work counter); its barriers are
+// warp barriers.
+__device__ __forceinline__ Blk first_warp(const Blk& b) {
+  Blk g = make_group(b.red, (int)(threadIdx.x >> 5) - b.warp, 1, b.bar);
+  g.work = b.work;
+  g.tcols = b.tcols;
+  g.kcut = b.kcut;
+  return g;
+}
+
 // The whole block of a kernel built for NW warps: with the group size a
 // compile-time constant, one-warp groups skip their cross-warp summaries.
 template <int NW>

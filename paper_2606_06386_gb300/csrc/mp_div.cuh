@@ -50,6 +50,18 @@ enum : int { FLAG_INJECT_LAMBDA = 1, FLAG_FULL_PRODUCTS = 2 };
 // shared memory gets ST_RETRY instead of ST_INTERNAL.
 constexpr int FLAG_FIT_OR_RETRY = 1 << 20;
 
+// Whether the early Refine iterations of a group of several warps run on its
+// first warp alone (see shinv), and up to which ell. The one- and two-warp
+// kernels, whose strip multiply is a called function, keep every iteration on
+// the whole group: there the one-warp copy of the iteration raised register
+// spills (2^15 bits: 20 % slower).
+#ifndef MP_EARLY_ON_ONE_WARP
+#define MP_EARLY_ON_ONE_WARP (!MP_MUL_NOINLINE)
+#endif
+#ifndef MP_TINY_ELL
+#define MP_TINY_ELL 64
+#endif
+
 // Guard digits of the clipped products: skipping the digit products below
 // position c - QGUARD of a product whose digits below c are shifted away drops
 // less than min(digit counts) B^(c-1) < B^c, so the shifted result is at most
@@ -268,6 +280,30 @@ __device__ __forceinline__ int shinv(const Blk& b, const Layout& L, int h, int k
   uint32_t* P = L.P;
   uint32_t* R = L.R;
   int pw = prec(b, W, lw);
+  // The early iterations work on a few dozen digits. In a group of several
+  // warps they run on its first warp alone (a one-warp group: warp barriers,
+  // no cross-warp reductions) while the other warps skip ahead; the group
+  // joins at the first iteration with ell > kTinyEll (or after the last),
+  // where the first warp hands over pw, lw and its status. The loop control
+  // (ell, m, s, ...) depends on h and k only, so every warp follows it.
+  constexpr int kTinyEll = MP_TINY_ELL;
+#if MP_EARLY_ON_ONE_WARP
+  const Blk b1 = first_warp(b);
+#endif
+  bool split = MP_EARLY_ON_ONE_WARP && b.nw > 1;
+  int st_split = ST_OK;
+  auto join = [&]() {
+    if (b.warp == 0 && b.lane == 0) {
+      b.red[RED_AUX] = pw;
+      b.red[RED_AUX + 1] = lw;
+      b.red[RED_AUX + 2] = st_split;
+    }
+    b.sync();
+    pw = b.red[RED_AUX];
+    lw = b.red[RED_AUX + 1];
+    st_split = b.red[RED_AUX + 2];
+    split = false;
+  };
   for (int it = 0; it < nit; it++) {
     const int m = min(h - k + 1 - ell, ell);
     const int s = max(0, k - 2 * ell + 1 - g);
@@ -278,111 +314,134 @@ __device__ __forceinline__ int shinv(const Blk& b, const Layout& L, int h, int k
     // operand (zero digits below it); its top digit is v's: prec(v') = kl - s
     const int pv = kl - s;
     if (pv > L.capX) return ST_INTERNAL;
-    copy(b, X, pv, [&](int i) { return V[s + i]; });
-    // ---- PowDiff(v', w, hp, ellp): (sign, |B^hp - v' w|)
-    const int hp = hh - m;
-    const int ellp = ell - g;
-    const int Lc = pv + pw - ellp + 1;
-    int sign, px;
-    if (pw == 0 || Lc >= hp) {
-      const int np = pv + pw;
-      if (np > L.capP || np > L.capX || hp + 1 > L.capX) return ST_INTERNAL;
-      mul_exact<NTT>(b, L, P, np, X, pv, W, pw);
-      const bool ge = find_first(b, hp, np, [&](int i) { return P[i] != 0u; }) >= 0;
-      if (!ge) {
-        sign = 1;
-        if (pw == 0) {  // v' w = 0: x = B^hp
-          for (int i = b.tid; i <= hp; i += b.nt) X[i] = (i == hp) ? 1u : 0u;
-          b.sync();
-          px = hp + 1;
+    if (split && ell > kTinyEll) {
+      join();
+      if (st_split != ST_OK) return st_split;
+    }
+    // one iteration (PowDiff, Step, the shift) by group gb: the whole group,
+    // or in the early iterations its first warp while the others skip it; a
+    // failure leaves the block with its status in rs
+#if MP_EARLY_ON_ONE_WARP
+    const Blk& gb = split ? b1 : b;
+#else
+    const Blk& gb = b;
+#endif
+    int rs = ST_OK;
+    if (!split || (b.warp == 0 && st_split == ST_OK)) do {
+      copy(gb, X, pv, [&](int i) { return V[s + i]; });
+      // ---- PowDiff(v', w, hp, ellp): (sign, |B^hp - v' w|)
+      const int hp = hh - m;
+      const int ellp = ell - g;
+      const int Lc = pv + pw - ellp + 1;
+      int sign, px;
+      if (pw == 0 || Lc >= hp) {
+        const int np = pv + pw;
+        if (np > L.capP || np > L.capX || hp + 1 > L.capX) { rs = ST_INTERNAL; break; }
+        mul_exact<NTT>(gb, L, P, np, X, pv, W, pw);
+        const bool ge = find_first(gb, hp, np, [&](int i) { return P[i] != 0u; }) >= 0;
+        if (!ge) {
+          sign = 1;
+          if (pw == 0) {  // v' w = 0: x = B^hp
+            for (int i = gb.tid; i <= hp; i += gb.nt) X[i] = (i == hp) ? 1u : 0u;
+            gb.sync();
+            px = hp + 1;
+          } else {
+            negate(gb, X, hp, P, np);
+            px = hp;
+          }
         } else {
-          negate(b, X, hp, P, np);
-          px = hp;
+          sign = 0;
+          copy(gb, X, np, [&](int i) { return P[i]; });
+          sub_pow(gb, X, hp, np);
+          px = np;
         }
+        px = (px > 0) ? prec(gb, X, px) : 0;
       } else {
-        sign = 0;
-        copy(b, X, np, [&](int i) { return P[i]; });
-        sub_pow(b, X, hp, np);
-        px = np;
+        if (Lc > L.capP || Lc > L.capX) { rs = ST_INTERNAL; break; }
+        if (clip_step) {
+          // MultMod clipped with the Newton step: only the digit products at
+          // columns plo = e - pw - 1 - QGUARD and up (the columns below are
+          // zero). The dropped sum D < B^(plo+2) makes the signed x larger by D,
+          // so w x grows by less than B^(e-1) and Step's result by at most one
+          // unit, which the later steps absorb
+          const int plo = max(0, e - pw - 1 - QGUARD);
+          for (int i = gb.tid; i < min(plo, Lc); i += gb.nt) P[i] = 0u;
+          mul(gb, P, Lc, X, pv, W, pw, L.OV, plo);
+        } else {
+          mul_exact<NTT>(gb, L, P, Lc, X, pv, W, pw);  // MultMod: v' w mod B^L
+        }
+        // one pass gives the sign test, the negation's pivot and |x|'s length
+        int z, t1, t2;
+        scan3(gb, P, Lc, &z, &t1, &t2);
+        if (t1 < 0) {
+          sign = 1;
+          px = 0;
+        } else if (t1 < Lc - 1) {  // top digit P_{L-1} = 0: v' w > B^hp, x = P
+          sign = 0;
+          copy(gb, X, t1 + 1, [&](int i) { return P[i]; });
+          px = t1 + 1;
+        } else {  // x = B^L - P: digits above z are the complements of P's
+          sign = 1;
+          negate_at(gb, X, Lc, P, Lc, z);
+          px = max(t2, z) + 1;
+        }
       }
-      px = (px > 0) ? prec(b, X, px) : 0;
-    } else {
-      if (Lc > L.capP || Lc > L.capX) return ST_INTERNAL;
-      if (clip_step) {
-        // MultMod clipped with the Newton step: only the digit products at
-        // columns plo = e - pw - 1 - QGUARD and up (the columns below are
-        // zero). The dropped sum D < B^(plo+2) makes the signed x larger by D,
-        // so w x grows by less than B^(e-1) and Step's result by at most one
-        // unit, which the later steps absorb
-        const int plo = max(0, e - pw - 1 - QGUARD);
-        for (int i = b.tid; i < min(plo, Lc); i += b.nt) P[i] = 0u;
-        mul(b, P, Lc, X, pv, W, pw, L.OV, plo);
+      // ---- Step: res = w B^m +/- shift_{2m-hh}(w x), floor semantics
+      int lr;
+      if (px == 0) {
+        lr = pw + m;
+        if (lr > L.capR) { rs = ST_INTERNAL; break; }
+        copy(gb, R, lr, [&](int i) { return i >= m ? W[i - m] : 0u; });
       } else {
-        mul_exact<NTT>(b, L, P, Lc, X, pv, W, pw);  // MultMod: v' w mod B^L
+        const int nt = pw + px;
+        if (!clip_step && nt > L.capP) { rs = ST_INTERNAL; break; }
+        int p0 = 0;  // lowest column of w x; column c of the product is at P[c - p0]
+        if (clip_step) {
+          // clipped: only the digit products at columns e - QGUARD and up, so
+          // shift_{-e} of the product may come out one short (and the floor's
+          // sticky digit is read from the computed columns only); the iterate may
+          // then differ from Algorithm 1's by one unit, which Refine's later steps
+          // and the quotient's corrections absorb
+          const int plo = max(0, e - QGUARD);
+          p0 = mul_first_column(nt, plo);
+          if (nt - p0 > L.capP || ov_words(nt - p0) > L.capOV) { rs = ST_INTERNAL; break; }
+          mul(gb, P, nt, W, pw, X, px, L.OV, plo, false, true);
+        } else if (ntt_fits<NTT>(gb, L, pw, px)) {
+          mul_exact<NTT>(gb, L, P, nt, W, pw, X, px);
+        } else {
+          // Karatsuba scratch: the product buffer's free tail, and R (free until
+          // Step's sum below) for chunk products
+          const int sa = (nt + 3) & ~3;
+          mul_full(gb, P, W, pw, X, px, L.OV, P + sa, L.capP - sa, R, L.capR);
+        }
+        lr = max(pw + m, nt - e) + 1;
+        if (lr > L.capR) { rs = ST_INTERNAL; break; }
+        auto wm = [&](int i) -> uint32_t { return (i >= m && i - m < pw) ? W[i - m] : 0u; };
+        const uint32_t* Pc = P - p0;
+        auto pe = [&](int i) -> uint32_t { return (i + e < nt) ? Pc[i + e] : 0u; };
+        if (sign) {
+          addsub<false>(gb, R, lr, wm, pe, 0u);
+        } else {
+          const uint32_t c = find_first(gb, p0, min(e, nt), [&](int i) { return Pc[i] != 0u; }) >= 0 ? 1u : 0u;
+          const uint32_t bout = addsub<true>(gb, R, lr, wm, pe, c);
+          if (bout) { rs = ST_INTERNAL; break; }  // a negative iterate never happens (Theorem 2)
+        }
       }
-      // one pass gives the sign test, the negation's pivot and |x|'s length
-      int z, t1, t2;
-      scan3(b, P, Lc, &z, &t1, &t2);
-      if (t1 < 0) {
-        sign = 1;
-        px = 0;
-      } else if (t1 < Lc - 1) {  // top digit P_{L-1} = 0: v' w > B^hp, x = P
-        sign = 0;
-        copy(b, X, t1 + 1, [&](int i) { return P[i]; });
-        px = t1 + 1;
-      } else {  // x = B^L - P: digits above z are the complements of P's
-        sign = 1;
-        negate_at(b, X, Lc, P, Lc, z);
-        px = max(t2, z) + 1;
-      }
+      // ---- w <- shift_{-m}(res) for the first two iterations, else shift_{-1}(res)
+      const int d = (it < 2) ? m : 1;
+      lw = max(lr - d, 0);
+      if (lw > L.capW) { rs = ST_INTERNAL; break; }
+      pw = copy_prec(gb, W, lw, [&](int i) { return R[i + d]; });
+    } while (false);
+    if (rs != ST_OK) {
+      if (!split) return rs;
+      st_split = rs;  // a failed early iteration stops the first warp's work until the join
     }
-    // ---- Step: res = w B^m +/- shift_{2m-hh}(w x), floor semantics
-    int lr;
-    if (px == 0) {
-      lr = pw + m;
-      if (lr > L.capR) return ST_INTERNAL;
-      copy(b, R, lr, [&](int i) { return i >= m ? W[i - m] : 0u; });
-    } else {
-      const int nt = pw + px;
-      if (!clip_step && nt > L.capP) return ST_INTERNAL;
-      int p0 = 0;  // lowest column of w x; column c of the product is at P[c - p0]
-      if (clip_step) {
-        // clipped: only the digit products at columns e - QGUARD and up, so
-        // shift_{-e} of the product may come out one short (and the floor's
-        // sticky digit is read from the computed columns only); the iterate may
-        // then differ from Algorithm 1's by one unit, which Refine's later steps
-        // and the quotient's corrections absorb
-        const int plo = max(0, e - QGUARD);
-        p0 = mul_first_column(nt, plo);
-        if (nt - p0 > L.capP || ov_words(nt - p0) > L.capOV) return ST_INTERNAL;
-        mul(b, P, nt, W, pw, X, px, L.OV, plo, false, true);
-      } else if (ntt_fits<NTT>(b, L, pw, px)) {
-        mul_exact<NTT>(b, L, P, nt, W, pw, X, px);
-      } else {
-        // Karatsuba scratch: the product buffer's free tail, and R (free until
-        // Step's sum below) for chunk products
-        const int sa = (nt + 3) & ~3;
-        mul_full(b, P, W, pw, X, px, L.OV, P + sa, L.capP - sa, R, L.capR);
-      }
-      lr = max(pw + m, nt - e) + 1;
-      if (lr > L.capR) return ST_INTERNAL;
-      auto wm = [&](int i) -> uint32_t { return (i >= m && i - m < pw) ? W[i - m] : 0u; };
-      const uint32_t* Pc = P - p0;
-      auto pe = [&](int i) -> uint32_t { return (i + e < nt) ? Pc[i + e] : 0u; };
-      if (sign) {
-        addsub<false>(b, R, lr, wm, pe, 0u);
-      } else {
-        const uint32_t c = find_first(b, p0, min(e, nt), [&](int i) { return Pc[i] != 0u; }) >= 0 ? 1u : 0u;
-        const uint32_t bout = addsub<true>(b, R, lr, wm, pe, c);
-        if (bout) return ST_INTERNAL;  // a negative iterate never happens (Theorem 2)
-      }
-    }
-    // ---- w <- shift_{-m}(res) for the first two iterations, else shift_{-1}(res)
-    const int d = (it < 2) ? m : 1;
-    lw = max(lr - d, 0);
-    if (lw > L.capW) return ST_INTERNAL;
-    pw = copy_prec(b, W, lw, [&](int i) { return R[i + d]; });
     if (it >= 2) ell = ell + m - 1;
+  }
+  if (split) {
+    join();
+    if (st_split != ST_OK) return st_split;
   }
   // final shift of Refine: h-k-4 digits when h-k < 2, else -2
   const int dd = (h - k < 2) ? 4 - (h - k) : 2;

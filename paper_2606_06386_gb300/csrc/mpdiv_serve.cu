@@ -5,21 +5,26 @@
 // classes whose shared-memory plan and block shape the launches are tuned
 // for), and a batch holds requests of one class only, so that a large request
 // never sets the block shape and shared memory of a batch of small ones.
-// Operands and results live in two device-resident pools (HBM): an input
-// ring (u and v of every request, in arrival order) and an output ring (q
-// and r of every launched request), each mirrored by a pinned host ring.
-// A batch copies its run of the input ring to the device (one copy, on one
-// in-order copy stream shared by all batches), runs, and copies its results
-// back (one copy); its offsets, lengths, order and statuses sit in pinned,
-// device-mapped memory of its slot that the kernel reads and writes
-// directly. With MPDIV_SERVE_MAPPED_RINGS the kernels instead read the
-// operands from, and write the results to, the pinned host rings through
-// their device addresses (host memory over the CPU-GPU link), and a batch is
-// one launch and one host function with no copy at all.
+// Operands and results stay in two pinned host rings mapped into the GPU's
+// address space: an input ring (u and v of every request, in arrival order)
+// and an output ring (q and r of every launched request). The division
+// kernels read the operands from the input ring and write the results to the
+// output ring through the rings' device addresses (host memory reached over
+// the coherent CPU-GPU link), and a batch's offsets, lengths, order and
+// statuses sit in pinned, device-mapped memory of its slot: a batch costs one
+// kernel launch (two with the plain kernel's retry pass) and one host
+// function, with no copy.
+// With MPDIV_SERVE_DEVICE_POOLS the operands and results live in device
+// pools (HBM) mirroring the rings instead: the input ring is then allocated
+// by footprint class in chunks, so that a batch (a run of consecutive
+// requests of one class) copies its operands to the device in one copy per
+// chunk it reaches into, runs, and copies its results back, all on its own
+// stream.
 // mpdiv_serve_submit reserves the request's digits at the tail of the input
 // ring and copies its operands there itself, outside the server lock. A
 // scheduler thread turns the oldest ready requests of a class into a batch
-// (requests whose submitters are still copying are left queued, in order):
+// (requests whose submitters are still copying them in are skipped and stay
+// queued, in order; a device-pool batch stops at the first of them):
 // the operand copy, one plain launch over the batch with the class's tuned
 // shape (or, with MPDIV_FLAG_PERSISTENT_QUEUE, one launch of the
 // self-splitting persistent kernel) and the result copy on the batch's own
@@ -130,15 +135,12 @@ struct MpServer {
   // and the rings the kernels use (k_*: the pools, or the mapped host rings)
   uint32_t *h_in = nullptr, *h_out = nullptr, *dv_in = nullptr, *dv_out = nullptr;
   uint32_t *d_in = nullptr, *d_out = nullptr, *k_in = nullptr, *k_out = nullptr;
-  bool mapped = false;  // MPDIV_SERVE_MAPPED_RINGS
-  // the operand copies of every batch, in admission order: a batch's run of
-  // the input ring may hold requests still being written by their submitters
-  // (skipped, to be taken by a later batch), and the later batch's own copy of
-  // that space must land after this stale one
-  cudaStream_t copy_stream = nullptr;
+  bool mapped = true;  // false with MPDIV_SERVE_DEVICE_POOLS
+
   SpinLock sub_mu;                 // in_ring, next_ticket, arrivals, ticket slots taken
-  // the input ring, allocated by footprint class in chunks, so that a batch's
-  // operands are one contiguous run per chunk with no other class inside
+  // the input ring, allocated by footprint class in chunks, so that a
+  // device-pool batch's operands are one contiguous run per chunk with no
+  // other class inside
   mp_serve::ChunkedRing in_ring{kClasses};
   std::vector<Request*> arrivals;  // submitted, not yet in a queue
   uint64_t next_ticket = 1;
@@ -174,7 +176,6 @@ struct MpServer {
     // forms in device memory
     uint32_t *h_meta = nullptr, *dv_meta = nullptr;
     int32_t* d_heads = nullptr;
-    cudaEvent_t copied = nullptr;         // the batch's operand copy is done (device pools)
     int64_t out_off = 0, out_len = 0;     // the batch's output-ring digits
     bool busy = false;           // scheduler-only
     std::atomic<int> done{0};    // set by the batch's host function
@@ -264,10 +265,11 @@ bool MpServer::launch(Slot& s) {
   int rc = MPDIV_OK;
   if (!mapped) {
     // the batch's operands: one copy per input-ring chunk the batch reaches
-    // into, from its first request there to the end of its last (the requests
-    // of a class are consecutive in its chunk, in ticket order; the run may
-    // hold requests of the class still being copied in by their submitters,
-    // which a later batch copies again), on the in-order copy stream
+    // into, from its first request there to the end of its last, on the
+    // batch's own stream. A device-pool batch is a run of consecutive
+    // requests of its class (the scheduler stops at a request still being
+    // copied in), so these copies hold no other batch's operands that are not
+    // final, and batches need no ordering among their copies.
     // the CPU's stores to the ring come before the copies read them
     std::atomic_thread_fence(std::memory_order_seq_cst);
     cudaError_t e = cudaSuccess;
@@ -277,11 +279,9 @@ bool MpServer::launch(Slot& s) {
       int64_t k = i;
       while (k + 1 < n && s.reqs[k + 1]->in_chunk == c) k++;
       const int64_t hi = s.reqs[k]->in_off + s.reqs[k]->u_len + s.reqs[k]->v_len;
-      e = cudaMemcpyAsync(d_in + lo, h_in + lo, 4 * (size_t)(hi - lo), cudaMemcpyHostToDevice, copy_stream);
+      e = cudaMemcpyAsync(d_in + lo, h_in + lo, 4 * (size_t)(hi - lo), cudaMemcpyHostToDevice, s.stream);
       i = k + 1;
     }
-    if (e == cudaSuccess) e = cudaEventRecord(s.copied, copy_stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s.stream, s.copied, 0);
     if (e != cudaSuccess) return false;
   }
   RaggedLaunch L{};
@@ -400,6 +400,8 @@ void MpServer::run() {
       while (!qc.empty() && (int64_t)b.size() < cfg.max_batch) {
         Request* r = qc.front();
         if (!r->ready.load(std::memory_order_acquire)) {
+          // a device-pool batch is a run of consecutive requests (see launch)
+          if (!mapped) break;
           skipped.push_back(r);
           qc.pop_front();
           continue;
@@ -535,9 +537,9 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
     for (uint64_t i = 0; i < cap; i++) S->by_ticket[i].store(nullptr, std::memory_order_relaxed);
     S->ticket_mask = cap - 1;
   }
-  S->mapped = (S->cfg.flags & MPDIV_SERVE_MAPPED_RINGS) != 0;
+  S->mapped = (S->cfg.flags & MPDIV_SERVE_DEVICE_POOLS) == 0;
   // pinned host rings, mapped into the device's address space (the kernels
-  // use them directly with MPDIV_SERVE_MAPPED_RINGS), and the device pools
+  // use them directly unless MPDIV_SERVE_DEVICE_POOLS), and the device pools
   const unsigned mapped = cudaHostAllocMapped | cudaHostAllocPortable;
   int rc = mpdiv_cuda_check(ctx, cudaHostAlloc((void**)&S->h_in, 4 * (size_t)half, mapped), "server pinned input ring");
   if (!rc)
@@ -551,9 +553,6 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
   if (!rc && !S->mapped) {
     rc = mpdiv_cuda_check(ctx, cudaMalloc(&S->d_in, 4 * (size_t)half), "server input pool");
     if (!rc) rc = mpdiv_cuda_check(ctx, cudaMalloc(&S->d_out, 4 * (size_t)half), "server output pool");
-    if (!rc)
-      rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking),
-                            "server copy stream");
   }
   S->k_in = S->mapped ? S->dv_in : S->d_in;
   S->k_out = S->mapped ? S->dv_out : S->d_out;
@@ -562,8 +561,6 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
     s.server = S;
     if (rc) break;
     rc = mpdiv_cuda_check(ctx, cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking), "server stream");
-    if (!rc && !S->mapped)
-      rc = mpdiv_cuda_check(ctx, cudaEventCreateWithFlags(&s.copied, cudaEventDisableTiming), "server event");
     if (!rc)
       rc = mpdiv_cuda_check(ctx, cudaHostAlloc((void**)&s.h_meta, 4 * (size_t)S->meta_words, mapped),
                             "server metadata");
@@ -749,13 +746,8 @@ void mpdiv_serve_shutdown(mpdiv_ctx* ctx) {
   for (auto& s : S->slots) {
     if (s.stream) cudaStreamSynchronize(s.stream);
     if (s.stream) cudaStreamDestroy(s.stream);
-    if (s.copied) cudaEventDestroy(s.copied);
     if (s.h_meta) cudaFreeHost(s.h_meta);
     if (s.d_heads) cudaFree(s.d_heads);
-  }
-  if (S->copy_stream) {
-    cudaStreamSynchronize(S->copy_stream);
-    cudaStreamDestroy(S->copy_stream);
   }
   if (S->d_in) cudaFree(S->d_in);
   if (S->d_out) cudaFree(S->d_out);

@@ -51,10 +51,10 @@ def test_results_alone_equal_results_in_the_mix():
         assert (q == qo).all() and (r == ro).all()
 
 
-@pytest.mark.parametrize("mapped", [False, True], ids=["device_pools", "mapped_rings"])
-def test_replay_of_a_poisson_stream(mapped):
-    # both places for operands and results: the device-resident pools (copies
-    # per batch) and the pinned host rings the kernels use directly
+@pytest.mark.parametrize("device_pools", [False, True], ids=["mapped_rings", "device_pools"])
+def test_replay_of_a_poisson_stream(device_pools):
+    # both places for operands and results: the pinned host rings the kernels
+    # use directly (the default) and device-resident pools (copies per batch)
     import paper_2606_06386_gb300 as mp
 
     n = 300
@@ -74,7 +74,7 @@ def test_replay_of_a_poisson_stream(mapped):
     c = mp.mpdiv_init(0)
     try:
         mp.mpdiv_serve_start(c, pool_digits=1 << 22, max_batch=64, max_inflight=3,
-                             flags=mp.MPDIV_SERVE_MAPPED_RINGS if mapped else 0)
+                             flags=mp.MPDIV_SERVE_DEVICE_POOLS if device_pools else 0)
         mp.mpdiv_serve_replay(c, arr, u_flat, u_off, u_len, v_flat, v_off, v_len, q, q_off, q_len, r, r_off, r_len,
                               st, lat, ph)
         mp.mpdiv_serve_stop(c)
