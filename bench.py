@@ -914,7 +914,8 @@ def main():
                     "products by the number-theoretic transform where it fits")
     ap.add_argument("--requests", type=int, default=200000, help="serve workload: number of requests")
     ap.add_argument("--max-batch", type=int, default=1024, help="serve workload: most requests per batch")
-    ap.add_argument("--max-inflight", type=int, default=32, help="serve workload: batches in flight")
+    ap.add_argument("--max-inflight", type=int, default=0, help="serve workload: batches in flight (0: the "
+                    "server's default)")
     ap.add_argument("--low-water", type=int, default=2048, help="serve workload: requests on the GPU below "
                     "which queued requests launch at once")
     ap.add_argument("--batch-step", type=int, default=0, help="serve workload: queued requests of a class per "

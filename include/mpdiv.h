@@ -269,14 +269,14 @@ typedef struct mpdiv_serve_config {
                            (pinned) and, with MPDIV_SERVE_DEVICE_POOLS, on the device too
                            (0: 64 Mi digits) */
   int32_t max_batch;    /* most requests per batch (0: 4096) */
-  int32_t max_inflight; /* batches in flight at once, each on its own stream (0: 32) */
+  int32_t max_inflight; /* batches in flight at once, each on its own stream (0: 64) */
   int32_t max_pending;  /* submitted-but-unfinished requests before EBUSY (0: 1<<20) */
   int32_t low_water;    /* below this many requests on the GPU, queued requests launch as
                            soon as there are batch_step of them per batch in flight; above it
                            they gather into larger batches (0: 2048) */
   int32_t max_wait_us;  /* longest a queued request waits for its batch to grow (0: 2000) */
   int32_t batch_step;   /* below low_water, a class's queued requests launch once there are this
-                           many per batch of that class in flight (0: 16) */
+                           many per batch of that class in flight (0: 32) */
   int32_t flags;        /* MPDIV_SERVE_* */
 } mpdiv_serve_config;
 

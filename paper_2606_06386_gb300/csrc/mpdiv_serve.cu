@@ -63,7 +63,7 @@ namespace {
 
 // Requests a launch needs per batch already in flight while the GPU is below
 // its low-water mark (see the header comment), unless configured.
-constexpr int kBatchStep = 16;
+constexpr int kBatchStep = 32;
 
 // Footprint classes: the dividend's size class (mp::class_of).
 constexpr int kClasses = MPDIV_SERVE_CLASSES;
@@ -521,7 +521,7 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
   if (cfg) S->cfg = *cfg;
   if (S->cfg.pool_digits <= 0) S->cfg.pool_digits = 64ll << 20;
   if (S->cfg.max_batch <= 0) S->cfg.max_batch = 4096;
-  if (S->cfg.max_inflight <= 0) S->cfg.max_inflight = 32;
+  if (S->cfg.max_inflight <= 0) S->cfg.max_inflight = 64;
   if (S->cfg.max_pending <= 0) S->cfg.max_pending = 1 << 20;
   if (S->cfg.low_water <= 0) S->cfg.low_water = 2048;
   if (S->cfg.max_wait_us <= 0) S->cfg.max_wait_us = 2000;
