@@ -64,12 +64,12 @@ SM_COUNT_GB300 = 152
 PRODUCTS_PER_CLK_SM = 32  # 64 32-bit IMAD results/clk/SM, two (lo, hi) per 32x32->64 digit product
 SM_MAX_MHZ = 2070.0
 # DRAM bytes per 2^18-bit division of k_div_uniform, from one ncu capture of
-# that kernel (dram__bytes_read.sum + dram__bytes_write.sum = 15,107,072 + 0
-# bytes over a 304-division launch, 8 warps, 5 columns per lane, 128 registers;
-# the 64-register build read 15,113,728 and wrote 256): the operands read once,
-# the results held in L2; the roofline's traffic is this times the launch's
-# divisions
-DRAM_BYTES_PER_DIV_2E18 = 15107072 / 304
+# that kernel (dram__bytes_read.sum + dram__bytes_write.sum = 15,427,840 +
+# 1,024 bytes over a 304-division launch, 8 warps, 5 columns per lane, 64
+# registers, early Refine iterations on the first warp): the operands read
+# once, the results held in L2; the roofline's traffic is this times the
+# launch's divisions
+DRAM_BYTES_PER_DIV_2E18 = (15427840 + 1024) / 304
 
 
 def _peaks():
@@ -408,8 +408,8 @@ def run_sweep(args, dev, dist, rank, ws):
                      "traffic": (DRAM_BYTES_PER_DIV_2E18 * sizes[big]["b"]
                                  if sizes[big]["n"] == 8192 and args.products == "clipped" else None),
                      "traffic_unit": "bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum of a "
-                                     "304-division launch, scaled by divisions; the writes are 0 (q and r stay in "
-                                     "L2 within the launch), the reads are the operands once",
+                                     "304-division launch, scaled by divisions; the writes are 1 KB (q and r stay "
+                                     "in L2 within the launch), the reads are the operands once",
                      "peak_basis": "derived: 152 SMs x 32 digit products/clk/SM (64 IMAD/clk/SM, lo+hi per "
                                    "32x32->64 product) x 2070 MHz max SM clock",
                      "work_basis": "algorithmic 32x32-bit digit products of Algorithms 1-3 at operand precision, "
