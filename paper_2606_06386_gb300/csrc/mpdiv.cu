@@ -422,7 +422,10 @@ int mpdiv_prepare_uniform(mpdiv_ctx* ctx, const UniformLaunch& L, PreparedLaunch
         a.smem_words = fit / 4;
         P->smem = fit;
         P->retry_smem = smem;
-        P->retry_grid = std::min<int64_t>(std::min<int64_t>(L.n, (int64_t)ctx->num_sms * occ_full), 0x7fffffff);
+        // one block per item, as the fit pass: the items it leaves can be many
+        // and of uneven cost (divisors shorter than the batch's digit count),
+        // and the block scheduler balances them; the others exit at once
+        P->retry_grid = std::min<int64_t>(L.n, 0x7fffffff);
       }
     }
   }
