@@ -54,7 +54,9 @@ constexpr int FLAG_FIT_OR_RETRY = 1 << 20;
 // first warp alone (see shinv), and up to which ell. The one- and two-warp
 // kernels, whose strip multiply is a called function, keep every iteration on
 // the whole group: there the one-warp copy of the iteration raised register
-// spills, and 2^15-bit divisions got slower (0.951 to 1.148 ms per 8192).
+// spills, and 2^15-bit divisions got slower (0.951 to 1.148 ms per 8192). So
+// does the self-splitting persistent kernel (its translation units set this
+// to 0), which ran the sweep's divisions 1.4 % slower with it.
 #ifndef MP_EARLY_ON_ONE_WARP
 #define MP_EARLY_ON_ONE_WARP (!MP_MUL_NOINLINE)
 #endif
