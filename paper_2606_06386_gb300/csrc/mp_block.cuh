@@ -436,6 +436,14 @@ __device__ __forceinline__ void mac3(uint32_t& c0, uint32_t& c1, uint32_t& c2, u
       : "r"(a), "r"(bb));
 }
 
+// Whether the strip multiply's loop takes two row groups per trip at T = 3. The
+// translation units of the one-, two- and four-warp kernels, which run the
+// sizes tuned to T = 3, define it to 1; in the larger kernels, which also
+// inline the wider strips, the longer code made the 2^18-bit launch 1 % slower.
+#ifndef MP_STRIP_T3_UNROLL
+#define MP_STRIP_T3_UNROLL 0
+#endif
+
 // One warp strip, columns [P0, P0 + 32T): lane owns columns [p0, p0+T) of A*B
 // restricted to rows j in [jlo, jhi) of B. Each lane's column sums come to T digits plus two
 // overflow digits, which belong to the next lane's first two columns; they are
@@ -461,16 +469,27 @@ __device__ __forceinline__ void mul_strip(const Blk& b, uint32_t* C, int npos, c
     ring[0] = 0u;
     const int ngroups = (jhi - jlo + T - 1) / T;
     int j = jlo;
-    for (int gi = 0; gi < ngroups; gi++) {
-#pragma unroll
-      for (int r = 0; r < T; r++) {
-        ring[(T - r) % T] = Aw[-(j + r)];
-        const uint32_t bj = Bv[j + r];
-#pragma unroll
-        for (int c = 0; c < T; c++) mac3(a0[c], a1[c], a2[c], ring[(c - r + T) % T], bj);
-      }
-      j += T;
+    // one group of T rows: each lane's window moves down one digit per row
+#define MP_STRIP_GROUP                                                               \
+  {                                                                                  \
+    _Pragma("unroll") for (int r = 0; r < T; r++) {                                  \
+      ring[(T - r) % T] = Aw[-(j + r)];                                              \
+      const uint32_t bj = Bv[j + r];                                                 \
+      _Pragma("unroll") for (int c = 0; c < T; c++)                                  \
+          mac3(a0[c], a1[c], a2[c], ring[(c - r + T) % T], bj);                      \
+    }                                                                                \
+    j += T;                                                                          \
+  }
+    if constexpr (T == 3 && MP_STRIP_T3_UNROLL) {
+      // two groups per loop trip at T = 3, whose short groups spend a larger
+      // share on the loop itself (2^16 bits: 2.5 % faster); the wider strips
+      // keep the compiler's own unrolling (two per trip: 4 % slower at T = 5)
+#pragma unroll 2
+      for (int gi = 0; gi < ngroups; gi++) MP_STRIP_GROUP
+    } else {
+      for (int gi = 0; gi < ngroups; gi++) MP_STRIP_GROUP
     }
+#undef MP_STRIP_GROUP
   }
   // fold the three-word columns into T+2 digits
   uint32_t o[T + 2];

@@ -4,6 +4,7 @@
 // sizes build in parallel).
 #define MP_MUL_NOINLINE 1  // the strip multiply as one called copy (see mp_block.cuh)
 #define MP_VECTOR_IO 0  // digit-by-digit operand loads and result stores (see mp_block.cuh)
+#define MP_STRIP_T3_UNROLL 1  // two row groups per loop trip at T = 3 (see mp_block.cuh)
 #include "mp_kernels.cuh"
 #include "mpdiv_kernels.h"
 

@@ -1,5 +1,6 @@
 // Division kernels instantiated for 128-thread blocks (compiled as a
 // separate translation unit so that the block sizes build in parallel).
+#define MP_STRIP_T3_UNROLL 1  // two row groups per loop trip at T = 3 (see mp_block.cuh)
 #include "mp_kernels.cuh"
 #include "mpdiv_kernels.h"
 
