@@ -370,3 +370,29 @@ def test_fit_pass_and_retry_pass(n, kl):
         Q, R, S, _ = run_uniform(U, V, cols=cols)
         assert (S == 0).all()
         assert_same(Q, R, S, Qo, Ro, So)
+
+
+@pytest.mark.parametrize("n,kl,warps,cols,items", [(1024, 512, 2, 3, 4096), (1024, 512, 1, 3, 4096),
+                                                    (4096, 2048, 4, 5, 1024)])
+def test_retry_pass_on_a_batch_of_several_waves(n, kl, warps, cols, items):
+    # a batch of several waves, where the plain launch runs as a fit pass and
+    # a retry pass (checked through mpdiv_batch_launches): the divisors have
+    # random lengths below their buffers, as in the paper's datasets, so most
+    # items need the larger plan and the retry pass divides them, one block
+    # per item; every status 0 and every digit the oracle's
+    import paper_2606_06386_gb300 as mp
+
+    c = ctx(warps=warps, cols=cols)  # shapes whose fit pass holds more blocks per SM
+    assert mp.mpdiv_batch_launches(c, items, n, kl) == 2
+    U = I.uniform_batch(items, n, seed=95 + n, stream=kl)
+    V = I.uniform_batch(items, kl, seed=96 + n, stream=kl)
+    rnd = np.random.default_rng(n * 7 + kl)
+    for i in range(items):
+        if i % 8:  # one item in eight keeps its full length (the fit pass divides it)
+            V[i, rnd.integers(1, kl):] = 0
+            if V[i].max() == 0:
+                V[i, 0] = 5
+    Q, R, S, _ = run_uniform(U, V, warps=warps, cols=cols)
+    assert (S == 0).all()
+    Qo, Ro, So = oracle_uniform(U, V)
+    assert_same(Q, R, S, Qo, Ro, So)
