@@ -268,7 +268,8 @@ def test_admission_by_footprint_keeps_classes_apart():
         assert (q == qo).all() and (r == ro).all()
 
 
-def test_a_failed_launch_fails_its_requests_and_the_server_refuses_work():
+@pytest.mark.parametrize("device_pools", [False, True], ids=["mapped_rings", "device_pools"])
+def test_a_failed_launch_fails_its_requests_and_the_server_refuses_work(device_pools):
     # the host-side hook fails the server's second launch before any of its
     # work reaches the GPU: the first request's result is exact; the failed
     # batch's requests and those still queued finish with status 4 and poll
@@ -279,7 +280,8 @@ def test_a_failed_launch_fails_its_requests_and_the_server_refuses_work():
     items = _mix(24, seed=I.SEED_BASE + 33)
     c = mp.mpdiv_init(0)
     try:
-        mp.mpdiv_serve_start(c, pool_digits=1 << 22, max_batch=4, max_inflight=2)
+        flags = mp.MPDIV_SERVE_DEVICE_POOLS if device_pools else 0
+        mp.mpdiv_serve_start(c, pool_digits=1 << 22, max_batch=4, max_inflight=2, flags=flags)
         mp.mpdiv_debug_serve_fail_launch(c, 1)
         u, v = items[0]
         t0 = _submit_retry(mp, c, u, v)
@@ -306,7 +308,7 @@ def test_a_failed_launch_fails_its_requests_and_the_server_refuses_work():
         with pytest.raises(mp.MpdivError) as e:
             mp.mpdiv_serve_stop(c)
         assert e.value.code == mp.MPDIV_ECUDA
-        mp.mpdiv_serve_start(c, pool_digits=1 << 22)  # a new server starts clean
+        mp.mpdiv_serve_start(c, pool_digits=1 << 22, flags=flags)  # a new server starts clean
         u, v = items[2]
         t = _submit_retry(mp, c, u, v)
         rc, q, r, st = mp.mpdiv_serve_poll(c, t, len(u), len(v), timeout_us=30_000_000)
