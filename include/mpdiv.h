@@ -253,9 +253,10 @@ int mpdiv_mul_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, const ui
  * on separate streams; the kernels read the operands from the input ring and
  * write the results into a pinned, mapped output ring directly (host memory
  * over the CPU-GPU link: a batch makes no copy), and each batch's completion
- * publishes its results. With MPDIV_SERVE_DEVICE_POOLS the operands and
- * results live in device-resident pools (HBM) instead, and each batch copies
- * its operands in and its results out. Requests that arrive while batches run
+ * publishes its results. With MPDIV_SERVE_DEVICE_POOLS the operands live in a
+ * device-resident pool (HBM) instead, and each batch copies its operands in
+ * before its launch; the results still go to the mapped output ring. Requests
+ * that arrive while batches run
  * join the next launch. Admission is by footprint: a request's footprint
  * class is the size class of its dividend (class 0: at most 1024 digits,
  * 1: 2048, 2: 4096, 3: 8192, 4: more), which sets the shared memory and block
@@ -263,11 +264,11 @@ int mpdiv_mul_batch(mpdiv_ctx *ctx, int64_t n_items, const uint32_t *u, const ui
  * requests of one class only, so that a large request never sets the launch
  * shape of small ones. Batches of different classes run at once. */
 #define MPDIV_SERVE_CLASSES 5
-#define MPDIV_SERVE_DEVICE_POOLS 1 /* serve_config.flags: operands and results in device pools (HBM) */
+#define MPDIV_SERVE_DEVICE_POOLS 1 /* serve_config.flags: operands in a device pool (HBM) */
 typedef struct mpdiv_serve_config {
   int64_t pool_digits;  /* digits of the operand and result rings, half each, on the host
-                           (pinned) and, with MPDIV_SERVE_DEVICE_POOLS, on the device too
-                           (0: 64 Mi digits) */
+                           (pinned); with MPDIV_SERVE_DEVICE_POOLS the operand half on the
+                           device too (0: 64 Mi digits) */
   int32_t max_batch;    /* most requests per batch (0: 4096) */
   int32_t max_inflight; /* batches in flight at once, each on its own stream (0: 64) */
   int32_t max_pending;  /* submitted-but-unfinished requests before EBUSY (0: 1<<20) */

@@ -14,12 +14,13 @@
 // statuses sit in pinned, device-mapped memory of its slot: a batch costs one
 // kernel launch (two with the plain kernel's retry pass) and one host
 // function, with no copy.
-// With MPDIV_SERVE_DEVICE_POOLS the operands and results live in device
-// pools (HBM) mirroring the rings instead: the input ring is then allocated
-// by footprint class in chunks, so that a batch (a run of consecutive
-// requests of one class) copies its operands to the device in one copy per
-// chunk it reaches into, runs, and copies its results back, all on its own
-// stream.
+// With MPDIV_SERVE_DEVICE_POOLS the operands live in a device pool (HBM)
+// mirroring the input ring instead: the input ring is then allocated by
+// footprint class in chunks, so that a batch (a run of consecutive requests
+// of one class) copies its operands to the device in one copy per chunk it
+// reaches into before its launch, on its own stream. The results go to the
+// mapped output ring in both forms: copying them back per batch made the
+// device-pool form's tails an order of magnitude longer at 80-95 % load.
 // mpdiv_serve_submit reserves the request's digits at the tail of the input
 // ring and copies its operands there itself, outside the server lock. A
 // scheduler thread turns the oldest ready requests of a class into a batch
@@ -134,7 +135,7 @@ struct MpServer {
   // pinned host rings (their device addresses dv_*), the device pools d_*,
   // and the rings the kernels use (k_*: the pools, or the mapped host rings)
   uint32_t *h_in = nullptr, *h_out = nullptr, *dv_in = nullptr, *dv_out = nullptr;
-  uint32_t *d_in = nullptr, *d_out = nullptr, *k_in = nullptr, *k_out = nullptr;
+  uint32_t *d_in = nullptr, *k_in = nullptr, *k_out = nullptr;
   bool mapped = true;  // false with MPDIV_SERVE_DEVICE_POOLS
 
   SpinLock sub_mu;                 // in_ring, next_ticket, arrivals, ticket slots taken
@@ -309,10 +310,6 @@ bool MpServer::launch(Slot& s) {
   // the CPU's stores to the rings and the metadata come before the launch
   std::atomic_thread_fence(std::memory_order_seq_cst);
   rc = mpdiv_launch_ragged(ctx, L, s.stream);
-  if (rc == MPDIV_OK && !mapped &&
-      cudaMemcpyAsync(h_out + s.out_off, d_out + s.out_off, 4 * (size_t)s.out_len, cudaMemcpyDeviceToHost,
-                      s.stream) != cudaSuccess)
-    rc = MPDIV_ECUDA;
   return rc == MPDIV_OK && cudaLaunchHostFunc(s.stream, slot_done, &s) == cudaSuccess;
 }
 
@@ -550,12 +547,10 @@ extern "C" int mpdiv_serve_start(mpdiv_ctx* ctx, const mpdiv_serve_config* cfg) 
   if (!rc)
     rc = mpdiv_cuda_check(ctx, cudaHostGetDevicePointer((void**)&S->dv_out, S->h_out, 0),
                           "device address of the output ring");
-  if (!rc && !S->mapped) {
-    rc = mpdiv_cuda_check(ctx, cudaMalloc(&S->d_in, 4 * (size_t)half), "server input pool");
-    if (!rc) rc = mpdiv_cuda_check(ctx, cudaMalloc(&S->d_out, 4 * (size_t)half), "server output pool");
-  }
+  if (!rc && !S->mapped) rc = mpdiv_cuda_check(ctx, cudaMalloc(&S->d_in, 4 * (size_t)half), "server input pool");
   S->k_in = S->mapped ? S->dv_in : S->d_in;
-  S->k_out = S->mapped ? S->dv_out : S->d_out;
+  // results always go to the mapped output ring directly (see the top)
+  S->k_out = S->dv_out;
   S->slots = std::vector<MpServer::Slot>(S->cfg.max_inflight);
   for (auto& s : S->slots) {
     s.server = S;
@@ -750,7 +745,6 @@ void mpdiv_serve_shutdown(mpdiv_ctx* ctx) {
     if (s.d_heads) cudaFree(s.d_heads);
   }
   if (S->d_in) cudaFree(S->d_in);
-  if (S->d_out) cudaFree(S->d_out);
   if (S->by_ticket)
     for (uint64_t i = 0; i <= S->ticket_mask; i++) delete S->by_ticket[i].exchange(nullptr);
   if (S->h_in) cudaFreeHost(S->h_in);
