@@ -177,7 +177,6 @@ struct MpServer {
     // forms in device memory
     uint32_t *h_meta = nullptr, *dv_meta = nullptr;
     int32_t* d_heads = nullptr;
-    int64_t out_off = 0, out_len = 0;     // the batch's output-ring digits
     bool busy = false;           // scheduler-only
     std::atomic<int> done{0};    // set by the batch's host function
     int cls = 0;                 // footprint class of the batch in flight
@@ -426,8 +425,6 @@ void MpServer::run() {
       } else {
         free_slot->busy = true;
         free_slot->cls = adm;
-        free_slot->out_off = off;
-        free_slot->out_len = out_need;
         auto ob = std::make_shared<OutBatch>();
         ob->seq = oseq;
         ob->remaining = (int)b.size();
